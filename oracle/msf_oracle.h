@@ -1,0 +1,63 @@
+/*
+ * msf_oracle.h -- plain FP64 CPU oracle of the conservative sharp-interface
+ * multi-material method of Pan, Han, Hu & Adams (arXiv:1704.00519).
+ *
+ * TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and the
+ * cpu_baseline leg of bench.py are the only users. The product (the CUDA
+ * library) neither includes nor links this file; the two share no code.
+ */
+#ifndef MSF_ORACLE_H
+#define MSF_ORACLE_H
+#include <stdint.h>
+
+#define ORC_MAXM 8
+
+typedef struct {
+  int32_t dim;               /* 1, 2 or 3 */
+  int32_t n[3];              /* interior cells per axis (1 for unused axes) */
+  double lo[3], hi[3];       /* domain box */
+  int32_t bc[3][2];          /* 0 transmissive, 1 reflective, 2 inflow */
+  double inflow_prim[3][2][5];
+  int32_t inflow_mat[3][2];
+  int32_t nmat;
+  double gamma[ORC_MAXM], pinf[ORC_MAXM]; /* stiffened gas p=(g-1)rho e - g pinf */
+  double cfl, weno_eps, mix_alpha;
+  int32_t ext_sweeps, vel_sweeps, reinit_iters;
+  int32_t scale_sep, reinit;
+  double scale_eps_h;        /* epsilon / h_min of the scale separation */
+  double phi_cap_h;          /* level-set clamp, in units of h_min */
+} orc_params;
+
+typedef struct orc orc;
+
+/* error bits (sticky) */
+#define ORC_ENONFINITE 1
+#define ORC_ENEGATIVE 2
+#define ORC_EBAND 4
+
+/* counters */
+enum { ORC_C_CUT = 0, ORC_C_MULTI, ORC_C_CORRECTED, ORC_C_SMALL, ORC_C_MIXFAIL,
+       ORC_C_MERGE, ORC_C_ODDBALL, ORC_C_STEPS, ORC_NCOUNT };
+
+orc* orc_create(const orc_params* p);
+void orc_destroy(orc* o);
+int orc_set_levelset(orc* o, const double* phi, const int32_t* chi, const double* prim);
+int orc_step(orc* o, int32_t nsteps, double t_end);
+void orc_get_state(const orc* o, double* Q, double* alpha, double* phi, int32_t* chi, double* t);
+void orc_set_state(orc* o, const double* Q, const double* phi, const int32_t* chi, double t);
+void orc_totals(const orc* o, double* totals, double* ledger);
+void orc_counters(const orc* o, int64_t* c);
+double orc_last_dt(const orc* o);
+int orc_error(const orc* o);
+/* intermediate fields of the last stage, interior cells: 0 alpha [N], 1 Uhat [N][nv],
+   2 exchange X [N][nv], 3 interface velocity [3], 4 mixed flag, 5 step mask */
+void orc_debug_field(const orc* o, int32_t which, double* out);
+
+/* building blocks, exported for pins */
+double orc_weno5(double a, double b, double c, double d, double e, double eps);
+void orc_hllc(const double* wl, const double* wr, const double* eosl, const double* eosr,
+              double* ustar, double* pstar);
+double orc_seg_frac(double a, double b);
+double orc_tri_frac(double a, double b, double c);
+double orc_tet_frac(double a, double b, double c, double d);
+#endif

@@ -1,0 +1,192 @@
+"""ctypes wrapper around the plain FP64 C oracle (libmsf_oracle.so).
+
+Test infrastructure only: tests/, __graft_entry__.smoke() and bench.py's
+cpu_baseline leg use it. The product path never imports this module.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "msf_oracle.c")
+LIB = os.path.join(HERE, "libmsf_oracle.so")
+MAXM = 8
+COUNTERS = ["cut", "multi", "corrected", "small", "mixfail", "merge", "oddball", "steps"]
+
+
+def build(force=False):
+    """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", LIB, SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    return LIB
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("n", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+        ("bc", (C.c_int32 * 2) * 3), ("inflow_prim", ((C.c_double * 5) * 2) * 3),
+        ("inflow_mat", (C.c_int32 * 2) * 3), ("nmat", C.c_int32),
+        ("gamma", C.c_double * MAXM), ("pinf", C.c_double * MAXM),
+        ("cfl", C.c_double), ("weno_eps", C.c_double), ("mix_alpha", C.c_double),
+        ("ext_sweeps", C.c_int32), ("vel_sweeps", C.c_int32), ("reinit_iters", C.c_int32),
+        ("scale_sep", C.c_int32), ("reinit", C.c_int32),
+        ("scale_eps_h", C.c_double), ("phi_cap_h", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.c_void_p
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int32)
+        _lib.orc_create.restype = P
+        _lib.orc_create.argtypes = [C.POINTER(Params)]
+        _lib.orc_destroy.argtypes = [P]
+        _lib.orc_set_levelset.argtypes = [P, dp, ip, dp]
+        _lib.orc_step.argtypes = [P, C.c_int32, C.c_double]
+        _lib.orc_get_state.argtypes = [P, dp, dp, dp, ip, dp]
+        _lib.orc_set_state.argtypes = [P, dp, dp, ip, C.c_double]
+        _lib.orc_totals.argtypes = [P, dp, dp]
+        _lib.orc_counters.argtypes = [P, C.POINTER(C.c_int64)]
+        _lib.orc_last_dt.restype = C.c_double
+        _lib.orc_last_dt.argtypes = [P]
+        _lib.orc_error.argtypes = [P]
+        _lib.orc_debug_field.argtypes = [P, C.c_int32, dp]
+        _lib.orc_weno5.restype = C.c_double
+        _lib.orc_weno5.argtypes = [C.c_double] * 6
+        _lib.orc_hllc.argtypes = [dp, dp, dp, dp, dp, dp]
+        for f in ("orc_seg_frac", "orc_tri_frac", "orc_tet_frac"):
+            getattr(_lib, f).restype = C.c_double
+        _lib.orc_seg_frac.argtypes = [C.c_double] * 2
+        _lib.orc_tri_frac.argtypes = [C.c_double] * 3
+        _lib.orc_tet_frac.argtypes = [C.c_double] * 4
+    return _lib
+
+
+def make_params(p: dict) -> Params:
+    s = Params()
+    s.dim = p["dim"]
+    for d in range(3):
+        s.n[d] = int(p["n"][d])
+        s.lo[d] = float(p["lo"][d])
+        s.hi[d] = float(p["hi"][d])
+        for side in range(2):
+            s.bc[d][side] = int(p["bc"][d][side])
+            s.inflow_mat[d][side] = int(p["inflow_mat"][d][side])
+            for v in range(5):
+                s.inflow_prim[d][side][v] = float(p["inflow_prim"][d][side][v])
+    s.nmat = p["nmat"]
+    for m in range(p["nmat"]):
+        s.gamma[m] = p["gamma"][m]
+        s.pinf[m] = p["pinf"][m]
+    for k in ("cfl", "weno_eps", "mix_alpha", "scale_eps_h", "phi_cap_h"):
+        setattr(s, k, float(p[k]))
+    for k in ("ext_sweeps", "vel_sweeps", "reinit_iters", "scale_sep", "reinit"):
+        setattr(s, k, int(p[k]))
+    return s
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+class Oracle:
+    """One simulation instance on the CPU oracle."""
+
+    def __init__(self, case, **opts):
+        self.case = case
+        self.p = case.params(**opts)
+        self._params = make_params(self.p)
+        self.h = lib().orc_create(C.byref(self._params))
+        if not self.h:
+            raise ValueError("oracle: invalid parameters")
+        self.N, self.NV, self.cells = case.nmat, case.nv, case.cells
+        phi = np.ascontiguousarray(case.phi, np.float64).ravel()
+        chi = np.ascontiguousarray(case.chi, np.int32).ravel()
+        prim = np.ascontiguousarray(case.prim, np.float64)
+        lib().orc_set_levelset(self.h, _dp(phi), _ip(chi), _dp(prim))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_destroy(self.h)
+            self.h = None
+
+    def step(self, n_steps, t_end=np.inf):
+        return lib().orc_step(self.h, int(n_steps), float(t_end))
+
+    def state(self):
+        Q = np.zeros((self.N, self.NV, self.cells))
+        alpha = np.zeros((self.N, self.cells))
+        phi = np.zeros(self.cells)
+        chi = np.zeros(self.cells, np.int32)
+        t = np.zeros(1)
+        lib().orc_get_state(self.h, _dp(Q), _dp(alpha), _dp(phi), _ip(chi), _dp(t))
+        return dict(Q=Q, alpha=alpha, phi=phi, chi=chi, t=float(t[0]))
+
+    def set_state(self, Q, phi, chi, t):
+        Q = np.ascontiguousarray(Q, np.float64)
+        phi = np.ascontiguousarray(phi, np.float64).ravel()
+        chi = np.ascontiguousarray(chi, np.int32).ravel()
+        lib().orc_set_state(self.h, _dp(Q), _dp(phi), _ip(chi), float(t))
+
+    def totals(self):
+        tot = np.zeros((self.N, self.NV))
+        led = np.zeros((self.N, self.NV))
+        lib().orc_totals(self.h, _dp(tot), _dp(led))
+        return tot, led
+
+    def counters(self):
+        c = np.zeros(len(COUNTERS), np.int64)
+        lib().orc_counters(self.h, c.ctypes.data_as(C.POINTER(C.c_int64)))
+        return dict(zip(COUNTERS, c.tolist()))
+
+    def error(self):
+        return lib().orc_error(self.h)
+
+    def last_dt(self):
+        return lib().orc_last_dt(self.h)
+
+    def debug(self, which):
+        sizes = {0: self.N, 1: self.N * self.NV, 2: self.N * self.NV, 3: 3, 4: 1, 5: 1}
+        out = np.zeros(sizes[which] * self.cells)
+        lib().orc_debug_field(self.h, int(which), _dp(out))
+        return out
+
+
+def weno5(a, b, c, d, e, eps=1e-6):
+    return lib().orc_weno5(a, b, c, d, e, eps)
+
+
+def hllc(wl, wr, eosl, eosr):
+    us, ps = np.zeros(1), np.zeros(1)
+    arrs = [np.asarray(x, np.float64) for x in (wl, wr, eosl, eosr)]
+    lib().orc_hllc(*[_dp(a) for a in arrs], _dp(us), _dp(ps))
+    return float(us[0]), float(ps[0])
+
+
+def seg_frac(a, b):
+    return lib().orc_seg_frac(a, b)
+
+
+def tri_frac(a, b, c):
+    return lib().orc_tri_frac(a, b, c)
+
+
+def tet_frac(a, b, c, d):
+    return lib().orc_tet_frac(a, b, c, d)
