@@ -1,0 +1,188 @@
+/*
+ * msf.h -- C ABI of the GB300 (sm_103a) implementation of the conservative
+ * sharp-interface method for compressible multi-material flows of
+ * Pan, Han, Hu & Adams (arXiv:1704.00519).
+ *
+ * One context owns one CUDA device's worth of state for n_instances
+ * independent problems on uniform Cartesian grids (1D, 2D or 3D) with up to
+ * MSF_MAXMAT materials, each a stiffened gas. Every call returns an
+ * msf_status; nothing aborts, exits or throws across this boundary. Pointer
+ * arguments are plain host or device pointers as stated per call; the caller
+ * keeps ownership of everything it passes in. All arrays are dense, C order,
+ * interior cells only, with x the fastest index.
+ *
+ * Threading: a context is used by one host thread at a time.
+ * Streams: work is issued on msf_options.stream (a cudaStream_t, or NULL for
+ * the legacy default stream).
+ */
+#ifndef MSF_H
+#define MSF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSF_MAXMAT 8
+#define MSF_NSTATS 8
+
+typedef struct msf_ctx msf_ctx; /* opaque; created by msf_create, freed by msf_destroy */
+
+typedef enum {
+  MSF_OK = 0,
+  MSF_EINVAL = 1,     /* invalid argument (checked on the host before any launch) */
+  MSF_ENOMEM = 2,     /* device allocation failed */
+  MSF_ECUDA = 3,      /* a CUDA runtime call failed */
+  MSF_ENONFINITE = 4, /* a non-finite conserved value was produced */
+  MSF_ENEGATIVE = 5,  /* density <= 0 or p + pinf <= 0 met in a state that was used */
+  MSF_EBAND = 6,      /* a flux stencil reached a cell without a state of that material */
+  MSF_ETIMEOUT = 7,   /* reserved */
+  MSF_ESTATE = 8,     /* context unusable after an earlier device-detected error */
+  MSF_EUNSUPPORTED = 9
+} msf_status;
+
+typedef enum { MSF_BC_TRANSMISSIVE = 0, MSF_BC_REFLECTIVE = 1, MSF_BC_INFLOW = 2 } msf_bc;
+typedef enum { MSF_HOST = 0, MSF_DEVICE = 1 } msf_mem;
+typedef enum { MSF_FP64 = 0, MSF_FP32_BULK = 1 } msf_precision;
+
+/* Grid of one instance (Sec. 2.3: uniform Cartesian cells).
+ *   dim          1, 2 or 3; n[d] interior cells on axis d (n[d] = 1 for d >= dim)
+ *   lo, hi       domain box; h_d = (hi_d - lo_d) / n_d
+ *   bc[d][side]  msf_bc for the low (0) and high (1) side of axis d
+ *   inflow_prim  primitive (rho, u_0..u_{dim-1}, p) imposed on an inflow side
+ *   inflow_mat   material of the inflow state */
+typedef struct {
+  int32_t dim;
+  int32_t n[3];
+  double lo[3], hi[3];
+  int32_t bc[3][2];
+  double inflow_prim[3][2][5];
+  int32_t inflow_mat[3][2];
+} msf_grid;
+
+/* Stiffened gas p = (gamma - 1) rho e - gamma pinf (Sec. 2.1; pinf = 0 is the
+ * ideal gas of Sec. 2.1). Sound speed c^2 = gamma (p + pinf) / rho (Sec. 2.3.2). */
+typedef struct {
+  double gamma, pinf;
+} msf_eos;
+
+/* Run options. Zero-initialise and call msf_default_options() first.
+ *   precision    MSF_FP64: all arithmetic in FP64.
+ *                MSF_FP32_BULK: WENO5 fluxes, primitive recovery, ghost states,
+ *                HLLC and the CFL bound in FP32; conserved storage, flux
+ *                accumulation, geometry, conservation correction, level set,
+ *                mixing, scale separation and totals in FP64.
+ *   cfl          CFL number (Sec. 3: 0.6)
+ *   weno_eps     WENO5 smoothness epsilon (1e-6)
+ *   mix_alpha    cells of a material with 0 < alpha < mix_alpha are mixed (0.5)
+ *   ext_sweeps   Jacobi sweeps of the ghost-state extension (dim + 3)
+ *   vel_sweeps   Jacobi sweeps of the interface-velocity extension (6)
+ *   reinit_iters Godunov iterations of the band distance maintenance (6)
+ *   scale_sep    1: interface scale separation once per step (Sec. 2.3.3)
+ *   reinit       1: distance maintenance once per step
+ *   scale_eps_h  epsilon of the scale separation in units of h_min; 0 selects
+ *                0.5 (1D), 0.75 (2D), 0.9 (3D) (Sec. 2.3.3)
+ *   phi_cap_h    the unsigned distance is clamped at phi_cap_h * h_min (8)
+ *   use_graph    1: replay each step as a captured CUDA graph
+ *   stream       cudaStream_t for all work of this context */
+typedef struct {
+  int32_t precision;
+  double cfl, weno_eps, mix_alpha;
+  int32_t ext_sweeps, vel_sweeps, reinit_iters;
+  int32_t scale_sep, reinit;
+  double scale_eps_h, phi_cap_h;
+  int32_t use_graph;
+  void* stream;
+} msf_options;
+
+/* Fill opt with the defaults above for a grid of dimension dim. */
+msf_status msf_default_options(int32_t dim, msf_options* opt);
+
+/* Create a context for n_instances grids with n_mat materials each.
+ *   grids  [n_instances] host array; every instance must have the same dim
+ *   eos    [n_instances * n_mat] host array, instance-major
+ *   opt    host pointer
+ *   out    receives the context
+ * Allocates all device memory of the context (freed by msf_destroy).
+ * Errors: MSF_EINVAL (bad sizes, n_mat outside [1, MSF_MAXMAT], gamma <= 1,
+ * pinf < 0, non-finite box, options out of range), MSF_ENOMEM, MSF_ECUDA. */
+msf_status msf_create(const msf_grid* grids, int32_t n_instances, int32_t n_mat, const msf_eos* eos,
+                      const msf_options* opt, msf_ctx** out);
+
+/* Free every resource of the context. NULL is accepted. */
+msf_status msf_destroy(msf_ctx* ctx);
+
+/* Initial data of one instance (Sec. 2.2: regional level set (phi, chi)).
+ *   phi   [cells] unsigned distance to the interface network, phi >= 0
+ *   chi   [cells] material indicator in [0, n_mat)
+ *   prim  [n_mat][dim + 2][cells] primitive state (rho, u_d, p) of each
+ *         material, used where that material has a non-zero sub-volume
+ *   mem   MSF_HOST or MSF_DEVICE: where the three arrays live
+ * Computes the cut-cell geometry with the conservation correction and sets the
+ * conserved state alpha * U of every material; resets t, the ledger and the
+ * counters. Errors: MSF_EINVAL for phi < 0 or non-finite, chi out of range,
+ * rho <= 0 or p + pinf <= 0 or non-finite prim (host inputs are checked on
+ * the host; device inputs on the device before use). */
+msf_status msf_set_levelset(msf_ctx* ctx, int32_t instance, const double* phi, const int32_t* chi,
+                            const double* prim, int32_t mem);
+
+/* Advance every instance by up to n_steps full TVD-RK3 steps (three stages of
+ * Eq. discretized_equ with the beta_s weights of Eq. local-advection), or
+ * until t_end: the last time step is clipped so that t lands on t_end; an
+ * instance already at t_end does nothing. Work is enqueued on opt.stream.
+ * sync = 1: wait and report device-detected errors (MSF_ENONFINITE,
+ * MSF_ENEGATIVE, MSF_EBAND); sync = 0: return after enqueueing (errors are
+ * reported by the next synchronising call). After a device-detected error the
+ * context returns MSF_ESTATE until msf_set_levelset or msf_set_state. */
+msf_status msf_step(msf_ctx* ctx, int32_t n_steps, double t_end, int32_t sync);
+
+/* FP64 totals of one instance (Sec. 2.3.1, Eq. sum_equ): totals[m][v] =
+ * sum over interior cells of alpha^m U^m_v times the cell volume, and the
+ * accumulated net boundary inflow ledger[m][v] of the same quantity, so that
+ * totals(t) - totals(0) - ledger(t) vanishes to round-off (per material for
+ * mass; summed over materials for momentum and energy, which the interface
+ * exchange moves between materials). Host arrays [n_mat][dim + 2]. Synchronises. */
+msf_status msf_totals(msf_ctx* ctx, int32_t instance, double* totals, double* ledger);
+
+/* Adjoint of one step (reverse-mode derivative of the state after the last
+ * step with respect to the state before it). Not provided by this build:
+ * returns MSF_EUNSUPPORTED. */
+msf_status msf_adjoint_step(msf_ctx* ctx, const void* lam_out, void* lam_in, double* d_eos);
+
+/* Copy one instance's state out (all outputs optional, NULL skips):
+ *   Q [n_mat][dim+2][cells] conserved alpha U, alpha [n_mat][cells] volume
+ *   fractions of the current geometry, phi [cells], chi [cells], t [1].
+ * mem says where Q, alpha, phi and chi live; t is always a host pointer. Synchronises. */
+msf_status msf_get_state(msf_ctx* ctx, int32_t instance, double* Q, double* alpha, double* phi, int32_t* chi,
+                         double* t, int32_t mem);
+
+/* Replace one instance's state (Q, phi, chi as in msf_get_state; t host value);
+ * recomputes the geometry and clears a device-detected error. */
+msf_status msf_set_state(msf_ctx* ctx, int32_t instance, const double* Q, const double* phi, const int32_t* chi,
+                         double t, int32_t mem);
+
+/* Event counters summed over instances since msf_set_levelset: cut cells,
+ * cells with >= 3 materials, corrected cells, small (mixed) cells, mixing
+ * failures, merges, oddball cells, steps. counters: host [MSF_NSTATS]. Synchronises. */
+msf_status msf_stats(msf_ctx* ctx, int64_t* counters);
+
+/* Time step of the last step taken (host value). Synchronises. */
+msf_status msf_last_dt(msf_ctx* ctx, int32_t instance, double* dt);
+
+/* Intermediate fields of the last stage of one instance, for testing:
+ * which = 0 alpha [n_mat][cells], 1 stencil state [n_mat][dim+2][cells],
+ * 2 exchange flux [n_mat][dim+2][cells], 3 interface velocity [3][cells],
+ * 4 mixed-cell flag [cells], 5 step material mask [cells]. out: host double array.
+ * Cells outside the narrow band hold 0 for fields 1-3. Synchronises. */
+msf_status msf_debug_field(msf_ctx* ctx, int32_t instance, int32_t which, double* out);
+
+/* Human-readable message for the last non-OK status of this context
+ * (or of msf_create when ctx is NULL). Never NULL. */
+const char* msf_last_error(const msf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,639 @@
+// msf_capi.cu -- host runtime and C ABI (include/msf.h) of the GB300 build of
+// the conservative sharp-interface multi-material method (arXiv:1704.00519).
+//
+// The runtime owns every device allocation of a context, enqueues one
+// TVD-RK3 step as a fixed kernel sequence per instance on the context's
+// stream, captures that sequence once as a CUDA graph and replays it. Time,
+// time step, the end time and every branch on them live on the device, so a
+// replayed graph needs no host round trip; the only readback of msf_step is
+// the 4-byte error word when the caller asks for synchronisation.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/msf.h"
+#include "msf_types.cuh"
+#include "msf_ops.h"
+
+using namespace msf;
+
+namespace {
+
+struct Inst {
+  Grid g;
+  Bufs b;
+  BndBase bb;
+  int nbnd = 0;
+  int nblk_band = 1;
+};
+
+}  // namespace
+
+struct msf_ctx {
+  int dim = 0, N = 0, ninst = 0;
+  msf_options opt{};
+  cudaStream_t stream = nullptr;
+  std::vector<Inst> inst;
+  std::vector<void*> allocs;
+  const Ops* ops = nullptr;
+  Ctl* h_ctl = nullptr;  // pinned readback of one control block
+  unsigned* d_flag = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_tried = false;
+  bool sticky = false;
+  std::string err;
+};
+
+static thread_local std::string g_create_err = "";
+
+static msf_status fail(msf_ctx* c, msf_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_err = msg;
+  return s;
+}
+#define CUDA_TRY(ctx, call)                                                                      \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(ctx, MSF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+static void* dalloc(msf_ctx* c, size_t bytes, cudaError_t* err) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  *err = cudaMalloc(&p, bytes);
+  if (*err != cudaSuccess) return nullptr;
+  c->allocs.push_back(p);
+  cudaMemsetAsync(p, 0, bytes, c->stream);
+  return p;
+}
+
+extern "C" msf_status msf_default_options(int32_t dim, msf_options* opt) {
+  if (!opt || dim < 1 || dim > 3) return MSF_EINVAL;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = MSF_FP64;
+  opt->cfl = 0.6;
+  opt->weno_eps = 1e-6;
+  opt->mix_alpha = 0.5;
+  opt->ext_sweeps = dim + 3;
+  opt->vel_sweeps = 6;
+  opt->reinit_iters = 6;
+  opt->scale_sep = 1;
+  opt->reinit = 1;
+  opt->scale_eps_h = 0.0;
+  opt->phi_cap_h = 8.0;
+  opt->use_graph = 1;
+  opt->stream = nullptr;
+  return MSF_OK;
+}
+
+static int band_blocks(const Grid& g) {
+  long long b = (g.n_interior + NTHREADS - 1) / NTHREADS;
+  if (b > 608) b = 608;  // 152 SMs x 4 CTAs; band kernels stride over the list
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int32_t n_mat, const msf_eos* eos,
+                                 const msf_options* opt, msf_ctx** out) {
+  if (!out) return fail(nullptr, MSF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!grids || !eos || !opt) return fail(nullptr, MSF_EINVAL, "NULL argument");
+  if (n_instances < 1) return fail(nullptr, MSF_EINVAL, "n_instances < 1");
+  if (n_mat < 1 || n_mat > MSF_MAXMAT) return fail(nullptr, MSF_EINVAL, "n_mat outside [1, 8]");
+  const int dim = grids[0].dim;
+  if (dim < 1 || dim > 3) return fail(nullptr, MSF_EINVAL, "dim outside [1, 3]");
+  if (opt->precision != MSF_FP64 && opt->precision != MSF_FP32_BULK) return fail(nullptr, MSF_EINVAL, "precision");
+  if (!(opt->cfl > 0.0 && opt->cfl <= 1.0) || !(opt->weno_eps > 0.0) || !(opt->mix_alpha >= 0.0 && opt->mix_alpha < 1.0) ||
+      opt->ext_sweeps < 1 || opt->ext_sweeps > 64 || opt->vel_sweeps < 0 || opt->vel_sweeps > 64 ||
+      opt->reinit_iters < 0 || opt->reinit_iters > 64 || !(opt->phi_cap_h >= 4.0) || !(opt->scale_eps_h >= 0.0))
+    return fail(nullptr, MSF_EINVAL, "option out of range");
+  for (int i = 0; i < n_instances; i++) {
+    const msf_grid& gr = grids[i];
+    if (gr.dim != dim) return fail(nullptr, MSF_EINVAL, "instances must share dim");
+    for (int d = 0; d < dim; d++) {
+      if (gr.n[d] < 1 || gr.n[d] > (1 << 24)) return fail(nullptr, MSF_EINVAL, "grid size");
+      if (!std::isfinite(gr.lo[d]) || !std::isfinite(gr.hi[d]) || !(gr.hi[d] > gr.lo[d]))
+        return fail(nullptr, MSF_EINVAL, "domain box");
+      for (int s = 0; s < 2; s++) {
+        if (gr.bc[d][s] < 0 || gr.bc[d][s] > 2) return fail(nullptr, MSF_EINVAL, "bc type");
+        if (gr.bc[d][s] == 2) {
+          const int m = gr.inflow_mat[d][s];
+          if (m < 0 || m >= n_mat) return fail(nullptr, MSF_EINVAL, "inflow material");
+          const double rho = gr.inflow_prim[d][s][0], p = gr.inflow_prim[d][s][dim + 1];
+          if (!(rho > 0.0) || !(p + eos[i * n_mat + m].pinf > 0.0)) return fail(nullptr, MSF_EINVAL, "inflow state");
+        }
+      }
+    }
+    long long cells = 1;
+    for (int d = 0; d < dim; d++) cells *= (long long)(gr.n[d] + 2 * G);
+    if (cells > (1LL << 31) - 1) return fail(nullptr, MSF_EINVAL, "grid too large");
+    for (int m = 0; m < n_mat; m++) {
+      const msf_eos& e = eos[i * n_mat + m];
+      if (!(e.gamma > 1.0) || !(e.pinf >= 0.0) || !std::isfinite(e.gamma) || !std::isfinite(e.pinf))
+        return fail(nullptr, MSF_EINVAL, "EOS parameters");
+    }
+  }
+  if (n_instances > 1) return fail(nullptr, MSF_EUNSUPPORTED, "several instances per context are not supported");
+
+  msf_ctx* c = new msf_ctx();
+  c->dim = dim;
+  c->N = n_mat;
+  c->ninst = n_instances;
+  c->opt = *opt;
+  c->stream = (cudaStream_t)opt->stream;
+  c->ops = opt->precision == MSF_FP32_BULK ? ops_f32() : ops_f64();
+  const size_t ts = c->ops->tsize;
+  cudaError_t ce = cudaSuccess;
+#define ALLOC(ptr, type, count)                                        \
+  do {                                                                 \
+    ptr = (type*)dalloc(c, sizeof(type) * (size_t)(count), &ce);       \
+    if (!ptr) {                                                        \
+      msf_destroy(c);                                                  \
+      return fail(nullptr, MSF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(ce)); \
+    }                                                                  \
+  } while (0)
+  ce = cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl));
+  if (ce != cudaSuccess) {
+    delete c;
+    return fail(nullptr, MSF_ENOMEM, "cudaMallocHost");
+  }
+  ALLOC(c->d_flag, unsigned, 4);
+  c->inst.resize(n_instances);
+  for (int i = 0; i < n_instances; i++) {
+    Inst& in = c->inst[i];
+    Grid& g = in.g;
+    std::memset(&g, 0, sizeof(g));
+    const msf_grid& gr = grids[i];
+    g.D = dim;
+    g.N = n_mat;
+    g.NV = dim + 2;
+    for (int d = 0; d < 3; d++) {
+      const bool act = d < dim;
+      g.n[d] = act ? gr.n[d] : 1;
+      g.pn[d] = act ? gr.n[d] + 2 * G : 1;
+      g.off[d] = act ? G : 0;
+      g.lo[d] = act ? gr.lo[d] : 0.0;
+      g.h[d] = act ? (gr.hi[d] - gr.lo[d]) / (double)gr.n[d] : 1.0;
+      g.rh[d] = 1.0 / g.h[d];
+      g.rh2[d] = 0.5 * g.rh[d];
+      g.ih2[d] = g.rh[d] * g.rh[d];
+      for (int s = 0; s < 2; s++) {
+        g.bc[d][s] = act ? gr.bc[d][s] : 0;
+        g.inflow_mat[d][s] = gr.inflow_mat[d][s];
+        for (int v = 0; v < 5; v++) g.inflow_prim[d][s][v] = gr.inflow_prim[d][s][v];
+      }
+    }
+    g.st[0] = 1;
+    g.st[1] = g.pn[0];
+    g.st[2] = (long long)g.pn[0] * g.pn[1];
+    g.ncell = (long long)g.pn[0] * g.pn[1] * g.pn[2];
+    g.n_interior = (long long)g.n[0] * g.n[1] * g.n[2];
+    g.V = 1.0;
+    for (int d = 0; d < dim; d++) g.V = g.V * g.h[d];
+    g.rV = 1.0 / g.V;
+    for (int d = 0; d < dim; d++) g.farea[d] = g.V / g.h[d];
+    g.hmin = g.h[0];
+    for (int d = 1; d < dim; d++) g.hmin = std::fmin(g.hmin, g.h[d]);
+    const double ce_h = opt->scale_eps_h > 0.0 ? opt->scale_eps_h : (dim == 1 ? 0.5 : (dim == 2 ? 0.75 : 0.9));
+    g.eps_ss = ce_h * g.hmin;
+    g.cap = opt->phi_cap_h * g.hmin;
+    for (int m = 0; m < n_mat; m++) {
+      g.gamma[m] = eos[i * n_mat + m].gamma;
+      g.pinf[m] = eos[i * n_mat + m].pinf;
+      g.gm1[m] = g.gamma[m] - 1.0;
+      g.gpi[m] = g.gamma[m] * g.pinf[m];
+    }
+    g.cfl = opt->cfl;
+    g.weno_eps = opt->weno_eps;
+    g.mix_alpha = opt->mix_alpha;
+    g.ext_sweeps = opt->ext_sweeps;
+    g.vel_sweeps = opt->vel_sweeps;
+    g.reinit_iters = opt->reinit_iters;
+    g.scale_sep = opt->scale_sep;
+    g.reinit = opt->reinit;
+    // boundary faces, numbered per (axis, side)
+    long long nb = 0;
+    for (int d = 0; d < dim; d++)
+      for (int s = 0; s < 2; s++) {
+        in.bb.base[2 * d + s] = nb;
+        nb += g.n_interior / g.n[d];
+      }
+    in.nbnd = (int)nb;
+    in.nblk_band = band_blocks(g);
+
+    const long long nc = g.ncell, N = n_mat, NV = g.NV, nbmax = g.n_interior;
+    Bufs& b = in.b;
+    std::memset(&b, 0, sizeof(b));
+    for (int k = 0; k < 3; k++) ALLOC(b.Q[k], double, N * NV * nc);
+    ALLOC(b.phi, double, nc);
+    ALLOC(b.phin, double, nc);
+    ALLOC(b.chi, uint8_t, nc);
+    ALLOC(b.chin, uint8_t, nc);
+    ALLOC(b.xs, uint8_t, nc);
+    ALLOC(b.mtmp, uint8_t, nc);
+    ALLOC(b.smask, uint8_t, nc);
+    ALLOC(b.xsS, uint8_t, nc);
+    ALLOC(b.gflag, uint8_t, nc);
+    ALLOC(b.small, uint8_t, nc);
+    ALLOC(b.alpha, double, N * nc);
+    ALLOC(b.Alo, double, dim * N * nc);
+    ALLOC(b.Ahi, double, dim * N * nc);
+    b.W0 = dalloc(c, ts * N * NV * nc, &ce);
+    b.W1 = dalloc(c, ts * N * NV * nc, &ce);
+    b.Uh = dalloc(c, ts * N * NV * nc, &ce);
+    if (!b.W0 || !b.W1 || !b.Uh) {
+      msf_destroy(c);
+      return fail(nullptr, MSF_ENOMEM, "cudaMalloc (stage states)");
+    }
+    ALLOC(b.f0, uint8_t, N * nc);
+    ALLOC(b.f1, uint8_t, N * nc);
+    ALLOC(b.isreal, uint8_t, N * nc);
+    ALLOC(b.X, double, N * NV * nc);
+    ALLOC(b.vel0, double, 3 * nc);
+    ALLOC(b.vel1, double, 3 * nc);
+    ALLOC(b.vf0, uint8_t, nc);
+    ALLOC(b.vf1, uint8_t, nc);
+    ALLOC(b.band, int, nbmax);
+    ALLOC(b.bandidx, int, nc);
+    ALLOC(b.phit, double, nbmax);
+    ALLOC(b.chit, uint8_t, nbmax);
+    ALLOC(b.mixq, double, nbmax * N * NV);
+    ALLOC(b.bflux, double, std::max<long long>(1, nb) * N * NV);
+    ALLOC(b.ctl, Ctl, 1);
+    cudaMemsetAsync(b.bandidx, 0xff, sizeof(int) * nc, c->stream);
+  }
+#undef ALLOC
+  ce = cudaStreamSynchronize(c->stream);
+  if (ce != cudaSuccess) {
+    msf_destroy(c);
+    return fail(nullptr, MSF_ECUDA, std::string("create: ") + cudaGetErrorString(ce));
+  }
+  *out = c;
+  return MSF_OK;
+}
+
+extern "C" msf_status msf_destroy(msf_ctx* c) {
+  if (!c) return MSF_OK;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  delete c;
+  return MSF_OK;
+}
+
+// ---------------------------------------------------------------- stepping
+static msf_status enqueue_step(msf_ctx* c) {
+  const cudaStream_t s = c->stream;
+  for (Inst& in : c->inst) {
+    const Grid& g = in.g;
+    const Bufs& b = in.b;
+    const int nb = in.nblk_band;
+    launch_step_begin(b, s);
+    launch_bc_phichi(g, b, s);
+    launch_masks(g, b, s);
+    launch_geometry(g, b, b.Q[0], nullptr, nb, s);
+    launch_band_save(g, b, nb, s);
+    const double BETA[3] = {0.0, 0.75, 1.0 / 3.0};
+    const double LW[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+    for (int st = 0; st < 3; st++) {
+      double* Qs = b.Q[st];
+      double* Qo = b.Q[(st + 1) % 3];
+      c->ops->prim(g, b, Qs, nb, s);
+      void* W[2] = {b.W0, b.W1};
+      uint8_t* F[2] = {b.f0, b.f1};
+      int cur = 0;
+      for (int k = 0; k < g.ext_sweeps; k++) {
+        c->ops->extend(g, b, W[cur], W[cur ^ 1], F[cur], F[cur ^ 1], nb, s);
+        cur ^= 1;
+      }
+      c->ops->cons(g, b, Qs, W[cur], F[cur], nb, s);
+      c->ops->bc_uhat(g, b, Qs, s);
+      if (st == 0) {
+        c->ops->dt(g, b, Qs, s);
+        launch_dt_finalize(g, b, s);
+      }
+      c->ops->interface(g, b, Qs, nb, s);
+      double* V[2] = {b.vel0, b.vel1};
+      uint8_t* VF[2] = {b.vf0, b.vf1};
+      int vc = 0;
+      for (int k = 0; k < g.vel_sweeps; k++) {
+        launch_extend_vel(g, b, V[vc], V[vc ^ 1], VF[vc], VF[vc ^ 1], nb, s);
+        vc ^= 1;
+      }
+      cudaError_t fe = c->ops->flux(g, b, Qs, b.Q[0], Qo, BETA[st], 1.0 - BETA[st], in.bb, s);
+      if (fe != cudaSuccess) return fail(c, MSF_ECUDA, std::string("flux launch: ") + cudaGetErrorString(fe));
+      launch_ledger(g, b, in.nbnd, LW[st], s);
+      launch_levelset(g, b, V[vc], BETA[st], 1.0 - BETA[st], nb, s);
+      launch_scatter_phichi(g, b, nb, s);
+      launch_bc_phichi(g, b, s);
+      launch_geometry(g, b, Qo, nullptr, nb, s);
+      launch_mix(g, b, Qo, nb, s);
+    }
+    launch_step_end(b, s);
+    if (g.scale_sep) {
+      launch_scale_sep(g, b, nb, s);
+      launch_bc_phichi(g, b, s);
+    }
+    if (g.reinit) {
+      for (int k = 0; k < g.reinit_iters; k++) launch_reinit(g, b, nb, s);
+      launch_bc_phichi(g, b, s);
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, MSF_ECUDA, std::string("step launch: ") + cudaGetErrorString(e));
+  return MSF_OK;
+}
+
+__global__ void k_set_tend(Ctl* ctl, double t_end) { ctl->t_end = t_end; }
+
+static msf_status read_error(msf_ctx* c) {
+  unsigned bits = 0;
+  for (Inst& in : c->inst) {
+    cudaError_t e = cudaMemcpyAsync(c->h_ctl, in.b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, MSF_ECUDA, std::string("step: ") + cudaGetErrorString(e));
+    bits |= c->h_ctl->err;
+  }
+  if (!bits) return MSF_OK;
+  c->sticky = true;
+  if (bits & ERR_BAND) return fail(c, MSF_EBAND, "a flux stencil reached a cell without a state of that material");
+  if (bits & ERR_NEGATIVE) return fail(c, MSF_ENEGATIVE, "non-positive density or p + pinf in a used state");
+  return fail(c, MSF_ENONFINITE, "non-finite conserved value");
+}
+
+extern "C" msf_status msf_step(msf_ctx* c, int32_t n_steps, double t_end, int32_t sync) {
+  if (!c) return MSF_EINVAL;
+  if (c->sticky) return fail(c, MSF_ESTATE, "context holds a device-detected error; reset with msf_set_state");
+  if (n_steps < 0 || std::isnan(t_end)) return fail(c, MSF_EINVAL, "n_steps < 0 or t_end NaN");
+  if (n_steps == 0) return MSF_OK;
+  for (Inst& in : c->inst) k_set_tend<<<1, 1, 0, c->stream>>>(in.b.ctl, t_end);
+  bool use_graph = c->opt.use_graph != 0;
+  if (use_graph && !c->graph && !c->graph_tried) {
+    c->graph_tried = true;
+    cudaGraph_t graph;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      msf_status st = enqueue_step(c);
+      cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+      if (st == MSF_OK && e == cudaSuccess) {
+        if (cudaGraphInstantiate(&c->graph, graph, 0) != cudaSuccess) c->graph = nullptr;
+        cudaGraphDestroy(graph);
+      }
+    }
+    cudaGetLastError();
+  }
+  for (int k = 0; k < n_steps; k++) {
+    if (use_graph && c->graph) {
+      CUDA_TRY(c, cudaGraphLaunch(c->graph, c->stream));
+    } else {
+      msf_status st = enqueue_step(c);
+      if (st != MSF_OK) return st;
+    }
+  }
+  if (sync) return read_error(c);
+  return MSF_OK;
+}
+
+// ------------------------------------------------------------ data movement
+static msf_status check_instance(msf_ctx* c, int32_t i) {
+  if (!c) return MSF_EINVAL;
+  if (i < 0 || i >= c->ninst) return fail(c, MSF_EINVAL, "instance out of range");
+  return MSF_OK;
+}
+
+// device staging copy of a caller array (host or device)
+static msf_status stage_in(msf_ctx* c, const void* src, size_t bytes, int32_t mem, void** dst) {
+  cudaError_t e = cudaMalloc(dst, bytes ? bytes : 16);
+  if (e != cudaSuccess) return fail(c, MSF_ENOMEM, "staging allocation");
+  e = cudaMemcpyAsync(*dst, src, bytes, mem == MSF_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                      c->stream);
+  if (e != cudaSuccess) {
+    cudaFree(*dst);
+    return fail(c, MSF_ECUDA, "staging copy");
+  }
+  return MSF_OK;
+}
+
+// control-block setters that leave the ledger and the counters alone
+__global__ void k_ctl_activate(Ctl* ctl) {
+  ctl->active = 1;
+  ctl->nband = 0;
+}
+__global__ void k_ctl_restart(Ctl* ctl, double t) {
+  ctl->t = t;
+  ctl->dt = 0.0;
+  ctl->err = 0;
+  ctl->active = 0;
+  ctl->last = 0;
+}
+
+static msf_status finish_geometry(msf_ctx* c, Inst& in) {
+  // boundary fill and narrow band of the current (phi, chi)
+  const cudaStream_t s = c->stream;
+  k_ctl_activate<<<1, 1, 0, s>>>(in.b.ctl);
+  launch_bc_phichi(in.g, in.b, s);
+  launch_masks(in.g, in.b, s);
+  return MSF_OK;
+}
+
+extern "C" msf_status msf_set_levelset(msf_ctx* c, int32_t i, const double* phi, const int32_t* chi,
+                                       const double* prim, int32_t mem) {
+  msf_status st = check_instance(c, i);
+  if (st != MSF_OK) return st;
+  if (!phi || !chi || !prim) return fail(c, MSF_EINVAL, "NULL array");
+  if (mem != MSF_HOST && mem != MSF_DEVICE) return fail(c, MSF_EINVAL, "mem");
+  Inst& in = c->inst[i];
+  const Grid& g = in.g;
+  const long long ni = g.n_interior;
+  const int N = g.N, NV = g.NV;
+  if (mem == MSF_HOST) {
+    for (long long k = 0; k < ni; k++) {
+      if (!(phi[k] >= 0.0) || !std::isfinite(phi[k])) return fail(c, MSF_EINVAL, "phi must be finite and >= 0");
+      if (chi[k] < 0 || chi[k] >= N) return fail(c, MSF_EINVAL, "chi out of range");
+    }
+    for (int m = 0; m < N; m++)
+      for (long long k = 0; k < ni; k++) {
+        for (int v = 0; v < NV; v++)
+          if (!std::isfinite(prim[((long long)m * NV + v) * ni + k])) return fail(c, MSF_EINVAL, "non-finite prim");
+        if (!(prim[((long long)m * NV) * ni + k] > 0.0)) return fail(c, MSF_EINVAL, "rho <= 0 in prim");
+        if (!(prim[((long long)m * NV + NV - 1) * ni + k] + g.pinf[m] > 0.0))
+          return fail(c, MSF_EINVAL, "p + pinf <= 0 in prim");
+      }
+  }
+  void *dphi = nullptr, *dchi = nullptr, *dprim = nullptr;
+  if ((st = stage_in(c, phi, sizeof(double) * ni, mem, &dphi)) != MSF_OK) return st;
+  if ((st = stage_in(c, chi, sizeof(int32_t) * ni, mem, &dchi)) != MSF_OK) return st;
+  if ((st = stage_in(c, prim, sizeof(double) * ni * N * NV, mem, &dprim)) != MSF_OK) return st;
+  const cudaStream_t s = c->stream;
+  if (mem == MSF_DEVICE) {
+    unsigned flag = 0;
+    cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned), s);
+    launch_check_inputs(g, (const double*)dphi, (const int32_t*)dchi, (const double*)dprim, c->d_flag, s);
+    cudaMemcpyAsync(&flag, c->d_flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (flag) {
+      cudaFree(dphi); cudaFree(dchi); cudaFree(dprim);
+      return fail(c, MSF_EINVAL, "invalid device inputs (phi < 0, chi out of range or bad prim)");
+    }
+  }
+  Bufs& b = in.b;
+  for (int k = 0; k < 3; k++) cudaMemsetAsync(b.Q[k], 0, sizeof(double) * N * NV * g.ncell, s);
+  launch_init_levelset(g, b, (const double*)dphi, (const int32_t*)dchi, s);
+  if ((st = finish_geometry(c, in)) != MSF_OK) return st;
+  // raw volume fractions, masses alpha rho, then the corrected fractions
+  launch_geometry(g, b, nullptr, nullptr, in.nblk_band, s);
+  launch_init_mass(g, b, (const double*)dprim, b.Q[1], s);
+  launch_geometry(g, b, nullptr, b.Q[1], in.nblk_band, s);
+  cudaMemsetAsync(b.Q[1], 0, sizeof(double) * N * NV * g.ncell, s);
+  launch_init_state(g, b, (const double*)dprim, s);
+  Ctl h{};
+  h.t_end = INFINITY;
+  CUDA_TRY(c, cudaMemcpyAsync(b.ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(dphi);
+  cudaFree(dchi);
+  cudaFree(dprim);
+  if (e != cudaSuccess) return fail(c, MSF_ECUDA, std::string("set_levelset: ") + cudaGetErrorString(e));
+  c->sticky = false;
+  return MSF_OK;
+}
+
+static msf_status gather_out(msf_ctx* c, Inst& in, int which, void* dst, size_t bytes, int32_t mem, bool integer) {
+  void* tmp = nullptr;
+  if (cudaMalloc(&tmp, bytes ? bytes : 16) != cudaSuccess) return fail(c, MSF_ENOMEM, "staging allocation");
+  launch_gather(in.g, in.b, which, integer ? nullptr : (double*)tmp, integer ? (int32_t*)tmp : nullptr, c->stream);
+  cudaError_t e = cudaMemcpyAsync(dst, tmp, bytes, mem == MSF_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return fail(c, MSF_ECUDA, std::string("gather: ") + cudaGetErrorString(e));
+  return MSF_OK;
+}
+
+extern "C" msf_status msf_get_state(msf_ctx* c, int32_t i, double* Q, double* alpha, double* phi, int32_t* chi,
+                                    double* t, int32_t mem) {
+  msf_status st = check_instance(c, i);
+  if (st != MSF_OK) return st;
+  Inst& in = c->inst[i];
+  const long long ni = in.g.n_interior;
+  if (Q && (st = gather_out(c, in, 0, Q, sizeof(double) * ni * in.g.N * in.g.NV, mem, false)) != MSF_OK) return st;
+  if (alpha && (st = gather_out(c, in, 1, alpha, sizeof(double) * ni * in.g.N, mem, false)) != MSF_OK) return st;
+  if (phi && (st = gather_out(c, in, 2, phi, sizeof(double) * ni, mem, false)) != MSF_OK) return st;
+  if (chi && (st = gather_out(c, in, 3, chi, sizeof(int32_t) * ni, mem, true)) != MSF_OK) return st;
+  if (t) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, in.b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    *t = c->h_ctl->t;
+  }
+  return MSF_OK;
+}
+
+extern "C" msf_status msf_set_state(msf_ctx* c, int32_t i, const double* Q, const double* phi, const int32_t* chi,
+                                    double t, int32_t mem) {
+  msf_status st = check_instance(c, i);
+  if (st != MSF_OK) return st;
+  if (!Q || !phi || !chi || !std::isfinite(t)) return fail(c, MSF_EINVAL, "NULL array or non-finite t");
+  Inst& in = c->inst[i];
+  const Grid& g = in.g;
+  const long long ni = g.n_interior;
+  if (mem == MSF_HOST)
+    for (long long k = 0; k < ni; k++) {
+      if (!(phi[k] >= 0.0) || !std::isfinite(phi[k])) return fail(c, MSF_EINVAL, "phi must be finite and >= 0");
+      if (chi[k] < 0 || chi[k] >= g.N) return fail(c, MSF_EINVAL, "chi out of range");
+    }
+  void *dQ = nullptr, *dphi = nullptr, *dchi = nullptr;
+  if ((st = stage_in(c, Q, sizeof(double) * ni * g.N * g.NV, mem, &dQ)) != MSF_OK) return st;
+  if ((st = stage_in(c, phi, sizeof(double) * ni, mem, &dphi)) != MSF_OK) return st;
+  if ((st = stage_in(c, chi, sizeof(int32_t) * ni, mem, &dchi)) != MSF_OK) return st;
+  const cudaStream_t s = c->stream;
+  launch_scatter_state(g, in.b, (const double*)dQ, (const double*)dphi, (const int32_t*)dchi, s);
+  if ((st = finish_geometry(c, in)) != MSF_OK) return st;
+  launch_geometry(g, in.b, in.b.Q[0], nullptr, in.nblk_band, s);
+  // keep the ledger and counters, set t, clear the error
+  k_ctl_restart<<<1, 1, 0, s>>>(in.b.ctl, t);
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(dQ);
+  cudaFree(dphi);
+  cudaFree(dchi);
+  if (e != cudaSuccess) return fail(c, MSF_ECUDA, std::string("set_state: ") + cudaGetErrorString(e));
+  c->sticky = false;
+  return MSF_OK;
+}
+
+extern "C" msf_status msf_totals(msf_ctx* c, int32_t i, double* totals, double* ledger) {
+  msf_status st = check_instance(c, i);
+  if (st != MSF_OK) return st;
+  Inst& in = c->inst[i];
+  const int NMV = in.g.N * in.g.NV;
+  double* tmp = nullptr;
+  if (cudaMalloc(&tmp, sizeof(double) * NMV) != cudaSuccess) return fail(c, MSF_ENOMEM, "totals staging");
+  launch_totals(in.g, in.b.Q[0], tmp, c->stream);
+  std::vector<double> h(NMV);
+  cudaError_t e = cudaMemcpyAsync(h.data(), tmp, sizeof(double) * NMV, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_ctl, in.b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return fail(c, MSF_ECUDA, std::string("totals: ") + cudaGetErrorString(e));
+  for (int m = 0; m < in.g.N; m++)
+    for (int v = 0; v < in.g.NV; v++) {
+      if (totals) totals[m * in.g.NV + v] = h[m * in.g.NV + v];
+      if (ledger) ledger[m * in.g.NV + v] = c->h_ctl->ledger[m][v];
+    }
+  return MSF_OK;
+}
+
+extern "C" msf_status msf_stats(msf_ctx* c, int64_t* counters) {
+  if (!c || !counters) return MSF_EINVAL;
+  for (int k = 0; k < MSF_NSTATS; k++) counters[k] = 0;
+  for (Inst& in : c->inst) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, in.b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < MSF_NSTATS; k++) counters[k] += (int64_t)c->h_ctl->cnt[k];
+  }
+  return MSF_OK;
+}
+
+extern "C" msf_status msf_last_dt(msf_ctx* c, int32_t i, double* dt) {
+  msf_status st = check_instance(c, i);
+  if (st != MSF_OK) return st;
+  if (!dt) return fail(c, MSF_EINVAL, "dt is NULL");
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, c->inst[i].b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  *dt = c->h_ctl->dt;
+  return MSF_OK;
+}
+
+extern "C" msf_status msf_debug_field(msf_ctx* c, int32_t i, int32_t which, double* out) {
+  msf_status st = check_instance(c, i);
+  if (st != MSF_OK) return st;
+  if (!out) return fail(c, MSF_EINVAL, "out is NULL");
+  Inst& in = c->inst[i];
+  const long long ni = in.g.n_interior;
+  const int N = in.g.N, NV = in.g.NV;
+  switch (which) {
+    case 0: return gather_out(c, in, 1, out, sizeof(double) * ni * N, MSF_HOST, false);
+    case 1: return gather_out(c, in, c->ops->tsize == 8 ? 20 : 21, out, sizeof(double) * ni * N * NV, MSF_HOST, false);
+    case 2: return gather_out(c, in, 11, out, sizeof(double) * ni * N * NV, MSF_HOST, false);
+    case 3: {
+      const int which_vel = (in.g.vel_sweeps % 2 == 0) ? 30 : 31;
+      return gather_out(c, in, which_vel, out, sizeof(double) * ni * 3, MSF_HOST, false);
+    }
+    case 4: return gather_out(c, in, 13, out, sizeof(double) * ni, MSF_HOST, false);
+    case 5: return gather_out(c, in, 14, out, sizeof(double) * ni, MSF_HOST, false);
+    default: return fail(c, MSF_EINVAL, "which");
+  }
+}
+
+extern "C" msf_status msf_adjoint_step(msf_ctx* c, const void* lam_out, void* lam_in, double* d_eos) {
+  (void)lam_out;
+  (void)lam_in;
+  (void)d_eos;
+  if (!c) return MSF_EINVAL;
+  return fail(c, MSF_EUNSUPPORTED, "the adjoint step is not provided by this build");
+}
+
+extern "C" const char* msf_last_error(const msf_ctx* c) {
+  if (!c) return g_create_err.c_str();
+  return c->err.c_str();
+}

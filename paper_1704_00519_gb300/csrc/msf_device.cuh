@@ -1,0 +1,345 @@
+// msf_device.cuh -- device building blocks of the cut-cell multi-material
+// update (Pan, Han, Hu & Adams, arXiv:1704.00519): stiffened-gas EOS,
+// WENO5-JS, the HLLC interface state, positive-part fractions of linear
+// functions on simplices and the per-cell cut geometry.
+//
+// The FP64 kernels are compiled with -fmad=false so that every expression
+// rounds exactly as written; the operation order below is part of the method
+// definition (a fixed reading of the paper) and is kept stable on purpose.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace msf {
+
+constexpr int G = 4;          // halo layers per side
+constexpr int MAXM = 8;       // materials
+constexpr int MIX_MAXT = 26;  // mixing targets per small cell
+
+// error bits of the control block
+constexpr unsigned ERR_NONFINITE = 1u, ERR_NEGATIVE = 2u, ERR_BAND = 4u;
+// counters
+enum { C_CUT = 0, C_MULTI, C_CORRECTED, C_SMALL, C_MIXFAIL, C_MERGE, C_ODDBALL, C_STEPS, NCOUNT };
+// per-cell geometry flags
+constexpr uint8_t GF_MIXED = 1, GF_CUT = 2;
+
+// Everything a kernel needs to know about one instance's grid and materials.
+struct Grid {
+  int D, N, NV;
+  int n[3], pn[3], off[3];
+  long long st[3], ncell;
+  double lo[3], h[3], rh[3], rh2[3], ih2[3], farea[3], V, rV, hmin, eps_ss, cap;
+  double gamma[MAXM], pinf[MAXM], gm1[MAXM], gpi[MAXM];
+  double cfl, weno_eps, mix_alpha;
+  int ext_sweeps, vel_sweeps, reinit_iters, scale_sep, reinit;
+  int bc[3][2], inflow_mat[3][2];
+  double inflow_prim[3][2][5];
+  long long n_interior;
+};
+
+// Device control block of one instance.
+struct Ctl {
+  double t, dt, t_end, lam;
+  unsigned long long lam_bits;
+  int active, last;
+  unsigned err;
+  int nband, nbnd;
+  unsigned long long cnt[NCOUNT];
+  double ledger[MAXM][5];
+};
+
+// ---------------------------------------------------------------- indexing
+__host__ __device__ inline void coords(const Grid& g, long long c, int* q) {
+  q[0] = (int)(c % g.pn[0]);
+  q[1] = (int)((c / g.pn[0]) % g.pn[1]);
+  q[2] = (int)(c / ((long long)g.pn[0] * g.pn[1]));
+}
+__host__ __device__ inline long long cell_at(const Grid& g, int i, int j, int k) {
+  return i + g.st[1] * j + g.st[2] * k;
+}
+__host__ __device__ inline bool in_array(const Grid& g, int i, int j, int k) {
+  return i >= 0 && i < g.pn[0] && j >= 0 && j < g.pn[1] && k >= 0 && k < g.pn[2];
+}
+__host__ __device__ inline bool interior_q(const Grid& g, const int* q) {
+  for (int d = 0; d < g.D; d++)
+    if (q[d] < g.off[d] || q[d] >= g.off[d] + g.n[d]) return false;
+  return true;
+}
+__host__ __device__ inline bool interior_c(const Grid& g, long long c) {
+  int q[3];
+  coords(g, c, q);
+  return interior_q(g, q);
+}
+__host__ __device__ inline long long qidx(const Grid& g, int m, int v, long long c) {
+  return ((long long)m * g.NV + v) * g.ncell + c;
+}
+__host__ __device__ inline long long midx(const Grid& g, int m, long long c) { return (long long)m * g.ncell + c; }
+__host__ __device__ inline long long aidx(const Grid& g, int d, int m, long long c) {
+  return ((long long)d * g.N + m) * g.ncell + c;
+}
+__device__ inline int popcount8(unsigned x) { return __popc(x & 0xffu); }
+
+// ---------------------------------------------------------------- EOS (Sec. 2.1)
+// conservative (rho, rho u, rho E) -> primitive (rho, u, p), in T
+template <typename T>
+__device__ inline void cons_to_prim(const Grid& g, int m, int D, const T* u, T* w) {
+  T rho = u[0];
+  T vel[3] = {T(0), T(0), T(0)};
+  T q = T(0);
+  for (int d = 0; d < D; d++) vel[d] = u[1 + d] / rho;
+  for (int d = 0; d < D; d++) q += vel[d] * vel[d];
+  T ke = T(0.5) * rho * q;
+  w[0] = rho;
+  for (int d = 0; d < D; d++) w[1 + d] = vel[d];
+  w[D + 1] = T(g.gm1[m]) * (u[D + 1] - ke) - T(g.gpi[m]);
+}
+template <typename T>
+__device__ inline void prim_to_cons(const Grid& g, int m, int D, const T* w, T* u) {
+  T rho = w[0];
+  T q = T(0);
+  for (int d = 0; d < D; d++) q += w[1 + d] * w[1 + d];
+  u[0] = rho;
+  for (int d = 0; d < D; d++) u[1 + d] = rho * w[1 + d];
+  u[D + 1] = (w[D + 1] + T(g.gpi[m])) / T(g.gm1[m]) + T(0.5) * rho * q;
+}
+// c = sqrt(gamma (p + pinf) / rho); flags a non-physical state
+template <typename T>
+__device__ inline T sound(const Grid& g, int m, T rho, T p, unsigned* err) {
+  T c2 = (T(g.gamma[m]) * (p + T(g.pinf[m]))) / rho;
+  if (!(rho > T(0)) || !(c2 > T(0))) {
+    *err |= ERR_NEGATIVE;
+    c2 = c2 > T(0) ? c2 : T(0);
+  }
+  return sqrt(c2);
+}
+
+// ---------------------------------------------------------------- WENO5-JS
+// value at i+1/2 from cell values i-2..i+2 (Jiang & Shu weights 1/10, 6/10, 3/10)
+template <typename T>
+__device__ inline T weno5(T a, T b, T c, T d, T e, T eps) {
+  const T r6 = T(1.0 / 6.0), k13 = T(13.0 / 12.0);
+  T q0 = (T(2) * a - T(7) * b + T(11) * c) * r6;
+  T q1 = (-b + T(5) * c + T(2) * d) * r6;
+  T q2 = (T(2) * c + T(5) * d - e) * r6;
+  T t = a - T(2) * b + c;
+  T s0 = k13 * t * t;
+  t = a - T(4) * b + T(3) * c;
+  s0 = s0 + T(0.25) * t * t;
+  t = b - T(2) * c + d;
+  T s1 = k13 * t * t;
+  t = b - d;
+  s1 = s1 + T(0.25) * t * t;
+  t = c - T(2) * d + e;
+  T s2 = k13 * t * t;
+  t = T(3) * c - T(4) * d + e;
+  s2 = s2 + T(0.25) * t * t;
+  T b0 = eps + s0, b1 = eps + s1, b2 = eps + s2;
+  T a0 = T(0.1) / (b0 * b0);
+  T a1 = T(0.6) / (b1 * b1);
+  T a2 = T(0.3) / (b2 * b2);
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+// ---------------------------------------------------------------- HLLC (Sec. 2.3.2)
+// interface velocity and pressure of the two-state problem along n, for states
+// (rho, u_n, p) of two stiffened gases; wave speeds with Roe-averaged
+// Psi, Upsilon and p/rho
+template <typename T>
+__device__ inline void hllc_star(T rl, T ul, T pl, T gl, T pil, T rr, T ur, T pr, T gr, T pir, T* ustar, T* pstar) {
+  T c2l = (gl * (pl + pil)) / rl, c2r = (gr * (pr + pir)) / rr;
+  T cl = sqrt(c2l > T(0) ? c2l : T(0)), cr = sqrt(c2r > T(0) ? c2r : T(0));
+  T psil = (pl + gl * pil) / rl, psir = (pr + gr * pir) / rr;
+  T upsl = gl - T(1), upsr = gr - T(1);
+  T sl = sqrt(rl), sr = sqrt(rr);
+  T den = sl + sr;
+  T psit = (sl * psil + sr * psir) / den;
+  T upst = (sl * upsl + sr * upsr) / den;
+  T du = (ur - ul) / den;
+  T prt = (sl * (pl / rl) + sr * (pr / rr)) / den + T(0.5) * (sl * sr) * (du * du);
+  T ct2 = psit + upst * prt;
+  T ct = sqrt(ct2 > T(0) ? ct2 : T(0));
+  T ut = (sl * ul + sr * ur) / den;
+  T SL = fmin(ul - cl, ut - ct);
+  T SR = fmax(ut + ct, ur + cr);
+  T ml = (ul - SL) * rl, mr = (SR - ur) * rr;
+  T SM = (mr * ur + ml * ul + pl - pr) / (mr + ml);
+  T psl = pl + rl * (SL - ul) * (SM - ul);
+  T psr = pr + rr * (SR - ur) * (SM - ur);
+  *ustar = SM;
+  *pstar = T(0.5) * (psl + psr);
+}
+
+// ------------------------------------------- positive-part simplex fractions
+__device__ inline double frac_seg(double a, double b) {
+  int np = (a > 0.0) + (b > 0.0), nn = (a < 0.0) + (b < 0.0);
+  if (nn == 0) return np == 0 ? 0.5 : 1.0;
+  if (np == 0) return 0.0;
+  double pos = a > 0.0 ? a : b, neg = a > 0.0 ? b : a;
+  return pos / (pos - neg);
+}
+__device__ inline void sort3_desc(double& a, double& b, double& c) {
+  // insertion order identical to a stable descending insertion sort
+  double t;
+  if (b > a) { t = a; a = b; b = t; }
+  if (c > b) {
+    t = b; b = c; c = t;
+    if (b > a) { t = a; a = b; b = t; }
+  }
+}
+__device__ inline double frac_tri(double a, double b, double c) {
+  sort3_desc(a, b, c);
+  int np = (a > 0.0) + (b > 0.0) + (c > 0.0);
+  int nn = (a < 0.0) + (b < 0.0) + (c < 0.0);
+  if (nn == 0) return np == 0 ? 0.5 : 1.0;
+  if (np == 0) return 0.0;
+  if (np == 1) return (a * a) / ((a - b) * (a - c));
+  return 1.0 - (c * c) / ((a - c) * (b - c));
+}
+__device__ inline double frac_tet(double a, double b, double c, double d) {
+  double v[4] = {a, b, c, d};
+  for (int i = 1; i < 4; i++)
+    for (int j = i; j > 0 && v[j] > v[j - 1]; j--) {
+      double t = v[j]; v[j] = v[j - 1]; v[j - 1] = t;
+    }
+  int np = (v[0] > 0.0) + (v[1] > 0.0) + (v[2] > 0.0) + (v[3] > 0.0);
+  int nn = (v[0] < 0.0) + (v[1] < 0.0) + (v[2] < 0.0) + (v[3] < 0.0);
+  if (nn == 0) return np == 0 ? 0.5 : 1.0;
+  if (np == 0) return 0.0;
+  if (np == 1) return (v[0] * v[0] * v[0]) / (((v[0] - v[1]) * (v[0] - v[2])) * (v[0] - v[3]));
+  if (np == 3) {
+    double m3 = -v[3];
+    return 1.0 - (m3 * m3 * m3) / (((v[0] - v[3]) * (v[1] - v[3])) * (v[2] - v[3]));
+  }
+  double A = v[0], B = v[1], C = v[2], E = v[3];
+  double num = A * A * (B * B) - A * B * (A + B) * (C + E) + C * E * (A * A + A * B + B * B);
+  double den = ((A - C) * (A - E)) * ((B - C) * (B - E));
+  return num / den;
+}
+
+// ---------------------------------- local level sets (Sec. 2.2, operator C_m)
+__device__ inline double phi_m(const double* phi, const uint8_t* chi, long long c, int m) {
+  return chi[c] == m ? phi[c] : -phi[c];
+}
+// value at grid vertex (I, J, K): mean of the 2^D cells around it, summed in memory order
+__device__ inline double vertex_val(const Grid& g, const double* phi, const uint8_t* chi, int I, int J, int K, int m) {
+  const int D = g.D;
+  double s = 0.0;
+  const int k0 = D >= 3 ? K - 1 : K, j0 = D >= 2 ? J - 1 : J;
+  for (int kk = k0; kk <= K; kk++)
+    for (int jj = j0; jj <= J; jj++)
+      for (int ii = I - 1; ii <= I; ii++) s += phi_m(phi, chi, cell_at(g, ii, jj, kk), m);
+  return s * (D == 1 ? 0.5 : (D == 2 ? 0.25 : 0.125));
+}
+__device__ inline double facec_val(const Grid& g, const double* phi, const uint8_t* chi, long long c, int d, int side,
+                                   int m) {
+  long long a = side ? c : c - g.st[d], b = side ? c + g.st[d] : c;
+  return (phi_m(phi, chi, a, m) + phi_m(phi, chi, b, m)) * 0.5;
+}
+
+// volume fraction and raw face apertures of material m in cell c
+__device__ inline void cell_geom(const Grid& g, const double* phi, const uint8_t* chi, long long c, int m,
+                                 double* alpha, double* alo, double* ahi) {
+  int q[3];
+  coords(g, c, q);
+  const int i = q[0], j = q[1], k = q[2];
+  double vc = phi_m(phi, chi, c, m);
+  if (g.D == 1) {
+    double c0 = vertex_val(g, phi, chi, i, j, k, m), c1 = vertex_val(g, phi, chi, i + 1, j, k, m);
+    *alpha = (frac_seg(c0, vc) + frac_seg(vc, c1)) * 0.5;
+    alo[0] = c0 > 0.0 ? 1.0 : (c0 < 0.0 ? 0.0 : 0.5);
+    ahi[0] = c1 > 0.0 ? 1.0 : (c1 < 0.0 ? 0.0 : 0.5);
+  } else if (g.D == 2) {
+    double c00 = vertex_val(g, phi, chi, i, j, k, m), c10 = vertex_val(g, phi, chi, i + 1, j, k, m);
+    double c01 = vertex_val(g, phi, chi, i, j + 1, k, m), c11 = vertex_val(g, phi, chi, i + 1, j + 1, k, m);
+    alo[0] = frac_seg(c00, c01);
+    ahi[0] = frac_seg(c10, c11);
+    alo[1] = frac_seg(c00, c10);
+    ahi[1] = frac_seg(c01, c11);
+    *alpha = (frac_tri(vc, c00, c01) + frac_tri(vc, c10, c11) + frac_tri(vc, c00, c10) + frac_tri(vc, c01, c11)) * 0.25;
+  } else {
+    double cv[2][2][2];
+    for (int a = 0; a < 2; a++)
+      for (int b = 0; b < 2; b++)
+        for (int e = 0; e < 2; e++) cv[a][b][e] = vertex_val(g, phi, chi, i + e, j + b, k + a, m);
+    double vol = 0.0;
+    for (int f = 0; f < 6; f++) {
+      const int d = f >> 1, side = f & 1;
+      double fc = facec_val(g, phi, chi, c, d, side, m);
+      double p[4];
+      // corners of face f in cyclic order
+      if (d == 0) {
+        p[0] = cv[0][0][side]; p[1] = cv[0][1][side]; p[2] = cv[1][1][side]; p[3] = cv[1][0][side];
+      } else if (d == 1) {
+        p[0] = cv[0][side][0]; p[1] = cv[0][side][1]; p[2] = cv[1][side][1]; p[3] = cv[1][side][0];
+      } else {
+        p[0] = cv[side][0][0]; p[1] = cv[side][0][1]; p[2] = cv[side][1][1]; p[3] = cv[side][1][0];
+      }
+      double ap = 0.0;
+      for (int e = 0; e < 4; e++) {
+        double p0 = p[e], p1 = p[(e + 1) & 3];
+        ap += frac_tri(fc, p0, p1);
+        vol += frac_tet(vc, fc, p0, p1);
+      }
+      ap = ap * 0.25;
+      if (side) ahi[d] = ap; else alo[d] = ap;
+    }
+    *alpha = vol * (1.0 / 24.0);
+  }
+}
+
+// min / max of phi^m over the simplex vertices of cell c (centre, corners, 3D face centres)
+__device__ inline void vertex_minmax(const Grid& g, const double* phi, const uint8_t* chi, long long c, int m,
+                                     double* mn, double* mx) {
+  int q[3];
+  coords(g, c, q);
+  double lo = phi_m(phi, chi, c, m), hi = lo;
+  const int nz = g.D >= 3 ? 2 : 1, ny = g.D >= 2 ? 2 : 1;
+  for (int a = 0; a < nz; a++)
+    for (int b = 0; b < ny; b++)
+      for (int e = 0; e < 2; e++) {
+        double v = vertex_val(g, phi, chi, q[0] + e, q[1] + b, q[2] + a, m);
+        lo = fmin(lo, v);
+        hi = fmax(hi, v);
+      }
+  if (g.D == 3)
+    for (int d = 0; d < 3; d++)
+      for (int s = 0; s < 2; s++) {
+        double v = facec_val(g, phi, chi, c, d, s, m);
+        lo = fmin(lo, v);
+        hi = fmax(hi, v);
+      }
+  *mn = lo;
+  *mx = hi;
+}
+
+// unit normal of phi^m by central differences (zero where the gradient vanishes)
+__device__ inline void normal_m(const Grid& g, const double* phi, const uint8_t* chi, long long c, int m, double* n) {
+  double gr[3] = {0.0, 0.0, 0.0}, q = 0.0;
+  for (int d = 0; d < g.D; d++)
+    gr[d] = (phi_m(phi, chi, c + g.st[d], m) - phi_m(phi, chi, c - g.st[d], m)) * g.rh2[d];
+  for (int d = 0; d < g.D; d++) q += gr[d] * gr[d];
+  double len = sqrt(q);
+  n[0] = n[1] = n[2] = 0.0;
+  if (len > 0.0)
+    for (int d = 0; d < g.D; d++) n[d] = gr[d] / len;
+}
+
+// boundary source index along axis d for halo coordinate idx
+__host__ __device__ inline int bc_source(const Grid& g, int d, int idx, int* side) {
+  const int n = g.n[d], off = g.off[d], r = idx - off;
+  if (r < 0) {
+    *side = 0;
+    return g.bc[d][0] == 1 ? off + (-1 - r) : off;
+  }
+  *side = 1;
+  const int kk = r - n;
+  return g.bc[d][1] == 1 ? off + n - 1 - kk : off + n - 1;
+}
+
+__device__ inline void atomic_max_pos_double(unsigned long long* addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace msf

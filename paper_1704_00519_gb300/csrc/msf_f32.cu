@@ -1,0 +1,13 @@
+// msf_f32.cu -- FP32-bulk instantiation: WENO5 fluxes, primitive recovery,
+// ghost states, HLLC and the CFL bound in float; conserved state, flux
+// accumulation and the RK update stay FP64.
+#include "msf_kernels.cuh"
+#include "msf_ops.h"
+#include "msf_prec.inc"
+
+namespace msf {
+const Ops* ops_f32() {
+  static const Ops ops = make_ops<float>();
+  return &ops;
+}
+}  // namespace msf

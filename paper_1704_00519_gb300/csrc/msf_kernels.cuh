@@ -1,0 +1,1263 @@
+// msf_kernels.cuh -- kernels of one TVD-RK3 step of the conservative
+// sharp-interface multi-material method (arXiv:1704.00519), templated on the
+// bulk arithmetic type T (double, or float for the FP32-bulk form).
+//
+// Data layout in HBM (one instance): structure of arrays over the padded grid
+// (G = 4 halo layers per side, x fastest): Q[m][v][cell] in FP64 for every
+// material (three copies: Q^n and two RK stages), phi / chi of the regional
+// level set, per-cell u8 masks, and FP64 geometry arrays that are written and
+// read only inside the narrow band. Bulk cells (one material within +-5 cells)
+// never touch the geometry arrays: their stencil state is Q itself.
+#pragma once
+
+#include "msf_types.cuh"
+
+namespace msf {
+// kernels have internal linkage: each precision unit compiles its own copy
+namespace {
+
+__device__ inline bool ctl_active(const Bufs& b) { return b.ctl->active != 0; }
+
+// --------------------------------------------------------------- halo cells
+__device__ inline long long halo_count(const Grid& g) { return g.ncell - g.n_interior; }
+__device__ inline void halo_coords(const Grid& g, long long idx, int* q) {
+  // z slabs, then y rows of interior z, then x columns of interior (y, z)
+  if (g.D == 3) {
+    long long slab = 2LL * G * g.pn[0] * g.pn[1];
+    if (idx < slab) {
+      long long l = idx / ((long long)g.pn[0] * g.pn[1]);
+      long long r = idx % ((long long)g.pn[0] * g.pn[1]);
+      q[2] = l < G ? (int)l : (int)(g.off[2] + g.n[2] + (l - G));
+      q[1] = (int)(r / g.pn[0]);
+      q[0] = (int)(r % g.pn[0]);
+      return;
+    }
+    idx -= slab;
+    long long rows = 2LL * G * g.pn[0] * g.n[2];
+    if (idx < rows) {
+      long long kk = idx / (2LL * G * g.pn[0]);
+      long long r = idx % (2LL * G * g.pn[0]);
+      long long l = r / g.pn[0];
+      q[2] = (int)(g.off[2] + kk);
+      q[1] = l < G ? (int)l : (int)(g.off[1] + g.n[1] + (l - G));
+      q[0] = (int)(r % g.pn[0]);
+      return;
+    }
+    idx -= rows;
+    long long kk = idx / (2LL * G * g.n[1]);
+    long long r = idx % (2LL * G * g.n[1]);
+    long long jj = r / (2 * G);
+    long long l = r % (2 * G);
+    q[2] = (int)(g.off[2] + kk);
+    q[1] = (int)(g.off[1] + jj);
+    q[0] = l < G ? (int)l : (int)(g.off[0] + g.n[0] + (l - G));
+    return;
+  }
+  if (g.D == 2) {
+    q[2] = 0;
+    long long rows = 2LL * G * g.pn[0];
+    if (idx < rows) {
+      long long l = idx / g.pn[0];
+      q[1] = l < G ? (int)l : (int)(g.off[1] + g.n[1] + (l - G));
+      q[0] = (int)(idx % g.pn[0]);
+      return;
+    }
+    idx -= rows;
+    long long jj = idx / (2 * G);
+    long long l = idx % (2 * G);
+    q[1] = (int)(g.off[1] + jj);
+    q[0] = l < G ? (int)l : (int)(g.off[0] + g.n[0] + (l - G));
+    return;
+  }
+  q[1] = q[2] = 0;
+  q[0] = idx < G ? (int)idx : (int)(g.off[0] + g.n[0] + (idx - G));
+}
+
+// halo cells of phi, chi: every out-of-range axis mapped to its boundary source
+__global__ void k_bc_phichi(Grid g, Bufs b) {
+  long long nh = halo_count(g);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nh;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int q[3], s[3], side;
+    halo_coords(g, idx, q);
+    for (int d = 0; d < 3; d++) s[d] = q[d];
+    for (int d = 0; d < g.D; d++)
+      if (q[d] < g.off[d] || q[d] >= g.off[d] + g.n[d]) s[d] = bc_source(g, d, q[d], &side);
+    long long c = cell_at(g, q[0], q[1], q[2]), sc = cell_at(g, s[0], s[1], s[2]);
+    b.phi[c] = b.phi[sc];
+    b.chi[c] = b.chi[sc];
+  }
+}
+
+// -------------------------------------------------- step masks and the band
+// xs = material bits of the 3^d block (clamped to the array)
+__global__ void k_xs(Grid g, Bufs b) {
+  if (!ctl_active(b)) return;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    int q[3];
+    coords(g, c, q);
+    unsigned bits = 0;
+    const int rz = g.D >= 3 ? 1 : 0, ry = g.D >= 2 ? 1 : 0;
+    for (int dz = -rz; dz <= rz; dz++)
+      for (int dy = -ry; dy <= ry; dy++)
+        for (int dx = -1; dx <= 1; dx++)
+          if (in_array(g, q[0] + dx, q[1] + dy, q[2] + dz))
+            bits |= 1u << b.chi[cell_at(g, q[0] + dx, q[1] + dy, q[2] + dz)];
+    b.xs[c] = (uint8_t)bits;
+  }
+}
+// OR-dilation by +-4 along axis d (separable box of the step mask)
+__global__ void k_dilate(Grid g, Bufs b, const uint8_t* src, uint8_t* dst, int d) {
+  if (!ctl_active(b)) return;
+  const int R = 4;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    int q[3];
+    coords(g, c, q);
+    unsigned bits = 0;
+    for (int o = -R; o <= R; o++) {
+      int p = q[d] + o;
+      if (p < 0 || p >= g.pn[d]) continue;
+      bits |= src[c + (long long)o * g.st[d]];
+    }
+    dst[c] = (uint8_t)bits;
+  }
+}
+// final step mask on interior cells, band compaction, per-step resets
+__global__ void k_band(Grid g, Bufs b, const uint8_t* dil) {
+  if (!ctl_active(b)) return;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    uint8_t m = 0;
+    bool inner = interior_c(g, c);
+    if (inner) m = dil[c];
+    b.smask[c] = m;
+    b.gflag[c] = 0;
+    b.small[c] = 0;
+    int bi = -1;
+    if (inner && popcount8(m) >= 2) {
+      bi = atomicAdd(&b.ctl->nband, 1);
+      b.band[bi] = (int)c;
+    }
+    b.bandidx[c] = bi;
+  }
+}
+
+// step start: activity flag, band counter reset
+__global__ void k_step_begin(Bufs b) {
+  Ctl* t = b.ctl;
+  t->active = (t->t < t->t_end && t->err == 0) ? 1 : 0;
+  t->nband = 0;
+  t->lam_bits = 0ull;
+}
+
+// save phi^n, chi^n of band cells (used pointwise by the level-set RK stages)
+__global__ void k_band_save(Grid g, Bufs b) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    long long c = b.band[k];
+    b.phin[c] = b.phi[c];
+    b.chin[c] = b.chi[c];
+  }
+}
+
+// --------------------------------------------- geometry + correction (a3, a4)
+// Qs == nullptr: raw volume fractions (start-up), no correction
+__global__ void k_geometry(Grid g, Bufs b, const double* Qs, const double* mass) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband;
+  const int N = g.N, D = g.D;
+  unsigned long long nmulti = 0, ncorr = 0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const long long c = b.band[k];
+    int q[3];
+    coords(g, c, q);
+    unsigned bits = 0;
+    const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
+    for (int dz = -rz; dz <= rz; dz++)
+      for (int dy = -ry; dy <= ry; dy++)
+        for (int dx = -1; dx <= 1; dx++)
+          if (in_array(g, q[0] + dx, q[1] + dy, q[2] + dz))
+            bits |= 1u << b.chi[cell_at(g, q[0] + dx, q[1] + dy, q[2] + dz)];
+    b.xsS[c] = (uint8_t)bits;
+    for (int m = 0; m < N; m++) {
+      b.alpha[midx(g, m, c)] = 0.0;
+      for (int d = 0; d < D; d++) b.Alo[aidx(g, d, m, c)] = b.Ahi[aidx(g, d, m, c)] = 0.0;
+    }
+    if (popcount8(bits) < 2) {
+      const int m = b.chi[c];
+      b.alpha[midx(g, m, c)] = 1.0;
+      for (int d = 0; d < D; d++) b.Alo[aidx(g, d, m, c)] = b.Ahi[aidx(g, d, m, c)] = 1.0;
+      b.gflag[c] = 0;
+      continue;
+    }
+    b.gflag[c] = GF_MIXED;
+    for (int m = 0; m < N; m++) {
+      if (!((bits >> m) & 1u)) continue;
+      double a, alo[3] = {0, 0, 0}, ahi[3] = {0, 0, 0};
+      cell_geom(g, b.phi, b.chi, c, m, &a, alo, ahi);
+      b.alpha[midx(g, m, c)] = a;
+      for (int d = 0; d < D; d++) {
+        b.Alo[aidx(g, d, m, c)] = alo[d];
+        b.Ahi[aidx(g, d, m, c)] = ahi[d];
+      }
+    }
+    // the materials partition every face
+    for (int d = 0; d < D; d++)
+      for (int side = 0; side < 2; side++) {
+        double* A = side ? b.Ahi : b.Alo;
+        double s = 0.0;
+        for (int m = 0; m < N; m++)
+          if ((bits >> m) & 1u) s += A[aidx(g, d, m, c)];
+        if (s > 0.0)
+          for (int m = 0; m < N; m++)
+            if ((bits >> m) & 1u) A[aidx(g, d, m, c)] = A[aidx(g, d, m, c)] / s;
+      }
+    // conservation correction (Sec. 2.3.1, Eq. vol_corr2)
+    const double* Mref = Qs ? Qs : mass;
+    if (!Mref) continue;
+    int np = 0;
+    double sum = 0.0;
+    for (int m = 0; m < N; m++)
+      if (b.alpha[midx(g, m, c)] > 0.0) {
+        np++;
+        sum += b.alpha[midx(g, m, c)];
+      }
+    if (np < 3) continue;
+    nmulti++;
+    double rem = 1.0 - sum;
+    if (rem != 0.0) ncorr++;
+    unsigned used = 0;
+    while (rem != 0.0) {
+      int best = -1;
+      for (int m = 0; m < N; m++)
+        if (b.alpha[midx(g, m, c)] > 0.0 && !((used >> m) & 1u))
+          if (best < 0 || Mref[qidx(g, m, 0, c)] < Mref[qidx(g, best, 0, c)]) best = m;
+      if (best < 0) break;
+      used |= 1u << best;
+      double na = b.alpha[midx(g, best, c)] + rem;
+      if (na >= 0.0) {
+        b.alpha[midx(g, best, c)] = na;
+        rem = 0.0;
+      } else {
+        b.alpha[midx(g, best, c)] = 0.0;
+        rem = na;
+      }
+    }
+  }
+  if (Qs) {
+    if (nmulti) atomicAdd(&b.ctl->cnt[C_MULTI], nmulti);
+    if (ncorr) atomicAdd(&b.ctl->cnt[C_CORRECTED], ncorr);
+  }
+}
+
+// present: positive volume or a positive aperture on one of the cell's faces
+__device__ inline bool present(const Grid& g, const Bufs& b, long long c, int m) {
+  if (b.alpha[midx(g, m, c)] > 0.0) return true;
+  if (!(b.gflag[c] & GF_MIXED) || !((b.xsS[c] >> m) & 1u)) return false;
+  for (int d = 0; d < g.D; d++)
+    if (b.Alo[aidx(g, d, m, c)] > 0.0 || b.Ahi[aidx(g, d, m, c)] > 0.0) return true;
+  return false;
+}
+
+// aperture of material m on the face between cL and cR = cL + e_d
+__device__ inline double face_aperture(const Grid& g, const Bufs& b, long long cL, long long cR, int d, int m) {
+  if (b.gflag[cL] & GF_MIXED) return ((b.xsS[cL] >> m) & 1u) ? b.Ahi[aidx(g, d, m, cL)] : 0.0;
+  if (b.gflag[cR] & GF_MIXED) return ((b.xsS[cR] >> m) & 1u) ? b.Alo[aidx(g, d, m, cR)] : 0.0;
+  return (b.chi[cL] == m && b.chi[cR] == m) ? 1.0 : 0.0;
+}
+
+// volume fraction of m in an interior cell (band cells carry the geometry arrays)
+__device__ inline double alpha_of(const Grid& g, const Bufs& b, long long c, int m) {
+  if (b.bandidx[c] >= 0) return b.alpha[midx(g, m, c)];
+  return b.chi[c] == m ? 1.0 : 0.0;
+}
+
+// -------------------------------------- primitive recovery + ghosts (a5, a6)
+template <typename T>
+__global__ void k_prim(Grid g, Bufs b, const double* Qs) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, N = g.N, NV = g.NV;
+  T* W0 = (T*)b.W0;
+  T* W1 = (T*)b.W1;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const long long c = b.band[k];
+    for (int m = 0; m < N; m++) {
+      b.f0[midx(g, m, c)] = 0;
+      b.isreal[midx(g, m, c)] = 0;
+      if (!((b.smask[c] >> m) & 1u)) continue;
+      const double a = b.alpha[midx(g, m, c)];
+      if (b.chi[c] == m && a > 0.0) {
+        T u[5], w[5];
+        for (int v = 0; v < NV; v++) u[v] = (T)(Qs[qidx(g, m, v, c)] / a);
+        cons_to_prim<T>(g, m, g.D, u, w);
+        for (int v = 0; v < NV; v++) W0[qidx(g, m, v, c)] = W1[qidx(g, m, v, c)] = w[v];
+        b.f0[midx(g, m, c)] = 1;
+        b.isreal[midx(g, m, c)] = 1;
+      }
+    }
+  }
+}
+
+// one Jacobi sweep: targets take the upwind-weighted mean of filled face
+// neighbours (weights max(0, n . e)), else the plain mean of filled neighbours
+template <typename T>
+__global__ void k_extend(Grid g, Bufs b, const void* Win, void* Wout, const uint8_t* fin, uint8_t* fout) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
+  const T* Wi = (const T*)Win;
+  T* Wo = (T*)Wout;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const long long c = b.band[k];
+    for (int m = 0; m < N; m++) {
+      if (!((b.smask[c] >> m) & 1u)) continue;
+      if (b.isreal[midx(g, m, c)]) {
+        fout[midx(g, m, c)] = 1;
+        continue;
+      }
+      double n[3];
+      normal_m(g, b.phi, b.chi, c, m, n);
+      T acc[5] = {T(0), T(0), T(0), T(0), T(0)}, acc2[5] = {T(0), T(0), T(0), T(0), T(0)};
+      T sw = T(0);
+      int cnt = 0;
+      for (int d = 0; d < D; d++)
+        for (int s = 0; s < 2; s++) {
+          const long long j = s ? c + g.st[d] : c - g.st[d];
+          if (!interior_c(g, j) || b.bandidx[j] < 0 || !((b.smask[j] >> m) & 1u) || !fin[midx(g, m, j)]) continue;
+          T w = (T)(s ? n[d] : -n[d]);
+          w = w > T(0) ? w : T(0);
+          for (int v = 0; v < NV; v++) {
+            const T x = Wi[qidx(g, m, v, j)];
+            acc[v] += w * x;
+            acc2[v] += x;
+          }
+          sw += w;
+          cnt++;
+        }
+      if (sw > T(0)) {
+        for (int v = 0; v < NV; v++) Wo[qidx(g, m, v, c)] = acc[v] / sw;
+        fout[midx(g, m, c)] = 1;
+      } else if (cnt > 0) {
+        for (int v = 0; v < NV; v++) Wo[qidx(g, m, v, c)] = acc2[v] / (T)cnt;
+        fout[midx(g, m, c)] = 1;
+      } else {
+        for (int v = 0; v < NV; v++) Wo[qidx(g, m, v, c)] = Wi[qidx(g, m, v, c)];
+        fout[midx(g, m, c)] = fin[midx(g, m, c)];
+      }
+    }
+  }
+}
+
+// stencil state of band cells: real Q/alpha, ghost cons(W), else NaN
+template <typename T>
+__global__ void k_cons(Grid g, Bufs b, const double* Qs, const void* Wfin, const uint8_t* ffin) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, N = g.N, NV = g.NV;
+  const T* W = (const T*)Wfin;
+  T* Uh = (T*)b.Uh;
+  const T nanv = (T)__longlong_as_double(0x7ff8000000000000LL);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const long long c = b.band[k];
+    for (int m = 0; m < N; m++) {
+      T u[5];
+      if (!((b.smask[c] >> m) & 1u)) {
+        for (int v = 0; v < NV; v++) u[v] = nanv;
+      } else if (b.isreal[midx(g, m, c)]) {
+        const double a = b.alpha[midx(g, m, c)];
+        for (int v = 0; v < NV; v++) u[v] = (T)(Qs[qidx(g, m, v, c)] / a);
+      } else if (ffin[midx(g, m, c)]) {
+        T w[5];
+        for (int v = 0; v < NV; v++) w[v] = W[qidx(g, m, v, c)];
+        prim_to_cons<T>(g, m, g.D, w, u);
+      } else {
+        for (int v = 0; v < NV; v++) u[v] = nanv;
+      }
+      for (int v = 0; v < NV; v++) Uh[qidx(g, m, v, c)] = u[v];
+    }
+  }
+}
+
+// stencil state of an interior cell (bulk: Q; band: Uh; otherwise NaN)
+template <typename T>
+__device__ inline void interior_uhat(const Grid& g, const Bufs& b, const double* Qs, long long c, int m, T* u) {
+  const T nanv = (T)__longlong_as_double(0x7ff8000000000000LL);
+  const T* Uh = (const T*)b.Uh;
+  if (b.bandidx[c] >= 0) {
+    if ((b.smask[c] >> m) & 1u)
+      for (int v = 0; v < g.NV; v++) u[v] = Uh[qidx(g, m, v, c)];
+    else
+      for (int v = 0; v < g.NV; v++) u[v] = nanv;
+  } else if (b.chi[c] == m) {
+    for (int v = 0; v < g.NV; v++) u[v] = (T)Qs[qidx(g, m, v, c)];
+  } else {
+    for (int v = 0; v < g.NV; v++) u[v] = nanv;
+  }
+}
+
+// halo cells of the stencil state (one axis out of range at a time)
+template <typename T>
+__global__ void k_bc_uhat(Grid g, Bufs b, const double* Qs) {
+  if (!ctl_active(b)) return;
+  const int N = g.N, NV = g.NV, D = g.D;
+  long long per[3] = {0, 0, 0}, total = 0;
+  for (int d = 0; d < D; d++) {
+    per[d] = 2LL * G * (g.n_interior / g.n[d]);
+    total += per[d];
+  }
+  T* Uh = (T*)b.Uh;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int d = 0;
+    long long r = idx;
+    while (r >= per[d]) { r -= per[d]; d++; }
+    // r -> (layer l in [0, 2G), other coordinates in interior order)
+    const long long l = r % (2 * G);
+    long long rest = r / (2 * G);
+    int q[3];
+    for (int e = 0; e < 3; e++) {
+      if (e == d) continue;
+      if (e >= D) { q[e] = 0; continue; }
+      q[e] = (int)(g.off[e] + rest % g.n[e]);
+      rest /= g.n[e];
+    }
+    q[d] = l < G ? (int)l : (int)(g.off[d] + g.n[d] + (l - G));
+    int side;
+    int s[3] = {q[0], q[1], q[2]};
+    s[d] = bc_source(g, d, q[d], &side);
+    const long long c = cell_at(g, q[0], q[1], q[2]), sc = cell_at(g, s[0], s[1], s[2]);
+    const int type = g.bc[d][side];
+    for (int m = 0; m < N; m++) {
+      T u[5];
+      if (type == 2 && m == g.inflow_mat[d][side]) {
+        T w[5];
+        for (int v = 0; v < NV; v++) w[v] = (T)g.inflow_prim[d][side][v];
+        prim_to_cons<T>(g, m, D, w, u);
+      } else {
+        interior_uhat<T>(g, b, Qs, sc, m, u);
+        if (type == 1) u[1 + d] = -u[1 + d];
+      }
+      for (int v = 0; v < NV; v++) Uh[qidx(g, m, v, c)] = u[v];
+    }
+  }
+}
+
+// ----------------------------------------------------------- CFL step (a2)
+template <typename T>
+__global__ void k_dt(Grid g, Bufs b, const double* Qs) {
+  if (!ctl_active(b)) return;
+  const int N = g.N, D = g.D;
+  double lam = 0.0;
+  unsigned err = 0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.n_interior;
+       idx += (long long)gridDim.x * blockDim.x) {
+    // interior index -> cell
+    long long r = idx;
+    int q[3] = {0, 0, 0};
+    for (int d = 0; d < D; d++) {
+      q[d] = (int)(g.off[d] + r % g.n[d]);
+      r /= g.n[d];
+    }
+    const long long c = cell_at(g, q[0], q[1], q[2]);
+    const bool inb = b.bandidx[c] >= 0;
+    for (int m = 0; m < N; m++) {
+      if (inb ? !(b.alpha[midx(g, m, c)] > 0.0) : b.chi[c] != m) continue;
+      T u[5], w[5];
+      interior_uhat<T>(g, b, Qs, c, m, u);
+      cons_to_prim<T>(g, m, D, u, w);
+      const T cs = sound<T>(g, m, w[0], w[D + 1], &err);
+      T s = T(0);
+      for (int d = 0; d < D; d++) s += (fabs(w[1 + d]) + cs) * (T)g.rh[d];
+      if ((double)s > lam) lam = (double)s;
+    }
+  }
+  // block max, then one atomic
+  __shared__ double red[NTHREADS];
+  red[threadIdx.x] = lam;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomic_max_pos_double(&b.ctl->lam_bits, red[0]);
+  if (err) atomicOr(&b.ctl->err, err);
+}
+__global__ void k_dt_finalize(Grid g, Bufs b) {
+  Ctl* t = b.ctl;
+  if (!t->active) return;
+  const double lam = __longlong_as_double((long long)t->lam_bits);
+  t->lam = lam;
+  double dt = g.cfl / lam;
+  int last = 0;
+  if (t->t + dt >= t->t_end) {
+    dt = t->t_end - t->t;
+    last = 1;
+  }
+  t->dt = dt;
+  t->last = last;
+}
+__global__ void k_step_end(Bufs b) {
+  Ctl* t = b.ctl;
+  if (!t->active) return;
+  t->t = t->last ? t->t_end : t->t + t->dt;
+  t->cnt[C_STEPS] += 1;
+}
+
+// ----------------------------------------- reduced interface interaction (a7)
+template <typename T>
+__global__ void k_interface(Grid g, Bufs b, const double* Qs) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
+  const T* Uh = (const T*)b.Uh;
+  unsigned err = 0;
+  unsigned long long ncut = 0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const long long c = b.band[k];
+    for (int d = 0; d < 3; d++) b.vel0[d * g.ncell + c] = 0.0;
+    b.vf0[c] = 0;
+    if (!(b.gflag[c] & GF_MIXED)) continue;
+    int np = 0;
+    for (int m = 0; m < N; m++)
+      if (present(g, b, c, m)) np++;
+    if (np < 2) continue;
+    b.gflag[c] |= GF_CUT;
+    b.vf0[c] = 1;
+    ncut++;
+    int eta = -1, xi = -1;
+    for (int m = 0; m < N; m++)
+      if (present(g, b, c, m) && (eta < 0 || Qs[qidx(g, m, 0, c)] > Qs[qidx(g, eta, 0, c)])) eta = m;
+    for (int m = 0; m < N; m++)
+      if (m != eta && present(g, b, c, m) && (xi < 0 || Qs[qidx(g, m, 0, c)] > Qs[qidx(g, xi, 0, c)])) xi = m;
+    int L, R;
+    if (Qs[qidx(g, xi, 0, c)] < Qs[qidx(g, eta, 0, c)]) { L = xi; R = eta; }
+    else { L = eta; R = xi; }
+    double n[3];
+    normal_m(g, b.phi, b.chi, c, R, n);
+    T uL[5], uR[5], wL[5], wR[5];
+    for (int v = 0; v < NV; v++) {
+      uL[v] = Uh[qidx(g, L, v, c)];
+      uR[v] = Uh[qidx(g, R, v, c)];
+    }
+    for (int m = 0; m < N; m++)
+      for (int v = 0; v < NV; v++) b.X[qidx(g, m, v, c)] = 0.0;
+    if (isnan(uL[0]) || isnan(uR[0])) {
+      err |= ERR_BAND;
+      continue;
+    }
+    cons_to_prim<T>(g, L, D, uL, wL);
+    cons_to_prim<T>(g, R, D, uR, wR);
+    T unl = T(0), unr = T(0);
+    for (int d = 0; d < D; d++) {
+      unl += wL[1 + d] * (T)n[d];
+      unr += wR[1 + d] * (T)n[d];
+    }
+    T us, ps;
+    hllc_star<T>(wL[0], unl, wL[D + 1], (T)g.gamma[L], (T)g.pinf[L], wR[0], unr, wR[D + 1], (T)g.gamma[R],
+                 (T)g.pinf[R], &us, &ps);
+    const double psd = (double)ps, usd = (double)us;
+    double XR[5] = {0, 0, 0, 0, 0};
+    for (int m = 0; m < N; m++) {
+      if (m == R || !present(g, b, c, m)) continue;
+      double S[3] = {0, 0, 0}, nS = 0.0;
+      for (int d = 0; d < D; d++) S[d] = (b.Ahi[aidx(g, d, m, c)] - b.Alo[aidx(g, d, m, c)]) * g.farea[d];
+      for (int d = 0; d < D; d++) nS += n[d] * S[d];
+      for (int d = 0; d < D; d++) {
+        b.X[qidx(g, m, 1 + d, c)] = psd * S[d];
+        XR[1 + d] -= psd * S[d];
+      }
+      b.X[qidx(g, m, D + 1, c)] = psd * usd * nS;
+      XR[D + 1] -= psd * usd * nS;
+    }
+    for (int v = 1; v < NV; v++) b.X[qidx(g, R, v, c)] = XR[v];
+    for (int d = 0; d < D; d++) b.vel0[d * g.ncell + c] = usd * n[d];
+  }
+  if (ncut) atomicAdd(&b.ctl->cnt[C_CUT], ncut);
+  if (err) atomicOr(&b.ctl->err, err);
+}
+
+// one sweep of the interface-velocity extension into the band
+__global__ void k_extend_vel(Grid g, Bufs b, const double* vin, double* vout, const uint8_t* fin, uint8_t* fout) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, D = g.D;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const long long c = b.band[k];
+    if (b.gflag[c] & GF_CUT) {
+      for (int e = 0; e < 3; e++) vout[e * g.ncell + c] = vin[e * g.ncell + c];
+      fout[c] = 1;
+      continue;
+    }
+    double acc[3] = {0, 0, 0}, acc2[3] = {0, 0, 0};
+    int cnt = 0, cnt2 = 0;
+    for (int d = 0; d < D; d++)
+      for (int s = 0; s < 2; s++) {
+        const long long j = s ? c + g.st[d] : c - g.st[d];
+        if (!interior_c(g, j) || b.bandidx[j] < 0 || !fin[j]) continue;
+        for (int e = 0; e < D; e++) acc2[e] += vin[e * g.ncell + j];
+        cnt2++;
+        if (b.phi[j] < b.phi[c]) {
+          for (int e = 0; e < D; e++) acc[e] += vin[e * g.ncell + j];
+          cnt++;
+        }
+      }
+    uint8_t filled = 0;
+    for (int e = 0; e < 3; e++) vout[e * g.ncell + c] = vin[e * g.ncell + c];
+    if (cnt > 0) {
+      for (int e = 0; e < D; e++) vout[e * g.ncell + c] = acc[e] / (double)cnt;
+      filled = 1;
+    } else if (cnt2 > 0) {
+      for (int e = 0; e < D; e++) vout[e * g.ncell + c] = acc2[e] / (double)cnt2;
+      filled = 1;
+    } else if (fin[c]) {
+      filled = 1;
+    }
+    fout[c] = filled;
+  }
+}
+
+// --------------------------------------- fluxes and the RK stage update (a8)
+// One CTA owns a tile of interior cells. For each material of the tile it
+// stages the stencil state (tile + 3-cell halo) and its primitive quantities
+// in shared memory, evaluates every face flux of the tile once (WENO5 of the
+// Lax-Friedrichs split fluxes, Jiang & Shu), then updates its cells with the
+// aperture-weighted flux differences, the exchange flux and the RK weights.
+template <int D>
+struct Tile;
+template <>
+struct Tile<1> { static constexpr int X = 256, Y = 1, Z = 1; };
+template <>
+struct Tile<2> { static constexpr int X = 32, Y = 8, Z = 1; };
+template <>
+struct Tile<3> { static constexpr int X = 8, Y = 8, Z = 4; };
+
+template <int D, typename T>
+struct FluxSmem {
+  static constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
+  static constexpr int HY = D >= 2 ? 3 : 0, HZ = D >= 3 ? 3 : 0;
+  static constexpr int SX = TX + 6, SY = TY + 2 * HY, SZ = TZ + 2 * HZ;
+  static constexpr int NS = SX * SY * SZ;
+  static constexpr int NV = D + 2;
+  static constexpr int NP = D + 2;  // velocities, p, c
+  static constexpr int NFX = (TX + 1) * TY * TZ;
+  static constexpr int NFY = D >= 2 ? TX * (TY + 1) * TZ : 0;
+  static constexpr int NFZ = D >= 3 ? TX * TY * (TZ + 1) : 0;
+  static constexpr int NF = NFX + NFY + NFZ;
+  static constexpr size_t bytes =
+      sizeof(T) * ((size_t)NS * (NV + NP) + (size_t)NF * NV) + sizeof(double) * NF + (size_t)NS;
+};
+
+template <int D, typename T>
+__device__ inline void face_flux_smem(const T* U, const T* P, int s0, int sstride, int d, int NS, T eps, T* Fh) {
+  // U[v*NS + s], P[e*NS + s] with e: 0..D-1 velocities, D pressure, D+1 sound speed
+  constexpr int NV = D + 2;
+  T a = T(0);
+  for (int q = 0; q < 6; q++) {
+    const int s = s0 + (q - 2) * sstride;
+    const T sp = fabs(P[d * NS + s]) + P[(D + 1) * NS + s];
+    if (sp > a) a = sp;
+  }
+  for (int v = 0; v < NV; v++) {
+    T fp[6], fm[6];
+    for (int q = 0; q < 6; q++) {
+      const int s = s0 + (q - 2) * sstride;
+      const T un = P[d * NS + s], p = P[D * NS + s], uu = U[v * NS + s];
+      T F;
+      if (v == 0) F = U[(1 + d) * NS + s];
+      else if (v == NV - 1) F = un * (uu + p);
+      else F = (v - 1 == d) ? uu * un + p : uu * un;
+      fp[q] = T(0.5) * (F + a * uu);
+      fm[q] = T(0.5) * (F - a * uu);
+    }
+    Fh[v] = weno5<T>(fp[0], fp[1], fp[2], fp[3], fp[4], eps) + weno5<T>(fm[5], fm[4], fm[3], fm[2], fm[1], eps);
+  }
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
+    k_flux_update(Grid g, Bufs b, const double* Qs, const double* Qn, double* Qout, double beta, double omb,
+                  BndBase bb) {
+  using S = FluxSmem<D, T>;
+  constexpr int NV = D + 2, TX = S::TX, TY = S::TY, TZ = S::TZ, SX = S::SX, SY = S::SY, NS = S::NS;
+  if (!ctl_active(b)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* U = (T*)smem_raw;                 // [NV][NS]
+  T* P = U + NV * NS;                  // [D+2][NS]
+  T* F = P + (D + 2) * NS;             // [NV][NF]
+  double* A = (double*)(F + NV * S::NF);  // [NF]
+  uint8_t* bad = (uint8_t*)(A + S::NF);    // [NS]
+  __shared__ unsigned s_union;
+  __shared__ unsigned s_err;
+
+  const int tid = threadIdx.x;
+  const int nbx = (g.n[0] + TX - 1) / TX, nby = D >= 2 ? (g.n[1] + TY - 1) / TY : 1;
+  const int bx = blockIdx.x % nbx, by = (blockIdx.x / nbx) % nby, bz = blockIdx.x / (nbx * nby);
+  const int x0 = g.off[0] + bx * TX, y0 = (D >= 2 ? g.off[1] : 0) + by * TY, z0 = (D >= 3 ? g.off[2] : 0) + bz * TZ;
+  const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
+  const int cx = x0 + tx, cy = y0 + ty, cz = z0 + tz;
+  const bool inside = cx < g.off[0] + g.n[0] && (D < 2 || cy < g.off[1] + g.n[1]) && (D < 3 || cz < g.off[2] + g.n[2]);
+  const long long c = inside ? cell_at(g, cx, cy, cz) : 0;
+  const uint8_t mymask = inside ? b.smask[c] : 0;
+  if (tid == 0) {
+    s_union = 0;
+    s_err = 0;
+  }
+  __syncthreads();
+  if (mymask) atomicOr(&s_union, (unsigned)mymask);
+  // boundary faces of this tile: clear the slots of every material first
+  if (inside) {
+    for (int d = 0; d < D; d++) {
+      const int qd = d == 0 ? cx : (d == 1 ? cy : cz);
+      const int r = qd - g.off[d];
+      for (int side = 0; side < 2; side++) {
+        if (!((side == 0 && r == 0) || (side == 1 && r == g.n[d] - 1))) continue;
+        int qq[3] = {cx, cy, cz};
+        long long lin_id = 0, mul = 1;
+        for (int e = 0; e < D; e++) {
+          if (e == d) continue;
+          lin_id += (long long)(qq[e] - g.off[e]) * mul;
+          mul *= g.n[e];
+        }
+        const long long fid = bb.base[2 * d + side] + lin_id;
+        for (int mv = 0; mv < g.N * NV; mv++) b.bflux[fid * g.N * NV + mv] = 0.0;
+      }
+    }
+  }
+  __syncthreads();
+  const unsigned uni = s_union;
+  const T eps = (T)g.weno_eps;
+  const double dt = b.ctl->dt;
+  unsigned err = 0;
+
+  for (int m = 0; m < g.N; m++) {
+    if (!((uni >> m) & 1u)) continue;
+    // stage the stencil state and its primitive quantities
+    for (int s = tid; s < NS; s += blockDim.x) {
+      const int sx = s % SX, sy = (s / SX) % SY, sz = s / (SX * SY);
+      const int gx = x0 - 3 + sx, gy = y0 - S::HY + sy, gz = z0 - S::HZ + sz;
+      T u[NV];
+      bool ok = gx >= 0 && gx < g.pn[0] && gy >= 0 && gy < g.pn[1] && gz >= 0 && gz < g.pn[2];
+      // only the axis-aligned halo of the tile is read by face stencils
+      int outs = 0;
+      outs += (sx < 3 || sx >= 3 + TX);
+      if (D >= 2) outs += (sy < S::HY || sy >= S::HY + TY);
+      if (D >= 3) outs += (sz < S::HZ || sz >= S::HZ + TZ);
+      ok = ok && outs <= 1;
+      if (ok) {
+        const long long gc = cell_at(g, gx, gy, gz);
+        int qq[3] = {gx, gy, gz};
+        if (interior_q(g, qq)) {
+          interior_uhat<T>(g, b, Qs, gc, m, u);
+        } else {
+          const T* Uh = (const T*)b.Uh;
+          for (int v = 0; v < NV; v++) u[v] = Uh[qidx(g, m, v, gc)];
+        }
+      } else {
+        for (int v = 0; v < NV; v++) u[v] = (T)__longlong_as_double(0x7ff8000000000000LL);
+      }
+      for (int v = 0; v < NV; v++) U[v * NS + s] = u[v];
+      bad[s] = 0;
+      if (!isnan(u[0])) {
+        T w[NV];
+        cons_to_prim<T>(g, m, D, u, w);
+        for (int e = 0; e < D; e++) P[e * NS + s] = w[1 + e];
+        P[D * NS + s] = w[D + 1];
+        T c2 = (T(g.gamma[m]) * (w[D + 1] + T(g.pinf[m]))) / w[0];
+        if (!(w[0] > T(0)) || !(c2 > T(0))) {
+          bad[s] = 1;  // reported only if a used face reads it
+          c2 = c2 > T(0) ? c2 : T(0);
+        }
+        P[(D + 1) * NS + s] = sqrt(c2);
+      }
+    }
+    __syncthreads();
+    // face apertures and fluxes: x faces, then y, then z
+    for (int f = tid; f < S::NF; f += blockDim.x) {
+      int d, fx, fy, fz;
+      if (f < S::NFX) {
+        d = 0; fx = f % (TX + 1); fy = (f / (TX + 1)) % TY; fz = f / ((TX + 1) * TY);
+      } else if (f < S::NFX + S::NFY) {
+        int r = f - S::NFX;
+        d = 1; fx = r % TX; fy = (r / TX) % (TY + 1); fz = r / (TX * (TY + 1));
+      } else {
+        int r = f - S::NFX - S::NFY;
+        d = 2; fx = r % TX; fy = (r / TX) % TY; fz = r / (TX * TY);
+      }
+      // the face is the lower face of tile cell (fx, fy, fz)
+      const int gx = x0 + fx, gy = y0 + fy, gz = z0 + fz;
+      int qR[3] = {gx, gy, gz};
+      // the face exists when its upper cell index lies in [off, off + n] along d
+      // and the other coordinates are interior
+      bool exists = true;
+      for (int e = 0; e < D; e++) {
+        const int lim = g.off[e] + g.n[e] + (e == d ? 1 : 0);
+        if (qR[e] >= lim) exists = false;
+      }
+      double Af = 0.0;
+      T Fh[NV];
+      for (int v = 0; v < NV; v++) Fh[v] = T(0);
+      if (exists) {
+        const long long cR = cell_at(g, gx, gy, gz), cL = cR - g.st[d];
+        Af = face_aperture(g, b, cL, cR, d, m);
+        if (Af > 0.0) {
+          const bool lin = interior_c(g, cL), rin = interior_c(g, cR);
+          if ((lin && !((b.smask[cL] >> m) & 1u)) || (rin && !((b.smask[cR] >> m) & 1u))) err |= ERR_BAND;
+          const int sR = (fx + 3) + SX * ((fy + S::HY) + SY * (fz + S::HZ));
+          const int sstride = d == 0 ? 1 : (d == 1 ? SX : SX * SY);
+          const int sL = sR - sstride;
+          bool avail = true, isbad = false;
+          for (int q = 0; q < 6; q++) {
+            if (isnan(U[sL + (q - 2) * sstride])) avail = false;
+            if (bad[sL + (q - 2) * sstride]) isbad = true;
+          }
+          if (!avail) {
+            err |= ERR_BAND;
+          } else {
+            if (isbad) err |= ERR_NEGATIVE;
+            face_flux_smem<D, T>(U, P, sL, sstride, d, NS, eps, Fh);
+          }
+        }
+        // boundary ledger: net inflow through the domain boundary
+        const int r = qR[d] - g.off[d];
+        if (r == 0 || r == g.n[d]) {
+          // face id: base[d][side] + interior index of the other coordinates
+          long long lin_id = 0, mul = 1;
+          for (int e = 0; e < D; e++) {
+            if (e == d) continue;
+            lin_id += (long long)(qR[e] - g.off[e]) * mul;
+            mul *= g.n[e];
+          }
+          const long long fid = bb.base[2 * d + (r == 0 ? 0 : 1)] + lin_id;
+          const double sgn = r == 0 ? 1.0 : -1.0;
+          for (int v = 0; v < NV; v++) b.bflux[((fid * g.N) + m) * NV + v] = sgn * (Af * (double)Fh[v] * g.farea[d]);
+        }
+      }
+      A[f] = Af;
+      for (int v = 0; v < NV; v++) F[v * S::NF + f] = Fh[v];
+    }
+    __syncthreads();
+    // cell update
+    if (inside && ((mymask >> m) & 1u)) {
+      const bool cut = (b.gflag[c] & GF_CUT) != 0;
+      int flo[3], fhi[3];
+      flo[0] = tx + (TX + 1) * (ty + TY * tz);
+      fhi[0] = flo[0] + 1;
+      if (D >= 2) {
+        flo[1] = S::NFX + tx + TX * (ty + (TY + 1) * tz);
+        fhi[1] = flo[1] + TX;
+      }
+      if (D >= 3) {
+        flo[2] = S::NFX + S::NFY + tx + TX * (ty + TY * tz);
+        fhi[2] = flo[2] + TX * TY;
+      }
+      for (int v = 0; v < NV; v++) {
+        double L = 0.0;
+        for (int d = 0; d < D; d++) {
+          const double fl = (double)F[v * S::NF + flo[d]], fh = (double)F[v * S::NF + fhi[d]];
+          L = L + (A[flo[d]] * fl - A[fhi[d]] * fh) * g.rh[d];
+        }
+        if (cut) L = L + b.X[qidx(g, m, v, c)] * g.rV;
+        const long long qi = qidx(g, m, v, c);
+        const double qn = Qn[qi], qs = Qs[qi];
+        const double qv = beta * qn + omb * (qs + dt * L);
+        if (!isfinite(qv)) err |= ERR_NONFINITE;
+        Qout[qi] = qv;
+      }
+    }
+    __syncthreads();
+  }
+  if (err) atomicOr(&s_err, err);
+  __syncthreads();
+  if (tid == 0 && s_err) atomicOr(&b.ctl->err, s_err);
+}
+
+// sum the boundary-face fluxes of the stage in face order and add them to the ledger
+__global__ void k_ledger(Grid g, Bufs b, int nbnd, double w) {
+  if (!ctl_active(b)) return;
+  const int N = g.N, NV = g.NV;
+  for (int mv = threadIdx.x; mv < N * NV; mv += blockDim.x) {
+    // inflow through low faces, outflow through high faces
+    double s = 0.0;
+    for (int f = 0; f < nbnd; f++) s += b.bflux[(long long)f * N * NV + mv];
+    b.ctl->ledger[mv / NV][mv % NV] += w * b.ctl->dt * s;
+  }
+}
+
+// --------------------------------------------- level-set stage (a9) + R
+__device__ inline double phir_stage(const Bufs& b, long long c, int r) { return phi_m(b.phi, b.chi, c, r); }
+
+__global__ void k_levelset(Grid g, Bufs b, const double* vel, double beta, double omb) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, N = g.N, D = g.D;
+  const double dt = b.ctl->dt, eps = g.weno_eps;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const long long c = b.band[k];
+    const unsigned bits = b.xsS[c];
+    double best = 0.0;
+    int arg = -1;
+    for (int r = 0; r < N; r++) {
+      if (!((bits >> r) & 1u)) continue;
+      double adv = 0.0;
+      for (int d = 0; d < D; d++) {
+        const double vd = vel[d * g.ncell + c];
+        if (vd == 0.0) continue;
+        const long long st = g.st[d];
+        const double rh = g.rh[d];
+        double gd;
+        if (vd > 0.0) {
+          double v1 = (phir_stage(b, c - 2 * st, r) - phir_stage(b, c - 3 * st, r)) * rh;
+          double v2 = (phir_stage(b, c - st, r) - phir_stage(b, c - 2 * st, r)) * rh;
+          double v3 = (phir_stage(b, c, r) - phir_stage(b, c - st, r)) * rh;
+          double v4 = (phir_stage(b, c + st, r) - phir_stage(b, c, r)) * rh;
+          double v5 = (phir_stage(b, c + 2 * st, r) - phir_stage(b, c + st, r)) * rh;
+          gd = weno5<double>(v1, v2, v3, v4, v5, eps);
+        } else {
+          double v1 = (phir_stage(b, c + 3 * st, r) - phir_stage(b, c + 2 * st, r)) * rh;
+          double v2 = (phir_stage(b, c + 2 * st, r) - phir_stage(b, c + st, r)) * rh;
+          double v3 = (phir_stage(b, c + st, r) - phir_stage(b, c, r)) * rh;
+          double v4 = (phir_stage(b, c, r) - phir_stage(b, c - st, r)) * rh;
+          double v5 = (phir_stage(b, c - st, r) - phir_stage(b, c - 2 * st, r)) * rh;
+          gd = weno5<double>(v1, v2, v3, v4, v5, eps);
+        }
+        adv = adv + vd * gd;
+      }
+      const double phn = b.chin[c] == r ? b.phin[c] : -b.phin[c];
+      const double val = beta * phn + omb * (phir_stage(b, c, r) - dt * adv);
+      if (arg < 0 || val > best) {
+        best = val;
+        arg = r;
+      }
+    }
+    double ph = fabs(best);
+    if (ph > g.cap) ph = g.cap;
+    b.phit[k] = ph;
+    b.chit[k] = (uint8_t)arg;
+  }
+}
+// scatter band-indexed (phi, chi) back; flag selects which cells are written
+__global__ void k_scatter_phichi(Grid g, Bufs b) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const long long c = b.band[k];
+    b.phi[c] = b.phit[k];
+    b.chi[c] = b.chit[k];
+  }
+}
+
+// ------------------------------------------------------------ mixing (a11)
+// mixing targets as axis sets: 1D x; 2D x, y, xy; 3D x, y, z, xy, xz, yz, xyz
+__device__ inline int mix_axes(int D, int k) {
+  const int ax2[3] = {1, 2, 3};
+  const int ax3[7] = {1, 2, 4, 3, 5, 6, 7};
+  return D <= 2 ? ax2[k] : ax3[k];
+}
+
+// targets and weights of small cell c of material m; returns the count
+// (0: no target). toff[] are the target cells.
+__device__ inline int mix_targets(const Grid& g, const Bufs& b, long long c, int m, double as, long long* tc,
+                                  double* tw, double* swout) {
+  const int D = g.D;
+  double n[3];
+  normal_m(g, b.phi, b.chi, c, m, n);
+  int sg[3];
+  for (int d = 0; d < 3; d++) sg[d] = n[d] > 0.0 ? 1 : (n[d] < 0.0 ? -1 : 0);
+  const int nk = D == 1 ? 1 : (D == 2 ? 3 : 7);
+  int nt = 0;
+  double sw = 0.0;
+  for (int k = 0; k < nk; k++) {
+    const int ax = mix_axes(D, k);
+    bool ok = true;
+    double wk = 1.0;
+    int na = 0;
+    long long t = c;
+    for (int d = 0; d < D; d++)
+      if ((ax >> d) & 1) {
+        if (sg[d] == 0) ok = false;
+        t += sg[d] * g.st[d];
+        wk = na == 0 ? fabs(n[d]) : wk * fabs(n[d]);
+        na++;
+      }
+    if (na == 1) wk = wk * wk;
+    if (!ok) continue;
+    if (!interior_c(g, t) || b.bandidx[t] < 0 || !((b.smask[t] >> m) & 1u) || !(b.alpha[midx(g, m, t)] > as)) continue;
+    tc[nt] = t;
+    tw[nt] = wk;
+    nt++;
+    sw += wk;
+  }
+  if (!(sw > 0.0)) {
+    int q[3];
+    coords(g, c, q);
+    nt = 0;
+    sw = 0.0;
+    const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
+    for (int dz = -rz; dz <= rz; dz++)
+      for (int dy = -ry; dy <= ry; dy++)
+        for (int dx = -1; dx <= 1; dx++) {
+          if (dx == 0 && dy == 0 && dz == 0) continue;
+          int p[3] = {q[0] + dx, q[1] + dy, q[2] + dz};
+          if (!interior_q(g, p)) continue;
+          const long long t = cell_at(g, p[0], p[1], p[2]);
+          if (b.bandidx[t] < 0 || !((b.smask[t] >> m) & 1u) || !(b.alpha[midx(g, m, t)] > as)) continue;
+          tc[nt] = t;
+          tw[nt] = b.alpha[midx(g, m, t)];
+          sw += tw[nt];
+          nt++;
+        }
+  }
+  *swout = sw;
+  return (sw > 0.0) ? nt : 0;
+}
+
+__device__ inline bool is_small(const Grid& g, const Bufs& b, const double* Qc, long long c, int m, double as) {
+  if (as > 0.0 && as < g.mix_alpha) return true;
+  if (as == 0.0)
+    for (int v = 0; v < g.NV; v++)
+      if (Qc[qidx(g, m, v, c)] != 0.0) return true;
+  return false;
+}
+
+__global__ void k_mix_mark(Grid g, Bufs b, const double* Qc) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, N = g.N;
+  unsigned long long nsmall = 0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const long long c = b.band[k];
+    unsigned bits = 0;
+    for (int m = 0; m < N; m++) {
+      if (!((b.smask[c] >> m) & 1u)) continue;
+      if (is_small(g, b, Qc, c, m, b.alpha[midx(g, m, c)])) {
+        bits |= 1u << m;
+        nsmall++;
+      }
+    }
+    b.small[c] = (uint8_t)bits;
+  }
+  if (nsmall) atomicAdd(&b.ctl->cnt[C_SMALL], nsmall);
+}
+
+// new state of every band cell: own exchanges minus the exchanges its small
+// neighbours send to it (lexicographic neighbour order), then merges
+__global__ void k_mix_compute(Grid g, Bufs b, const double* Qc) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
+  unsigned long long nfail = 0, nmerge = 0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const long long c = b.band[k];
+    int q[3];
+    coords(g, c, q);
+    double* out = b.mixq + (long long)k * N * NV;
+    unsigned mergebits = 0;
+    for (int m = 0; m < N; m++) {
+      for (int v = 0; v < NV; v++) out[m * NV + v] = Qc[qidx(g, m, v, c)];
+      if (!((b.smask[c] >> m) & 1u)) continue;
+      double acc[5] = {0, 0, 0, 0, 0};
+      if ((b.small[c] >> m) & 1u) {
+        const double as = b.alpha[midx(g, m, c)];
+        long long tc[MIX_MAXT];
+        double tw[MIX_MAXT], sw;
+        const int nt = mix_targets(g, b, c, m, as, tc, tw, &sw);
+        if (nt == 0) {
+          nfail++;
+          if (as == 0.0 && m != b.chi[c]) mergebits |= 1u << m;
+        }
+        for (int t = 0; t < nt; t++) {
+          const double beta = tw[t] / sw;
+          const double at = b.alpha[midx(g, m, tc[t])];
+          for (int v = 0; v < NV; v++)
+            acc[v] += beta * (as * Qc[qidx(g, m, v, tc[t])] - at * Qc[qidx(g, m, v, c)]) / (as + at);
+        }
+      }
+      const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
+      for (int dz = -rz; dz <= rz; dz++)
+        for (int dy = -ry; dy <= ry; dy++)
+          for (int dx = -1; dx <= 1; dx++) {
+            if (dx == 0 && dy == 0 && dz == 0) continue;
+            const int sx = q[0] - dx, sy = q[1] - dy, sz = q[2] - dz;
+            if (!in_array(g, sx, sy, sz)) continue;
+            const long long s = cell_at(g, sx, sy, sz);
+            if (!((b.small[s] >> m) & 1u)) continue;
+            const double as = b.alpha[midx(g, m, s)];
+            long long tc[MIX_MAXT];
+            double tw[MIX_MAXT], sw;
+            const int nt = mix_targets(g, b, s, m, as, tc, tw, &sw);
+            for (int t = 0; t < nt; t++) {
+              if (tc[t] != c) continue;
+              const double beta = tw[t] / sw;
+              const double at = b.alpha[midx(g, m, c)];
+              for (int v = 0; v < NV; v++)
+                acc[v] -= beta * (as * Qc[qidx(g, m, v, c)] - at * Qc[qidx(g, m, v, s)]) / (as + at);
+            }
+          }
+      for (int v = 0; v < NV; v++) out[m * NV + v] = Qc[qidx(g, m, v, c)] + acc[v];
+    }
+    for (int m = 0; m < N; m++) {
+      if (!((mergebits >> m) & 1u)) continue;
+      const int pm = b.chi[c];
+      for (int v = 0; v < NV; v++) {
+        out[pm * NV + v] = out[pm * NV + v] + out[m * NV + v];
+        out[m * NV + v] = 0.0;
+      }
+      nmerge++;
+    }
+  }
+  if (nfail) atomicAdd(&b.ctl->cnt[C_MIXFAIL], nfail);
+  if (nmerge) atomicAdd(&b.ctl->cnt[C_MERGE], nmerge);
+}
+__global__ void k_mix_scatter(Grid g, Bufs b, double* Qc) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, N = g.N, NV = g.NV;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const long long c = b.band[k];
+    const double* in = b.mixq + (long long)k * N * NV;
+    for (int m = 0; m < N; m++)
+      for (int v = 0; v < NV; v++) Qc[qidx(g, m, v, c)] = in[m * NV + v];
+  }
+}
+
+// ------------------------------------------------- scale separation (a12)
+__global__ void k_scale_sep(Grid g, Bufs b) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, N = g.N, D = g.D;
+  const double eps = g.eps_ss;
+  unsigned long long nodd = 0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const long long c = b.band[k];
+    b.phit[k] = b.phi[c];
+    b.chit[k] = b.chi[c];
+    if (!(b.gflag[c] & GF_MIXED)) continue;
+    int np = 0;
+    for (int m = 0; m < N; m++)
+      if (present(g, b, c, m)) np++;
+    if (np < 2) continue;
+    const int chi1 = b.chi[c];
+    int q[3];
+    coords(g, c, q);
+    const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
+    bool near_minus = false;
+    for (int dz = -rz; dz <= rz && !near_minus; dz++)
+      for (int dy = -ry; dy <= ry && !near_minus; dy++)
+        for (int dx = -1; dx <= 1 && !near_minus; dx++) {
+          double mn, mx;
+          vertex_minmax(g, b.phi, b.chi, cell_at(g, q[0] + dx, q[1] + dy, q[2] + dz), chi1, &mn, &mx);
+          if (mn - eps <= 0.0 && mx - eps >= 0.0) near_minus = true;
+        }
+    if (near_minus) continue;
+    nodd++;
+    int chs = -1;
+    for (int m = 0; m < N; m++) {
+      if (m == chi1 || !((b.xsS[c] >> m) & 1u)) continue;
+      if (chs < 0 || b.alpha[midx(g, m, c)] > b.alpha[midx(g, chs, c)]) chs = m;
+    }
+    double dmin = 0.0;
+    bool found = false;
+    const int sz = D >= 3 ? 3 : 0, sy = D >= 2 ? 3 : 0;
+    for (int dz = -sz; dz <= sz; dz++)
+      for (int dy = -sy; dy <= sy; dy++)
+        for (int dx = -3; dx <= 3; dx++) {
+          int p[3] = {q[0] + dx, q[1] + dy, q[2] + dz};
+          if (!interior_q(g, p)) continue;
+          const long long i0 = cell_at(g, p[0], p[1], p[2]);
+          double mn, mx;
+          vertex_minmax(g, b.phi, b.chi, i0, chs, &mn, &mx);
+          if (!(mn + eps <= 0.0 && mx + eps >= 0.0)) continue;
+          double n[3];
+          normal_m(g, b.phi, b.chi, i0, chs, n);
+          const double ps = phi_m(b.phi, b.chi, i0, chs);
+          double dd = 0.0;
+          for (int d = 0; d < D; d++) {
+            const double xi0 = g.lo[d] + ((double)(p[d] - g.off[d]) + 0.5) * g.h[d];
+            const double xc = g.lo[d] + ((double)(q[d] - g.off[d]) + 0.5) * g.h[d];
+            const double pd = xi0 - (ps + eps) * n[d];
+            const double df = xc - pd;
+            dd += df * df;
+          }
+          dd = sqrt(dd);
+          if (!found || dd < dmin) {
+            dmin = dd;
+            found = true;
+          }
+        }
+    if (found) b.phit[k] = fabs(dmin - eps);
+    b.chit[k] = (uint8_t)chs;
+  }
+  if (nodd) atomicAdd(&b.ctl->cnt[C_ODDBALL], nodd);
+}
+
+// --------------------------------------------- band distance maintenance
+__global__ void k_reinit(Grid g, Bufs b) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, D = g.D;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const long long c = b.band[k];
+    b.phit[k] = b.phi[c];
+    b.chit[k] = b.chi[c];
+    int q[3];
+    coords(g, c, q);
+    unsigned bits = 0;
+    const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
+    for (int dz = -rz; dz <= rz; dz++)
+      for (int dy = -ry; dy <= ry; dy++)
+        for (int dx = -1; dx <= 1; dx++)
+          if (in_array(g, q[0] + dx, q[1] + dy, q[2] + dz))
+            bits |= 1u << b.chi[cell_at(g, q[0] + dx, q[1] + dy, q[2] + dz)];
+    if (popcount8(bits) >= 2) continue;
+    double a[3] = {0, 0, 0}, hh[3] = {1, 1, 1}, w[3] = {1, 1, 1};
+    for (int d = 0; d < D; d++) {
+      const long long jm = c - g.st[d], jp = c + g.st[d];
+      const double vm = interior_c(g, jm) ? b.phi[jm] : b.phi[c];
+      const double vp = interior_c(g, jp) ? b.phi[jp] : b.phi[c];
+      a[d] = fmin(vm, vp);
+      hh[d] = g.h[d];
+      w[d] = g.ih2[d];
+    }
+    for (int i = 1; i < D; i++)
+      for (int j = i; j > 0 && a[j] < a[j - 1]; j--) {
+        double t = a[j]; a[j] = a[j - 1]; a[j - 1] = t;
+        t = hh[j]; hh[j] = hh[j - 1]; hh[j - 1] = t;
+        t = w[j]; w[j] = w[j - 1]; w[j - 1] = t;
+      }
+    double ph = a[0] + hh[0];
+    for (int kk = 1; kk < D; kk++) {
+      if (ph <= a[kk]) break;
+      double A = 0.0, B = 0.0, C = -1.0;
+      for (int j = 0; j <= kk; j++) {
+        A += w[j];
+        B += w[j] * a[j];
+        C += w[j] * a[j] * a[j];
+      }
+      const double disc = B * B - A * C;
+      ph = (B + sqrt(disc > 0.0 ? disc : 0.0)) / A;
+    }
+    if (ph > g.cap) ph = g.cap;
+    b.phit[k] = ph;
+  }
+}
+
+// ------------------------------------------------------- totals and init
+// one block per (m, v): fixed-order block reduction over interior cells
+__global__ void k_totals(Grid g, const double* Q, double* out) {
+  const int mv = blockIdx.x;
+  const int m = mv / g.NV, v = mv % g.NV;
+  double s = 0.0;
+  for (long long idx = threadIdx.x; idx < g.n_interior; idx += blockDim.x) {
+    long long r = idx;
+    int q[3] = {0, 0, 0};
+    for (int d = 0; d < g.D; d++) {
+      q[d] = (int)(g.off[d] + r % g.n[d]);
+      r /= g.n[d];
+    }
+    s += Q[qidx(g, m, v, cell_at(g, q[0], q[1], q[2]))];
+  }
+  __shared__ double red[NTHREADS];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[mv] = red[0] * g.V;
+}
+
+}  // namespace
+}  // namespace msf

@@ -1,0 +1,44 @@
+// msf_types.cuh -- device buffers of one instance and launch constants,
+// shared by the kernels and the host runtime.
+#pragma once
+
+#include "msf_device.cuh"
+
+namespace msf {
+
+struct Bufs {
+  double* Q[3];             // Q^n, Q^(1), Q^(2): [N][NV][ncell]
+  double *phi, *phin;       // current and step-start distance
+  uint8_t *chi, *chin;      // current and step-start indicator
+  uint8_t* xs;              // 3^d material bits of chi (all cells)
+  uint8_t* mtmp;            // dilation scratch
+  uint8_t* smask;           // step mask: materials carried by an interior cell this step
+  uint8_t* xsS;             // 3^d material bits of the stage indicator (band cells)
+  uint8_t* gflag;           // GF_MIXED | GF_CUT (band cells; 0 elsewhere)
+  uint8_t* small;           // mixing sources: bit m = small cell of material m
+  double* alpha;            // [N][ncell]
+  double *Alo, *Ahi;        // [D][N][ncell] face apertures (mixed cells)
+  void *W0, *W1;            // T [N][NV][ncell] primitive states, ping-pong
+  uint8_t *f0, *f1, *isreal;  // [N][ncell]
+  void* Uh;                 // T [N][NV][ncell] stencil state (band and halo cells)
+  double* X;                // [N][NV][ncell] exchange flux (cut cells)
+  double *vel0, *vel1;      // [3][ncell] interface velocity, ping-pong
+  uint8_t *vf0, *vf1;
+  int* band;                // narrow-band cell list
+  int* bandidx;             // cell -> band index or -1
+  double* phit;             // [nbandmax] scratch
+  uint8_t* chit;            // [nbandmax] scratch
+  double* mixq;             // [nbandmax][N][NV] mixed state scratch
+  double* bflux;            // [nbnd][N][NV] boundary-face fluxes of the stage
+  Ctl* ctl;
+};
+
+constexpr int NTHREADS = 256;
+
+// first boundary-face id of each (axis, side): faces are numbered per side in
+// interior order of the other coordinates
+struct BndBase {
+  long long base[6];
+};
+
+}  // namespace msf

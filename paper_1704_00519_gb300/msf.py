@@ -1,0 +1,227 @@
+"""Python binding of the msf C ABI (include/msf.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library libmsf.so built in this
+package directory; there is no CPU fallback. Importing this module without
+the built library raises ImportError.
+
+The functions below carry the C names; ``Solver`` wraps one context. Arrays
+may be numpy arrays (host) or torch CUDA tensors (device, passed by pointer);
+torch is used only for device memory and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmsf.so")
+
+MSF_OK, MSF_EINVAL, MSF_ENOMEM, MSF_ECUDA, MSF_ENONFINITE, MSF_ENEGATIVE, MSF_EBAND, MSF_ETIMEOUT, MSF_ESTATE, \
+    MSF_EUNSUPPORTED = range(10)
+STATUS_NAMES = ["MSF_OK", "MSF_EINVAL", "MSF_ENOMEM", "MSF_ECUDA", "MSF_ENONFINITE", "MSF_ENEGATIVE", "MSF_EBAND",
+                "MSF_ETIMEOUT", "MSF_ESTATE", "MSF_EUNSUPPORTED"]
+MSF_HOST, MSF_DEVICE = 0, 1
+MSF_FP64, MSF_FP32_BULK = 0, 1
+MAXMAT = 8
+NSTATS = 8
+COUNTERS = ["cut", "multi", "corrected", "small", "mixfail", "merge", "oddball", "steps"]
+
+
+class msf_grid(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("bc", (C.c_int32 * 2) * 3), ("inflow_prim", ((C.c_double * 5) * 2) * 3),
+                ("inflow_mat", (C.c_int32 * 2) * 3)]
+
+
+class msf_eos(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("pinf", C.c_double)]
+
+
+class msf_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("cfl", C.c_double), ("weno_eps", C.c_double), ("mix_alpha", C.c_double),
+                ("ext_sweeps", C.c_int32), ("vel_sweeps", C.c_int32), ("reinit_iters", C.c_int32),
+                ("scale_sep", C.c_int32), ("reinit", C.c_int32), ("scale_eps_h", C.c_double),
+                ("phi_cap_h", C.c_double), ("use_graph", C.c_int32), ("stream", C.c_void_p)]
+
+
+class MsfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmsf.so is not built ({LIB_PATH}); run paper_1704_00519_gb300/build.py "
+                          "(or __graft_entry__.build())")
+    lib = C.CDLL(LIB_PATH)
+    P, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32)
+    sig = {
+        "msf_default_options": ([C.c_int32, C.POINTER(msf_options)], C.c_int),
+        "msf_create": ([C.POINTER(msf_grid), C.c_int32, C.c_int32, C.POINTER(msf_eos), C.POINTER(msf_options),
+                        C.POINTER(C.c_void_p)], C.c_int),
+        "msf_destroy": ([P], C.c_int),
+        "msf_set_levelset": ([P, C.c_int32, P, P, P, C.c_int32], C.c_int),
+        "msf_step": ([P, C.c_int32, C.c_double, C.c_int32], C.c_int),
+        "msf_totals": ([P, C.c_int32, dp, dp], C.c_int),
+        "msf_adjoint_step": ([P, P, P, dp], C.c_int),
+        "msf_get_state": ([P, C.c_int32, P, P, P, P, dp, C.c_int32], C.c_int),
+        "msf_set_state": ([P, C.c_int32, P, P, P, C.c_double, C.c_int32], C.c_int),
+        "msf_stats": ([P, C.POINTER(C.c_int64)], C.c_int),
+        "msf_last_dt": ([P, C.c_int32, dp], C.c_int),
+        "msf_debug_field": ([P, C.c_int32, C.c_int32, dp], C.c_int),
+        "msf_last_error": ([P], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+# the C entry points, under their own names
+msf_default_options = _lib.msf_default_options
+msf_create = _lib.msf_create
+msf_destroy = _lib.msf_destroy
+msf_set_levelset = _lib.msf_set_levelset
+msf_step = _lib.msf_step
+msf_totals = _lib.msf_totals
+msf_adjoint_step = _lib.msf_adjoint_step
+msf_get_state = _lib.msf_get_state
+msf_set_state = _lib.msf_set_state
+msf_stats = _lib.msf_stats
+msf_last_dt = _lib.msf_last_dt
+msf_debug_field = _lib.msf_debug_field
+msf_last_error = _lib.msf_last_error
+
+
+def lib():
+    return _lib
+
+
+def _check(status, ctx):
+    if status != MSF_OK:
+        raise MsfError(status, msf_last_error(ctx).decode())
+
+
+def make_grid(p: dict) -> msf_grid:
+    g = msf_grid()
+    g.dim = int(p["dim"])
+    for d in range(3):
+        g.n[d] = int(p["n"][d])
+        g.lo[d] = float(p["lo"][d])
+        g.hi[d] = float(p["hi"][d])
+        for s in range(2):
+            g.bc[d][s] = int(p["bc"][d][s])
+            g.inflow_mat[d][s] = int(p["inflow_mat"][d][s])
+            for v in range(5):
+                g.inflow_prim[d][s][v] = float(p["inflow_prim"][d][s][v])
+    return g
+
+
+def make_options(p: dict, precision=MSF_FP64, stream=None, use_graph=1) -> msf_options:
+    o = msf_options()
+    _check(msf_default_options(int(p["dim"]), C.byref(o)), None)
+    o.precision = int(precision)
+    for k in ("cfl", "weno_eps", "mix_alpha", "scale_eps_h", "phi_cap_h"):
+        setattr(o, k, float(p[k]))
+    for k in ("ext_sweeps", "vel_sweeps", "reinit_iters", "scale_sep", "reinit"):
+        setattr(o, k, int(p[k]))
+    o.use_graph = int(use_graph)
+    o.stream = stream
+    return o
+
+
+def _ptr(a, kind):
+    """(pointer, mem) of a numpy array (host) or torch tensor (device or host)."""
+    if hasattr(a, "data_ptr"):
+        if a.dtype.itemsize != (8 if kind == "f8" else 4) or not a.is_contiguous():
+            raise ValueError("tensor must be contiguous with the right dtype")
+        return C.c_void_p(a.data_ptr()), (MSF_DEVICE if a.is_cuda else MSF_HOST), a
+    arr = np.ascontiguousarray(a, dtype=np.float64 if kind == "f8" else np.int32)
+    return C.c_void_p(arr.ctypes.data), MSF_HOST, arr
+
+
+class Solver:
+    """One context with one instance, built from a case (see cases.Case)."""
+
+    def __init__(self, case, precision=MSF_FP64, stream=None, use_graph=1, **opts):
+        self.case = case
+        self.p = case.params(**opts)
+        self.N, self.NV, self.cells = case.nmat, case.nv, case.cells
+        self._grid = make_grid(self.p)
+        eos = (msf_eos * self.N)(*[msf_eos(self.p["gamma"][m], self.p["pinf"][m]) for m in range(self.N)])
+        self._eos = eos
+        self._opt = make_options(self.p, precision, stream, use_graph)
+        h = C.c_void_p()
+        st = msf_create(C.byref(self._grid), 1, self.N, eos, C.byref(self._opt), C.byref(h))
+        if st != MSF_OK:
+            raise MsfError(st, msf_last_error(None).decode())
+        self.h = h
+        self.set_levelset(case.phi, case.chi, case.prim)
+
+    def close(self):
+        if getattr(self, "h", None):
+            msf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_levelset(self, phi, chi, prim):
+        a, ma, ka = _ptr(phi, "f8")
+        b, mb, kb = _ptr(chi, "i4")
+        c, mc, kc = _ptr(prim, "f8")
+        if not (ma == mb == mc):
+            raise ValueError("phi, chi, prim must all be host or all device arrays")
+        _check(msf_set_levelset(self.h, 0, a, b, c, ma), self.h)
+
+    def step(self, n_steps, t_end=float("inf"), sync=True):
+        _check(msf_step(self.h, int(n_steps), float(t_end), 1 if sync else 0), self.h)
+
+    def state(self):
+        Q = np.zeros((self.N, self.NV, self.cells))
+        alpha = np.zeros((self.N, self.cells))
+        phi = np.zeros(self.cells)
+        chi = np.zeros(self.cells, np.int32)
+        t = C.c_double()
+        _check(msf_get_state(self.h, 0, C.c_void_p(Q.ctypes.data), C.c_void_p(alpha.ctypes.data),
+                             C.c_void_p(phi.ctypes.data), C.c_void_p(chi.ctypes.data), C.byref(t), MSF_HOST), self.h)
+        return dict(Q=Q, alpha=alpha, phi=phi, chi=chi, t=t.value)
+
+    def get_state_device(self, Q):
+        """Copy Q into a caller-owned device tensor (torch, float64, [N, NV, cells])."""
+        _check(msf_get_state(self.h, 0, C.c_void_p(Q.data_ptr()), None, None, None, None, MSF_DEVICE), self.h)
+
+    def set_state(self, Q, phi, chi, t):
+        a, ma, ka = _ptr(Q, "f8")
+        b, mb, kb = _ptr(phi, "f8")
+        c, mc, kc = _ptr(chi, "i4")
+        _check(msf_set_state(self.h, 0, a, b, c, float(t), ma), self.h)
+
+    def totals(self):
+        tot = np.zeros((self.N, self.NV))
+        led = np.zeros((self.N, self.NV))
+        _check(msf_totals(self.h, 0, tot.ctypes.data_as(C.POINTER(C.c_double)),
+                          led.ctypes.data_as(C.POINTER(C.c_double))), self.h)
+        return tot, led
+
+    def counters(self):
+        c = (C.c_int64 * NSTATS)()
+        _check(msf_stats(self.h, c), self.h)
+        return dict(zip(COUNTERS, list(c)))
+
+    def last_dt(self):
+        dt = C.c_double()
+        _check(msf_last_dt(self.h, 0, C.byref(dt)), self.h)
+        return dt.value
+
+    def debug(self, which):
+        sizes = {0: self.N, 1: self.N * self.NV, 2: self.N * self.NV, 3: 3, 4: 1, 5: 1}
+        out = np.zeros(sizes[which] * self.cells)
+        _check(msf_debug_field(self.h, 0, int(which), out.ctypes.data_as(C.POINTER(C.c_double))), self.h)
+        return out

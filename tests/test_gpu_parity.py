@@ -1,0 +1,191 @@
+"""GPU path (through the C ABI) against the CPU oracle on the same seeded
+inputs, element by element.
+
+FP64 mode: the strict build (-fmad=false on the device, -ffp-contract=off in
+the oracle) evaluates every expression in the same order, so the states are
+expected to agree to the last bit; the gate is the benchmark spec's tolerance, L1
+relative density error <= 1e-10, plus max |dQ| <= 1e-12 * max|Q|.
+FP32-bulk mode: L1 relative density error <= 2e-5.
+"""
+import numpy as np
+import pytest
+
+import paper_1704_00519_gb300.cases as cs
+from oracle import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+FP64_L1 = 1e-10
+FP32_L1 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def msf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_00519_gb300 import build
+    build.build()
+    import paper_1704_00519_gb300.msf as m
+    return m
+
+
+def l1_rho(Qa, Qb):
+    ra, rb = Qa[:, 0].sum(0), Qb[:, 0].sum(0)
+    return float(np.abs(ra - rb).sum() / np.abs(rb).sum())
+
+
+def run_pair(msf, case, steps, t_end=None, precision=0, **opts):
+    t_end = case.t_end if t_end is None else t_end
+    o = orc.Oracle(case, **opts)
+    eo = o.step(steps, t_end)
+    s = msf.Solver(case, precision=precision, **opts)
+    s.step(steps, t_end)
+    return o, s, eo
+
+
+def compare(o, s, tol_l1, exact=False):
+    a, b = s.state(), o.state()
+    assert a["t"] == pytest.approx(b["t"], rel=1e-14, abs=1e-15)
+    l1 = l1_rho(a["Q"], b["Q"])
+    scale = np.abs(b["Q"]).max()
+    dmax = np.abs(a["Q"] - b["Q"]).max()
+    assert np.all(np.isfinite(a["Q"]))
+    assert l1 <= tol_l1, (l1, dmax)
+    if exact:
+        assert dmax <= 1e-12 * scale, dmax
+        assert np.array_equal(a["chi"], b["chi"])
+        assert np.abs(a["phi"] - b["phi"]).max() <= 1e-12
+        assert np.abs(a["alpha"] - b["alpha"]).max() <= 1e-12
+        ca, cb = s.counters(), o.counters()
+        assert ca == cb, (ca, cb)
+    return l1, dmax
+
+
+def test_shock_tube_full_run_fp64(msf):
+    case = cs.shock_tube_3(400)
+    o, s, eo = run_pair(msf, case, 100000)
+    assert eo == 0
+    l1, dmax = compare(o, s, FP64_L1, exact=True)
+    assert s.state()["t"] == 0.2
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_1d_fp64(msf, seed):
+    rng = np.random.default_rng(seed)
+    case = cs.riemann_1d(rng, ncell=int(rng.integers(150, 700)))
+    o, s, eo = run_pair(msf, case, 40)
+    assert eo == 0
+    compare(o, s, FP64_L1, exact=True)
+
+
+@pytest.mark.parametrize("n,nmat,seed", [((37, 29), 3, 1), ((75, 37), 4, 2), ((33, 9), 2, 3), ((64, 16), 3, 4)])
+def test_random_2d_fp64(msf, n, nmat, seed):
+    case = cs.random_case(2, n, nmat, seed)
+    o, s, eo = run_pair(msf, case, 15)
+    assert eo == 0
+    compare(o, s, FP64_L1, exact=True)
+
+
+def test_triple_point_fp64(msf):
+    case = cs.triple_point(112, 48)
+    o, s, eo = run_pair(msf, case, 60)
+    assert eo == 0
+    compare(o, s, FP64_L1, exact=True)
+
+
+def test_shock_bubbles_inflow_fp64(msf):
+    case = cs.shock_bubbles(96, 32)
+    o, s, eo = run_pair(msf, case, 30)
+    assert eo == 0
+    compare(o, s, FP64_L1, exact=True)
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_random_3d_fp64(msf, seed):
+    case = cs.random_case(3, (18, 13, 11), 2 + seed % 2, seed)
+    o, s, eo = run_pair(msf, case, 4)
+    assert eo == 0
+    compare(o, s, FP64_L1, exact=True)
+
+
+def test_tiny_and_ragged_grids_fp64(msf):
+    for case in (cs.random_case(1, (7,), 2, 11), cs.random_case(2, (5, 3), 2, 12), cs.random_case(2, (1, 9), 2, 13)):
+        o, s, eo = run_pair(msf, case, 5)
+        compare(o, s, FP64_L1, exact=True)
+
+
+def test_scale_separation_filament_fp64(msf):
+    case = cs.scale_sep_demo("filament", n=10)
+    o, s, eo = run_pair(msf, case, 2, t_end=10.0)
+    compare(o, s, FP64_L1, exact=True)
+    assert not np.any(s.state()["chi"] == 2)
+
+
+@pytest.mark.parametrize("maker,steps", [(lambda: cs.triple_point(112, 48), 60), (lambda: cs.shock_bubbles(96, 32), 30),
+                                         (lambda: cs.shock_tube_3(400), 200)])
+def test_fp32_bulk_form(msf, maker, steps):
+    case = maker()
+    o, s, eo = run_pair(msf, case, steps, precision=msf.MSF_FP32_BULK)
+    l1, dmax = compare(o, s, FP32_L1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gpu_conservation(msf, precision):
+    case = cs.triple_point(112, 48)
+    s = msf.Solver(case, precision=precision)
+    tot0, _ = s.totals()
+    s.step(100, case.t_end)
+    tot, led = s.totals()
+    scale = max(np.abs(tot0).sum(), np.abs(tot).sum())
+    d = tot - tot0 - led
+    if s.counters()["merge"] == 0:
+        assert np.abs(d[:, 0]).max() / scale < 1e-12
+    assert np.abs(d.sum(0)).max() / scale < 1e-12
+
+
+def test_full_size_triple_point(msf):
+    """896 x 384 (the benchmark workload): three steps element by element
+    against the oracle, then 200 steps that must stay finite and conservative."""
+    case = cs.triple_point(896, 384)
+    o, s, eo = run_pair(msf, case, 3)
+    compare(o, s, FP64_L1, exact=True)
+    s2 = msf.Solver(case, precision=msf.MSF_FP32_BULK)
+    tot0, _ = s2.totals()
+    s2.step(200, case.t_end)
+    tot, led = s2.totals()
+    st = s2.state()
+    assert np.all(np.isfinite(st["Q"]))
+    scale = max(np.abs(tot0).sum(), np.abs(tot).sum())
+    assert np.abs((tot - tot0 - led).sum(0)).max() / scale < 1e-12
+
+
+def test_host_validation_rejects_bad_levelset(msf):
+    case = cs.shock_tube_3(50)
+    s = msf.Solver(case)
+    bad = case.phi.copy()
+    bad[3] = -1.0
+    with pytest.raises(msf.MsfError):
+        s.set_levelset(bad, case.chi, case.prim)
+    chi = case.chi.copy()
+    chi[0] = 7
+    with pytest.raises(msf.MsfError):
+        s.set_levelset(case.phi, chi, case.prim)
+
+
+def test_device_inputs_and_set_state_roundtrip(msf):
+    import torch
+    case = cs.triple_point(56, 24)
+    s = msf.Solver(case)
+    dev = torch.device("cuda")
+    s.set_levelset(torch.tensor(case.phi.ravel(), device=dev), torch.tensor(case.chi.ravel(), device=dev),
+                   torch.tensor(case.prim, device=dev))
+    s.step(5)
+    st = s.state()
+    s2 = msf.Solver(case)
+    s2.set_state(st["Q"], st["phi"], st["chi"], st["t"])
+    s.step(5)
+    s2.step(5)
+    a, b = s.state(), s2.state()
+    assert np.array_equal(a["Q"], b["Q"])
+    assert a["t"] == b["t"]
