@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Throughput of the cut-cell multi-material update on GB300.
+
+Workload: the 2D triple-point problem, 896 x 384 cells, three materials
+(configs of the paper's Sec. 3.3 shape, synthetic initial data). One step is
+one full TVD-RK3 step (three stages of every step of the method) over the
+whole grid; the metric is cell-stage updates per second (cells x 3 per step).
+
+The headline value is the FP32-bulk form; the plain FP64 path runs beside it
+on the same workload and its throughput, and the L1 density difference of the
+two after the same number of steps, are reported in the same JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl msf|reference]
+
+--impl reference times the CPU oracle (the plain FP64 C implementation under
+oracle/) on the host cores for the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="triple_point_896x384", nx=896, ny=384)
+METRIC = "cell-stage updates/s: FP32/batched/adjoint vs plain FP64 on GB300 at stated L1"
+UNIT = "cell-stage updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="msf", choices=["msf", "reference"])
+    ap.add_argument("--only", default=None, choices=["fp32", "fp64"],
+                    help="profiling aid: run warm-up and timed steps of one precision only, print nothing else")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_case():
+    import paper_1704_00519_gb300.cases as cs
+    return cs.triple_point(WORKLOAD["nx"], WORKLOAD["ny"])
+
+
+# ------------------------------------------------------------ reference arm
+def oracle_rate(case, steps, warmup):
+    """Time the CPU oracle as it stands (single thread) on full steps of the
+    workload; returns (cell-stages/s, seconds, steps timed)."""
+    from oracle.oracle import Oracle
+    o = Oracle(case)
+    if warmup:
+        o.step(warmup, case.t_end)
+    t0 = time.perf_counter()
+    o.step(steps, case.t_end)
+    dt = time.perf_counter() - t0
+    return case.cells * 3 * steps / dt, dt, steps
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as orc
+    orc.build()
+    case = make_case()
+    # one full oracle step of the workload takes ~2 s: bound the run to a few minutes
+    steps = max(1, min(args.steps, 30))
+    warm = max(0, min(args.warmup, 3))
+    val, secs, steps = oracle_rate(case, steps, warm)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+        "n_gpus": 0, "steps": steps, "warmup": warm, "ms_per_step": 1e3 * secs / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "cells": case.cells, "materials": case.nmat},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} full TVD-RK3 steps of the {WORKLOAD['name']} workload after {warm} warm-up steps"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def flux_kernel_hash():
+    h = hashlib.sha256()
+    for f in ("msf_kernels.cuh", "msf_device.cuh", "msf_types.cuh", "msf_prec.inc"):
+        with open(os.path.join(ROOT, "paper_1704_00519_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(precision):
+    """DRAM bytes per flux-update launch from the committed ncu summary, when
+    it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "flux_update_triple_point_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_hash") != flux_kernel_hash():
+        return None
+    return d.get(precision, {}).get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def pairs_per_cell(s):
+    """(cell, material) pairs the flux update processes: popcount of the step mask."""
+    vals, counts = np.unique(s.debug(5).astype(np.int64), return_counts=True)
+    return int(sum(bin(int(v)).count("1") * int(c) for v, c in zip(vals, counts)))
+
+
+def flux_bytes_per_step(case, npairs):
+    """Algorithmic DRAM bytes of the three flux-update launches of one step:
+    per (cell, material) pair the stage state is read and the new state written
+    (FP64, nv values each), stages 2 and 3 also read Q^n; per cell one indicator
+    byte and one mask byte."""
+    nv = case.nv
+    per_pair = nv * 8 * (2 + 3 + 3)
+    return npairs * per_pair + case.cells * 2 * 3
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        from paper_1704_00519_gb300 import build
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_1704_00519_gb300.msf as msf
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    case = make_case()
+    cells, stages = case.cells, 3
+    K, W = args.steps, max(3, args.warmup)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def timed(precision):
+        s = msf.Solver(case, precision=precision, stream=sptr, profile=1)
+        s.step(W, case.t_end)
+        step_ms, flux_ms = [], []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        clocks = ClockSampler(local)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        for k in range(K):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            s.step(1, case.t_end, sync=False)
+            ev[k][1].record(stream)
+            flux_ms.append(s.flux_ms())   # synchronises after the step
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        return s, step_ms, flux_ms, clk
+
+    if args.only:
+        s, ms, fl, _ = timed(msf.MSF_FP32_BULK if args.only == "fp32" else msf.MSF_FP64)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "ms_per_step": sum(ms) / K, "flux_ms_per_step": sum(map(sum, fl)) / K}))
+        return 0
+    s32, ms32, fl32, clk = timed(msf.MSF_FP32_BULK)
+    s64, ms64, fl64, _ = timed(msf.MSF_FP64)
+    total32 = sum(ms32) / 1e3
+    total64 = sum(ms64) / 1e3
+    if world > 1:
+        t = torch.tensor([total32, total64], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total32, total64 = float(t[0]), float(t[1])
+    value = world * cells * stages * K / total32
+    value64 = world * cells * stages * K / total64
+    a, b = s32.state(), s64.state()
+    ra, rb = a["Q"][:, 0].sum(0), b["Q"][:, 0].sum(0)
+    l1 = float(np.abs(ra - rb).sum() / np.abs(rb).sum())
+
+    # roofline of the dominant kernel (flux update), FP32-bulk form
+    npairs = pairs_per_cell(s32)
+    bytes_step = flux_bytes_per_step(case, npairs)
+    flux_s = sum(sum(x) for x in fl32) / 1e3 / K
+    achieved = bytes_step / flux_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = profiled_traffic("fp32_bulk")
+
+    # end to end through the public API with host buffers: initial data in,
+    # K steps, final state out (wall clock)
+    torch.cuda.synchronize()
+    phi = np.ascontiguousarray(case.phi.ravel(), np.float64)
+    chi = np.ascontiguousarray(case.chi.ravel(), np.int32)
+    prim = np.ascontiguousarray(case.prim, np.float64)
+    se = msf.Solver(case, precision=msf.MSF_FP32_BULK, stream=sptr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    se.set_levelset(phi, chi, prim)
+    se.step(K, case.t_end)
+    st = se.state()
+    t1 = time.perf_counter()
+    e2e_val = world * cells * stages * K / (t1 - t0)
+    h2d = phi.nbytes + chi.nbytes + prim.nbytes
+    d2h = st["Q"].nbytes + st["alpha"].nbytes + st["phi"].nbytes + st["chi"].nbytes
+
+    launches = s32.launches_per_step() * K
+    if rank != 0:
+        return 0
+
+    # CPU oracle on a bounded sample of the same workload
+    from oracle import oracle as orc
+    orc.build()
+    cpu_val, cpu_secs, cpu_steps = oracle_rate(case, 2, 0)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": 1e3 * total32 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "cells": cells, "materials": case.nmat,
+                   "precision": "fp32_bulk (FP32 fluxes, FP64 storage/geometry/correction/totals)",
+                   "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+                   "parallelism": f"replicas{world}"},
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * total64 / K,
+                 "flux_ms_per_step": sum(sum(x) for x in fl64) / K},
+        "fp32_over_fp64": value / value64,
+        "l1_rho_fp32_vs_fp64": l1,
+        "roofline": {"kernel": "k_flux_update<2,float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                     "algorithmic_bytes_per_step": bytes_step, "flux_ms_per_step": 1e3 * flux_s,
+                     "flux_share_of_step": flux_s / (total32 / K)},
+        "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{cpu_steps} full TVD-RK3 steps of {WORKLOAD['name']} (single thread)"},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+                "how": "wall clock: msf_set_levelset from host arrays, K steps, msf_get_state to host"},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -86,6 +86,8 @@ typedef struct {
  *                0.5 (1D), 0.75 (2D), 0.9 (3D) (Sec. 2.3.3)
  *   phi_cap_h    the unsigned distance is clamped at phi_cap_h * h_min (8)
  *   use_graph    1: replay each step as a captured CUDA graph
+ *   profile      1: record CUDA events around the flux-update kernel of each
+ *                stage (read back with msf_profile_read)
  *   stream       cudaStream_t for all work of this context */
 typedef struct {
   int32_t precision;
@@ -93,7 +95,7 @@ typedef struct {
   int32_t ext_sweeps, vel_sweeps, reinit_iters;
   int32_t scale_sep, reinit;
   double scale_eps_h, phi_cap_h;
-  int32_t use_graph;
+  int32_t use_graph, profile;
   void* stream;
 } msf_options;
 
@@ -177,6 +179,14 @@ msf_status msf_last_dt(msf_ctx* ctx, int32_t instance, double* dt);
  * 4 mixed-cell flag [cells], 5 step material mask [cells]. out: host double array.
  * Cells outside the narrow band hold 0 for fields 1-3. Synchronises. */
 msf_status msf_debug_field(msf_ctx* ctx, int32_t instance, int32_t which, double* out);
+
+/* Number of kernel launches one step enqueues (all instances). */
+msf_status msf_launches_per_step(msf_ctx* ctx, int64_t* n);
+
+/* With opt.profile = 1: device time in ms of the flux-update kernel of each of
+ * the three stages of the last step of instance 0 (flux_ms: host [3]).
+ * Synchronises. MSF_EINVAL when profiling is off. */
+msf_status msf_profile_read(msf_ctx* ctx, double* flux_ms);
 
 /* Human-readable message for the last non-OK status of this context
  * (or of msf_create when ctx is NULL). Never NULL. */

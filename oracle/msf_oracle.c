@@ -373,15 +373,18 @@ static void normal_m(const orc* o, long c, int m, double* n) {
 /* ------------------------------------------------------------------ */
 /* boundary fill of phi, chi (a1)                                        */
 /* ------------------------------------------------------------------ */
-static int bc_src(const orc* o, int d, int idx, int* side) {
+/* source cell of a halo coordinate along axis d: transmissive and inflow copy
+   the nearest interior cell; reflective mirrors about the boundary, repeatedly
+   when the halo is deeper than the interior (flip = odd number of mirrors) */
+static int bc_src(const orc* o, int d, int idx, int* side, int* flip) {
   int n = o->n[d], off = o->off[d], r = idx - off;
-  if (r < 0) {
-    *side = 0;
-    return o->p.bc[d][0] == 1 ? off + (-1 - r) : off;
-  }
-  *side = 1;
-  int kk = r - n;
-  return o->p.bc[d][1] == 1 ? off + n - 1 - kk : off + n - 1;
+  *side = r < 0 ? 0 : 1;
+  *flip = 0;
+  if (o->p.bc[d][*side] != 1) return r < 0 ? off : off + n - 1;
+  int P = 2 * n, k = ((r % P) + P) % P;
+  int count = r < 0 ? (-r - 1) / n + 1 : (r - n) / n + 1;
+  *flip = count & 1;
+  return off + (k >= n ? P - 1 - k : k);
 }
 static void bc_phichi(orc* o) {
   for (int d = 0; d < o->D; d++) {
@@ -394,8 +397,8 @@ static void bc_phichi(orc* o) {
       for (int e = d + 1; e < o->D; e++) /* later axes: interior only, filled by their own pass */
         if (ijk[e] < o->off[e] || ijk[e] >= o->off[e] + o->n[e]) ok = 0;
       if (!ok) continue;
-      int src[3] = {ijk[0], ijk[1], ijk[2]};
-      src[d] = bc_src(o, d, ijk[d], &side);
+      int src[3] = {ijk[0], ijk[1], ijk[2]}, flip;
+      src[d] = bc_src(o, d, ijk[d], &side, &flip);
       long s = cell_at(o, src);
       o->phi[c] = o->phi[s];
       o->chi[c] = o->chi[s];
@@ -644,8 +647,8 @@ static void bc_uhat(orc* o) {
       for (int e = 0; e < D; e++)
         if (e != d && (ijk[e] < o->off[e] || ijk[e] >= o->off[e] + o->n[e])) ok = 0;
       if (!ok) continue;
-      int src[3] = {ijk[0], ijk[1], ijk[2]};
-      src[d] = bc_src(o, d, ijk[d], &side);
+      int src[3] = {ijk[0], ijk[1], ijk[2]}, flip;
+      src[d] = bc_src(o, d, ijk[d], &side, &flip);
       long s = cell_at(o, src);
       int type = o->p.bc[d][side];
       for (int m = 0; m < N; m++) {
@@ -654,7 +657,7 @@ static void bc_uhat(orc* o) {
           prim_to_cons(o, m, o->p.inflow_prim[d][side], u);
         } else {
           for (int v = 0; v < NV; v++) u[v] = o->Uh[QI(o, m, v, s)];
-          if (type == 1) u[1 + d] = -u[1 + d];
+          if (flip) u[1 + d] = -u[1 + d];
         }
         for (int v = 0; v < NV; v++) o->Uh[QI(o, m, v, c)] = u[v];
       }

@@ -42,6 +42,8 @@ struct msf_ctx {
   unsigned* d_flag = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool graph_tried = false;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  long long launches = 0;  // kernel launches of the last enqueued step
   bool sticky = false;
   std::string err;
 };
@@ -84,6 +86,7 @@ extern "C" msf_status msf_default_options(int32_t dim, msf_options* opt) {
   opt->scale_eps_h = 0.0;
   opt->phi_cap_h = 8.0;
   opt->use_graph = 1;
+  opt->profile = 0;
   opt->stream = nullptr;
   return MSF_OK;
 }
@@ -160,6 +163,12 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
     return fail(nullptr, MSF_ENOMEM, "cudaMallocHost");
   }
   ALLOC(c->d_flag, unsigned, 4);
+  if (opt->profile)
+    for (int k = 0; k < 6; k++)
+      if (cudaEventCreate(&c->ev[k]) != cudaSuccess) {
+        msf_destroy(c);
+        return fail(nullptr, MSF_ECUDA, "cudaEventCreate");
+      }
   c->inst.resize(n_instances);
   for (int i = 0; i < n_instances; i++) {
     Inst& in = c->inst[i];
@@ -277,6 +286,8 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
 extern "C" msf_status msf_destroy(msf_ctx* c) {
   if (!c) return MSF_OK;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (int k = 0; k < 6; k++)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
   delete c;
@@ -322,8 +333,11 @@ static msf_status enqueue_step(msf_ctx* c) {
         launch_extend_vel(g, b, V[vc], V[vc ^ 1], VF[vc], VF[vc ^ 1], nb, s);
         vc ^= 1;
       }
+      const bool prof = c->ev[0] && &in == &c->inst[0];
+      if (prof) cudaEventRecord(c->ev[2 * st], s);
       cudaError_t fe = c->ops->flux(g, b, Qs, b.Q[0], Qo, BETA[st], 1.0 - BETA[st], in.bb, s);
       if (fe != cudaSuccess) return fail(c, MSF_ECUDA, std::string("flux launch: ") + cudaGetErrorString(fe));
+      if (prof) cudaEventRecord(c->ev[2 * st + 1], s);
       launch_ledger(g, b, in.nbnd, LW[st], s);
       launch_levelset(g, b, V[vc], BETA[st], 1.0 - BETA[st], nb, s);
       launch_scatter_phichi(g, b, nb, s);
@@ -341,6 +355,16 @@ static msf_status enqueue_step(msf_ctx* c) {
       launch_bc_phichi(g, b, s);
     }
   }
+  // kernels enqueued above (keep in step with the sequence)
+  long long n = 0;
+  for (Inst& in : c->inst) {
+    const Grid& g = in.g;
+    const long long per_stage = 1 + g.ext_sweeps + 1 + 1 + 1 + g.vel_sweeps + 1 + 1 + 1 + 1 + 1 + 1 + 3;
+    n += 1 + 1 + (2 + g.D) + 1 + 1 + 3 * per_stage + 2 + 1;
+    if (g.scale_sep) n += 2 + 1;
+    if (g.reinit) n += 2LL * g.reinit_iters + 1;
+  }
+  c->launches = n;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(c, MSF_ECUDA, std::string("step launch: ") + cudaGetErrorString(e));
   return MSF_OK;
@@ -623,6 +647,37 @@ extern "C" msf_status msf_debug_field(msf_ctx* c, int32_t i, int32_t which, doub
     case 5: return gather_out(c, in, 14, out, sizeof(double) * ni, MSF_HOST, false);
     default: return fail(c, MSF_EINVAL, "which");
   }
+}
+
+extern "C" msf_status msf_launches_per_step(msf_ctx* c, int64_t* n) {
+  if (!c || !n) return MSF_EINVAL;
+  if (!c->launches) {
+    // count without launching: the formula of enqueue_step
+    long long k = 0;
+    for (Inst& in : c->inst) {
+      const Grid& g = in.g;
+      const long long per_stage = 1 + g.ext_sweeps + 1 + 1 + 1 + g.vel_sweeps + 1 + 1 + 1 + 1 + 1 + 1 + 3;
+      k += 1 + 1 + (2 + g.D) + 1 + 1 + 3 * per_stage + 2 + 1;
+      if (g.scale_sep) k += 2 + 1;
+      if (g.reinit) k += 2LL * g.reinit_iters + 1;
+    }
+    *n = k;
+    return MSF_OK;
+  }
+  *n = c->launches;
+  return MSF_OK;
+}
+
+extern "C" msf_status msf_profile_read(msf_ctx* c, double* flux_ms) {
+  if (!c || !flux_ms) return MSF_EINVAL;
+  if (!c->ev[0]) return fail(c, MSF_EINVAL, "profiling is off (msf_options.profile = 0)");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (int st = 0; st < 3; st++) {
+    float ms = 0.0f;
+    CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev[2 * st], c->ev[2 * st + 1]));
+    flux_ms[st] = ms;
+  }
+  return MSF_OK;
 }
 
 extern "C" msf_status msf_adjoint_step(msf_ctx* c, const void* lam_out, void* lam_in, double* d_eos) {

@@ -325,16 +325,18 @@ __device__ inline void normal_m(const Grid& g, const double* phi, const uint8_t*
     for (int d = 0; d < g.D; d++) n[d] = gr[d] / len;
 }
 
-// boundary source index along axis d for halo coordinate idx
-__host__ __device__ inline int bc_source(const Grid& g, int d, int idx, int* side) {
+// boundary source along axis d of halo coordinate idx: transmissive / inflow
+// take the nearest interior cell; reflective mirrors about the boundary,
+// repeatedly when the halo is deeper than the interior (flip: odd count)
+__host__ __device__ inline int bc_source(const Grid& g, int d, int idx, int* side, int* flip) {
   const int n = g.n[d], off = g.off[d], r = idx - off;
-  if (r < 0) {
-    *side = 0;
-    return g.bc[d][0] == 1 ? off + (-1 - r) : off;
-  }
-  *side = 1;
-  const int kk = r - n;
-  return g.bc[d][1] == 1 ? off + n - 1 - kk : off + n - 1;
+  *side = r < 0 ? 0 : 1;
+  *flip = 0;
+  if (g.bc[d][*side] != 1) return r < 0 ? off : off + n - 1;
+  const int P = 2 * n, k = ((r % P) + P) % P;
+  const int count = r < 0 ? (-r - 1) / n + 1 : (r - n) / n + 1;
+  *flip = count & 1;
+  return off + (k >= n ? P - 1 - k : k);
 }
 
 __device__ inline void atomic_max_pos_double(unsigned long long* addr, double v) {

@@ -78,11 +78,11 @@ __global__ void k_bc_phichi(Grid g, Bufs b) {
   long long nh = halo_count(g);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nh;
        idx += (long long)gridDim.x * blockDim.x) {
-    int q[3], s[3], side;
+    int q[3], s[3], side, flip;
     halo_coords(g, idx, q);
     for (int d = 0; d < 3; d++) s[d] = q[d];
     for (int d = 0; d < g.D; d++)
-      if (q[d] < g.off[d] || q[d] >= g.off[d] + g.n[d]) s[d] = bc_source(g, d, q[d], &side);
+      if (q[d] < g.off[d] || q[d] >= g.off[d] + g.n[d]) s[d] = bc_source(g, d, q[d], &side, &flip);
     long long c = cell_at(g, q[0], q[1], q[2]), sc = cell_at(g, s[0], s[1], s[2]);
     b.phi[c] = b.phi[sc];
     b.chi[c] = b.chi[sc];
@@ -423,9 +423,9 @@ __global__ void k_bc_uhat(Grid g, Bufs b, const double* Qs) {
       rest /= g.n[e];
     }
     q[d] = l < G ? (int)l : (int)(g.off[d] + g.n[d] + (l - G));
-    int side;
+    int side, flip;
     int s[3] = {q[0], q[1], q[2]};
-    s[d] = bc_source(g, d, q[d], &side);
+    s[d] = bc_source(g, d, q[d], &side, &flip);
     const long long c = cell_at(g, q[0], q[1], q[2]), sc = cell_at(g, s[0], s[1], s[2]);
     const int type = g.bc[d][side];
     for (int m = 0; m < N; m++) {
@@ -436,7 +436,7 @@ __global__ void k_bc_uhat(Grid g, Bufs b, const double* Qs) {
         prim_to_cons<T>(g, m, D, w, u);
       } else {
         interior_uhat<T>(g, b, Qs, sc, m, u);
-        if (type == 1) u[1 + d] = -u[1 + d];
+        if (flip) u[1 + d] = -u[1 + d];
       }
       for (int v = 0; v < NV; v++) Uh[qidx(g, m, v, c)] = u[v];
     }
@@ -680,11 +680,11 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
   constexpr int NV = D + 2, TX = S::TX, TY = S::TY, TZ = S::TZ, SX = S::SX, SY = S::SY, NS = S::NS;
   if (!ctl_active(b)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* U = (T*)smem_raw;                 // [NV][NS]
+  double* A = (double*)smem_raw;       // [NF] apertures (8-byte aligned first)
+  T* U = (T*)(A + S::NF);              // [NV][NS]
   T* P = U + NV * NS;                  // [D+2][NS]
   T* F = P + (D + 2) * NS;             // [NV][NF]
-  double* A = (double*)(F + NV * S::NF);  // [NF]
-  uint8_t* bad = (uint8_t*)(A + S::NF);    // [NS]
+  uint8_t* bad = (uint8_t*)(F + NV * S::NF);  // [NS]
   __shared__ unsigned s_union;
   __shared__ unsigned s_err;
 

@@ -43,7 +43,8 @@ class msf_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("cfl", C.c_double), ("weno_eps", C.c_double), ("mix_alpha", C.c_double),
                 ("ext_sweeps", C.c_int32), ("vel_sweeps", C.c_int32), ("reinit_iters", C.c_int32),
                 ("scale_sep", C.c_int32), ("reinit", C.c_int32), ("scale_eps_h", C.c_double),
-                ("phi_cap_h", C.c_double), ("use_graph", C.c_int32), ("stream", C.c_void_p)]
+                ("phi_cap_h", C.c_double), ("use_graph", C.c_int32), ("profile", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class MsfError(RuntimeError):
@@ -72,6 +73,8 @@ def _load():
         "msf_stats": ([P, C.POINTER(C.c_int64)], C.c_int),
         "msf_last_dt": ([P, C.c_int32, dp], C.c_int),
         "msf_debug_field": ([P, C.c_int32, C.c_int32, dp], C.c_int),
+        "msf_launches_per_step": ([P, C.POINTER(C.c_int64)], C.c_int),
+        "msf_profile_read": ([P, dp], C.c_int),
         "msf_last_error": ([P], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -96,6 +99,8 @@ msf_set_state = _lib.msf_set_state
 msf_stats = _lib.msf_stats
 msf_last_dt = _lib.msf_last_dt
 msf_debug_field = _lib.msf_debug_field
+msf_launches_per_step = _lib.msf_launches_per_step
+msf_profile_read = _lib.msf_profile_read
 msf_last_error = _lib.msf_last_error
 
 
@@ -123,7 +128,7 @@ def make_grid(p: dict) -> msf_grid:
     return g
 
 
-def make_options(p: dict, precision=MSF_FP64, stream=None, use_graph=1) -> msf_options:
+def make_options(p: dict, precision=MSF_FP64, stream=None, use_graph=1, profile=0) -> msf_options:
     o = msf_options()
     _check(msf_default_options(int(p["dim"]), C.byref(o)), None)
     o.precision = int(precision)
@@ -132,6 +137,7 @@ def make_options(p: dict, precision=MSF_FP64, stream=None, use_graph=1) -> msf_o
     for k in ("ext_sweeps", "vel_sweeps", "reinit_iters", "scale_sep", "reinit"):
         setattr(o, k, int(p[k]))
     o.use_graph = int(use_graph)
+    o.profile = int(profile)
     o.stream = stream
     return o
 
@@ -149,14 +155,14 @@ def _ptr(a, kind):
 class Solver:
     """One context with one instance, built from a case (see cases.Case)."""
 
-    def __init__(self, case, precision=MSF_FP64, stream=None, use_graph=1, **opts):
+    def __init__(self, case, precision=MSF_FP64, stream=None, use_graph=1, profile=0, **opts):
         self.case = case
         self.p = case.params(**opts)
         self.N, self.NV, self.cells = case.nmat, case.nv, case.cells
         self._grid = make_grid(self.p)
         eos = (msf_eos * self.N)(*[msf_eos(self.p["gamma"][m], self.p["pinf"][m]) for m in range(self.N)])
         self._eos = eos
-        self._opt = make_options(self.p, precision, stream, use_graph)
+        self._opt = make_options(self.p, precision, stream, use_graph, profile)
         h = C.c_void_p()
         st = msf_create(C.byref(self._grid), 1, self.N, eos, C.byref(self._opt), C.byref(h))
         if st != MSF_OK:
@@ -219,6 +225,16 @@ class Solver:
         dt = C.c_double()
         _check(msf_last_dt(self.h, 0, C.byref(dt)), self.h)
         return dt.value
+
+    def launches_per_step(self):
+        n = C.c_int64()
+        _check(msf_launches_per_step(self.h, C.byref(n)), self.h)
+        return n.value
+
+    def flux_ms(self):
+        out = (C.c_double * 3)()
+        _check(msf_profile_read(self.h, out), self.h)
+        return list(out)
 
     def debug(self, which):
         sizes = {0: self.N, 1: self.N * self.NV, 2: self.N * self.NV, 3: 3, 4: 1, 5: 1}
