@@ -269,6 +269,7 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
     ALLOC(b.phit, double, nbmax);
     ALLOC(b.chit, uint8_t, nbmax);
     ALLOC(b.mixq, double, nbmax * N * NV);
+    ALLOC(b.mixmerge, unsigned, nbmax);
     ALLOC(b.bflux, double, std::max<long long>(1, nb) * N * NV);
     ALLOC(b.ctl, Ctl, 1);
     cudaMemsetAsync(b.bandidx, 0xff, sizeof(int) * nc, c->stream);

@@ -50,10 +50,25 @@ struct Ctl {
 };
 
 // ---------------------------------------------------------------- indexing
+// cell counts are below 2^31 (checked at creation): 32-bit unsigned division
 __host__ __device__ inline void coords(const Grid& g, long long c, int* q) {
-  q[0] = (int)(c % g.pn[0]);
-  q[1] = (int)((c / g.pn[0]) % g.pn[1]);
-  q[2] = (int)(c / ((long long)g.pn[0] * g.pn[1]));
+  const unsigned cc = (unsigned)c, p0 = (unsigned)g.pn[0], p1 = (unsigned)g.pn[1];
+  const unsigned t = cc / p0;
+  q[0] = (int)(cc - t * p0);
+  const unsigned z = t / p1;
+  q[1] = (int)(t - z * p1);
+  q[2] = (int)z;
+}
+// padded cell of the idx-th interior cell (interior order, x fastest)
+__host__ __device__ inline long long interior_cell(const Grid& g, long long idx) {
+  unsigned r = (unsigned)idx;
+  int q[3] = {0, 0, 0};
+  for (int d = 0; d < g.D; d++) {
+    const unsigned nd = (unsigned)g.n[d], t = r / nd;
+    q[d] = g.off[d] + (int)(r - t * nd);
+    r = t;
+  }
+  return q[0] + g.st[1] * q[1] + g.st[2] * q[2];
 }
 __host__ __device__ inline long long cell_at(const Grid& g, int i, int j, int k) {
   return i + g.st[1] * j + g.st[2] * k;

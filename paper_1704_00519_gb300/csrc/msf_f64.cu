@@ -21,16 +21,6 @@ static int grid_blocks(long long n) {
   return (int)b;
 }
 
-__device__ inline long long interior_cell(const Grid& g, long long idx) {
-  long long r = idx;
-  int q[3] = {0, 0, 0};
-  for (int d = 0; d < g.D; d++) {
-    q[d] = (int)(g.off[d] + r % g.n[d]);
-    r /= g.n[d];
-  }
-  return cell_at(g, q[0], q[1], q[2]);
-}
-
 // ------------------------------------------------------------ start-up
 __global__ void k_init_levelset(Grid g, Bufs b, const double* phi_in, const int32_t* chi_in) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.n_interior;
@@ -193,7 +183,7 @@ void launch_extend_vel(const Grid& g, const Bufs& b, const double* vin, double* 
   k_extend_vel<<<nblk, NTHREADS, 0, s>>>(g, b, vin, vout, fin, fout);
 }
 void launch_ledger(const Grid& g, const Bufs& b, int nbnd, double w, cudaStream_t s) {
-  k_ledger<<<1, 64, 0, s>>>(g, b, nbnd, w);
+  k_ledger<<<g.N * g.NV, NTHREADS, 0, s>>>(g, b, nbnd, w);
 }
 void launch_levelset(const Grid& g, const Bufs& b, const double* vel, double beta, double omb, int nblk,
                      cudaStream_t s) {

@@ -20,57 +20,52 @@ __device__ inline bool ctl_active(const Bufs& b) { return b.ctl->active != 0; }
 
 // --------------------------------------------------------------- halo cells
 __device__ inline long long halo_count(const Grid& g) { return g.ncell - g.n_interior; }
-__device__ inline void halo_coords(const Grid& g, long long idx, int* q) {
+__device__ inline void halo_coords(const Grid& g, long long idx_, int* q) {
   // z slabs, then y rows of interior z, then x columns of interior (y, z)
+  unsigned idx = (unsigned)idx_;
+  const unsigned p0 = g.pn[0], p1 = g.pn[1], TG = 2u * G;
   if (g.D == 3) {
-    long long slab = 2LL * G * g.pn[0] * g.pn[1];
+    const unsigned slab = TG * p0 * p1;
     if (idx < slab) {
-      long long l = idx / ((long long)g.pn[0] * g.pn[1]);
-      long long r = idx % ((long long)g.pn[0] * g.pn[1]);
-      q[2] = l < G ? (int)l : (int)(g.off[2] + g.n[2] + (l - G));
-      q[1] = (int)(r / g.pn[0]);
-      q[0] = (int)(r % g.pn[0]);
+      const unsigned l = idx / (p0 * p1), r = idx - l * (p0 * p1);
+      q[2] = l < (unsigned)G ? (int)l : g.off[2] + g.n[2] + (int)(l - G);
+      q[1] = (int)(r / p0);
+      q[0] = (int)(r - (r / p0) * p0);
       return;
     }
     idx -= slab;
-    long long rows = 2LL * G * g.pn[0] * g.n[2];
+    const unsigned rows = TG * p0 * g.n[2];
     if (idx < rows) {
-      long long kk = idx / (2LL * G * g.pn[0]);
-      long long r = idx % (2LL * G * g.pn[0]);
-      long long l = r / g.pn[0];
-      q[2] = (int)(g.off[2] + kk);
-      q[1] = l < G ? (int)l : (int)(g.off[1] + g.n[1] + (l - G));
-      q[0] = (int)(r % g.pn[0]);
+      const unsigned kk = idx / (TG * p0), r = idx - kk * (TG * p0), l = r / p0;
+      q[2] = g.off[2] + (int)kk;
+      q[1] = l < (unsigned)G ? (int)l : g.off[1] + g.n[1] + (int)(l - G);
+      q[0] = (int)(r - l * p0);
       return;
     }
     idx -= rows;
-    long long kk = idx / (2LL * G * g.n[1]);
-    long long r = idx % (2LL * G * g.n[1]);
-    long long jj = r / (2 * G);
-    long long l = r % (2 * G);
-    q[2] = (int)(g.off[2] + kk);
-    q[1] = (int)(g.off[1] + jj);
-    q[0] = l < G ? (int)l : (int)(g.off[0] + g.n[0] + (l - G));
+    const unsigned kk = idx / (TG * g.n[1]), r = idx - kk * (TG * g.n[1]), jj = r / TG, l = r - jj * TG;
+    q[2] = g.off[2] + (int)kk;
+    q[1] = g.off[1] + (int)jj;
+    q[0] = l < (unsigned)G ? (int)l : g.off[0] + g.n[0] + (int)(l - G);
     return;
   }
   if (g.D == 2) {
     q[2] = 0;
-    long long rows = 2LL * G * g.pn[0];
+    const unsigned rows = TG * p0;
     if (idx < rows) {
-      long long l = idx / g.pn[0];
-      q[1] = l < G ? (int)l : (int)(g.off[1] + g.n[1] + (l - G));
-      q[0] = (int)(idx % g.pn[0]);
+      const unsigned l = idx / p0;
+      q[1] = l < (unsigned)G ? (int)l : g.off[1] + g.n[1] + (int)(l - G);
+      q[0] = (int)(idx - l * p0);
       return;
     }
     idx -= rows;
-    long long jj = idx / (2 * G);
-    long long l = idx % (2 * G);
-    q[1] = (int)(g.off[1] + jj);
-    q[0] = l < G ? (int)l : (int)(g.off[0] + g.n[0] + (l - G));
+    const unsigned jj = idx / TG, l = idx - jj * TG;
+    q[1] = g.off[1] + (int)jj;
+    q[0] = l < (unsigned)G ? (int)l : g.off[0] + g.n[0] + (int)(l - G);
     return;
   }
   q[1] = q[2] = 0;
-  q[0] = idx < G ? (int)idx : (int)(g.off[0] + g.n[0] + (idx - G));
+  q[0] = idx < (unsigned)G ? (int)idx : g.off[0] + g.n[0] + (int)(idx - G);
 }
 
 // halo cells of phi, chi: every out-of-range axis mapped to its boundary source
@@ -253,6 +248,12 @@ __global__ void k_geometry(Grid g, Bufs b, const double* Qs, const double* mass)
   }
 }
 
+// interior test of the face neighbour of a cell with coordinates q (side 0: -e_d)
+__device__ inline bool nb_interior(const Grid& g, const int* q, int d, int side) {
+  const int p = q[d] + (side ? 1 : -1);
+  return p >= g.off[d] && p < g.off[d] + g.n[d];
+}
+
 // present: positive volume or a positive aperture on one of the cell's faces
 __device__ inline bool present(const Grid& g, const Bufs& b, long long c, int m) {
   if (b.alpha[midx(g, m, c)] > 0.0) return true;
@@ -282,21 +283,21 @@ __global__ void k_prim(Grid g, Bufs b, const double* Qs) {
   const int nb = b.ctl->nband, N = g.N, NV = g.NV;
   T* W0 = (T*)b.W0;
   T* W1 = (T*)b.W1;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+  const int total = nb * N;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
-    for (int m = 0; m < N; m++) {
-      b.f0[midx(g, m, c)] = 0;
-      b.isreal[midx(g, m, c)] = 0;
-      if (!((b.smask[c] >> m) & 1u)) continue;
-      const double a = b.alpha[midx(g, m, c)];
-      if (b.chi[c] == m && a > 0.0) {
-        T u[5], w[5];
-        for (int v = 0; v < NV; v++) u[v] = (T)(Qs[qidx(g, m, v, c)] / a);
-        cons_to_prim<T>(g, m, g.D, u, w);
-        for (int v = 0; v < NV; v++) W0[qidx(g, m, v, c)] = W1[qidx(g, m, v, c)] = w[v];
-        b.f0[midx(g, m, c)] = 1;
-        b.isreal[midx(g, m, c)] = 1;
-      }
+    b.f0[midx(g, m, c)] = 0;
+    b.isreal[midx(g, m, c)] = 0;
+    if (!((b.smask[c] >> m) & 1u)) continue;
+    const double a = b.alpha[midx(g, m, c)];
+    if (b.chi[c] == m && a > 0.0) {
+      T u[5], w[5];
+      for (int v = 0; v < NV; v++) u[v] = (T)(Qs[qidx(g, m, v, c)] / a);
+      cons_to_prim<T>(g, m, g.D, u, w);
+      for (int v = 0; v < NV; v++) W0[qidx(g, m, v, c)] = W1[qidx(g, m, v, c)] = w[v];
+      b.f0[midx(g, m, c)] = 1;
+      b.isreal[midx(g, m, c)] = 1;
     }
   }
 }
@@ -309,43 +310,46 @@ __global__ void k_extend(Grid g, Bufs b, const void* Win, void* Wout, const uint
   const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
   const T* Wi = (const T*)Win;
   T* Wo = (T*)Wout;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+  const int total = nb * N;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
-    for (int m = 0; m < N; m++) {
-      if (!((b.smask[c] >> m) & 1u)) continue;
-      if (b.isreal[midx(g, m, c)]) {
-        fout[midx(g, m, c)] = 1;
-        continue;
-      }
-      double n[3];
-      normal_m(g, b.phi, b.chi, c, m, n);
-      T acc[5] = {T(0), T(0), T(0), T(0), T(0)}, acc2[5] = {T(0), T(0), T(0), T(0), T(0)};
-      T sw = T(0);
-      int cnt = 0;
-      for (int d = 0; d < D; d++)
-        for (int s = 0; s < 2; s++) {
-          const long long j = s ? c + g.st[d] : c - g.st[d];
-          if (!interior_c(g, j) || b.bandidx[j] < 0 || !((b.smask[j] >> m) & 1u) || !fin[midx(g, m, j)]) continue;
-          T w = (T)(s ? n[d] : -n[d]);
-          w = w > T(0) ? w : T(0);
-          for (int v = 0; v < NV; v++) {
-            const T x = Wi[qidx(g, m, v, j)];
-            acc[v] += w * x;
-            acc2[v] += x;
-          }
-          sw += w;
-          cnt++;
+    if (!((b.smask[c] >> m) & 1u)) continue;
+    if (b.isreal[midx(g, m, c)]) {
+      fout[midx(g, m, c)] = 1;
+      continue;
+    }
+    int q[3];
+    coords(g, c, q);
+    double n[3];
+    normal_m(g, b.phi, b.chi, c, m, n);
+    T acc[5] = {T(0), T(0), T(0), T(0), T(0)}, acc2[5] = {T(0), T(0), T(0), T(0), T(0)};
+    T sw = T(0);
+    int cnt = 0;
+    for (int d = 0; d < D; d++)
+      for (int s = 0; s < 2; s++) {
+        if (!nb_interior(g, q, d, s)) continue;
+        const long long j = s ? c + g.st[d] : c - g.st[d];
+        if (b.bandidx[j] < 0 || !((b.smask[j] >> m) & 1u) || !fin[midx(g, m, j)]) continue;
+        T w = (T)(s ? n[d] : -n[d]);
+        w = w > T(0) ? w : T(0);
+        for (int v = 0; v < NV; v++) {
+          const T x = Wi[qidx(g, m, v, j)];
+          acc[v] += w * x;
+          acc2[v] += x;
         }
-      if (sw > T(0)) {
-        for (int v = 0; v < NV; v++) Wo[qidx(g, m, v, c)] = acc[v] / sw;
-        fout[midx(g, m, c)] = 1;
-      } else if (cnt > 0) {
-        for (int v = 0; v < NV; v++) Wo[qidx(g, m, v, c)] = acc2[v] / (T)cnt;
-        fout[midx(g, m, c)] = 1;
-      } else {
-        for (int v = 0; v < NV; v++) Wo[qidx(g, m, v, c)] = Wi[qidx(g, m, v, c)];
-        fout[midx(g, m, c)] = fin[midx(g, m, c)];
+        sw += w;
+        cnt++;
       }
+    if (sw > T(0)) {
+      for (int v = 0; v < NV; v++) Wo[qidx(g, m, v, c)] = acc[v] / sw;
+      fout[midx(g, m, c)] = 1;
+    } else if (cnt > 0) {
+      for (int v = 0; v < NV; v++) Wo[qidx(g, m, v, c)] = acc2[v] / (T)cnt;
+      fout[midx(g, m, c)] = 1;
+    } else {
+      for (int v = 0; v < NV; v++) Wo[qidx(g, m, v, c)] = Wi[qidx(g, m, v, c)];
+      fout[midx(g, m, c)] = fin[midx(g, m, c)];
     }
   }
 }
@@ -358,9 +362,11 @@ __global__ void k_cons(Grid g, Bufs b, const double* Qs, const void* Wfin, const
   const T* W = (const T*)Wfin;
   T* Uh = (T*)b.Uh;
   const T nanv = (T)__longlong_as_double(0x7ff8000000000000LL);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+  const int total = nb * N;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
-    for (int m = 0; m < N; m++) {
+    {
       T u[5];
       if (!((b.smask[c] >> m) & 1u)) {
         for (int v = 0; v < NV; v++) u[v] = nanv;
@@ -410,19 +416,22 @@ __global__ void k_bc_uhat(Grid g, Bufs b, const double* Qs) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     int d = 0;
-    long long r = idx;
-    while (r >= per[d]) { r -= per[d]; d++; }
+    long long r0 = idx;
+    while (r0 >= per[d]) { r0 -= per[d]; d++; }
     // r -> (layer l in [0, 2G), other coordinates in interior order)
-    const long long l = r % (2 * G);
-    long long rest = r / (2 * G);
+    const unsigned r = (unsigned)r0;
+    const unsigned rest0 = r / (2u * G);
+    const unsigned l = r - rest0 * (2u * G);
+    unsigned rest = rest0;
     int q[3];
     for (int e = 0; e < 3; e++) {
       if (e == d) continue;
       if (e >= D) { q[e] = 0; continue; }
-      q[e] = (int)(g.off[e] + rest % g.n[e]);
-      rest /= g.n[e];
+      const unsigned ne = (unsigned)g.n[e], t = rest / ne;
+      q[e] = g.off[e] + (int)(rest - t * ne);
+      rest = t;
     }
-    q[d] = l < G ? (int)l : (int)(g.off[d] + g.n[d] + (l - G));
+    q[d] = l < (unsigned)G ? (int)l : g.off[d] + g.n[d] + (int)(l - G);
     int side, flip;
     int s[3] = {q[0], q[1], q[2]};
     s[d] = bc_source(g, d, q[d], &side, &flip);
@@ -452,14 +461,7 @@ __global__ void k_dt(Grid g, Bufs b, const double* Qs) {
   unsigned err = 0;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.n_interior;
        idx += (long long)gridDim.x * blockDim.x) {
-    // interior index -> cell
-    long long r = idx;
-    int q[3] = {0, 0, 0};
-    for (int d = 0; d < D; d++) {
-      q[d] = (int)(g.off[d] + r % g.n[d]);
-      r /= g.n[d];
-    }
-    const long long c = cell_at(g, q[0], q[1], q[2]);
+    const long long c = interior_cell(g, idx);
     const bool inb = b.bandidx[c] >= 0;
     for (int m = 0; m < N; m++) {
       if (inb ? !(b.alpha[midx(g, m, c)] > 0.0) : b.chi[c] != m) continue;
@@ -589,10 +591,13 @@ __global__ void k_extend_vel(Grid g, Bufs b, const double* vin, double* vout, co
     }
     double acc[3] = {0, 0, 0}, acc2[3] = {0, 0, 0};
     int cnt = 0, cnt2 = 0;
+    int q[3];
+    coords(g, c, q);
     for (int d = 0; d < D; d++)
       for (int s = 0; s < 2; s++) {
+        if (!nb_interior(g, q, d, s)) continue;
         const long long j = s ? c + g.st[d] : c - g.st[d];
-        if (!interior_c(g, j) || b.bandidx[j] < 0 || !fin[j]) continue;
+        if (b.bandidx[j] < 0 || !fin[j]) continue;
         for (int e = 0; e < D; e++) acc2[e] += vin[e * g.ncell + j];
         cnt2++;
         if (b.phi[j] < b.phi[c]) {
@@ -703,6 +708,8 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
   }
   __syncthreads();
   if (mymask) atomicOr(&s_union, (unsigned)mymask);
+  // a tile without band cells has one material whose faces all have aperture 1
+  const bool anyband = __syncthreads_or(inside && b.bandidx[c] >= 0) != 0;
   // boundary faces of this tile: clear the slots of every material first
   if (inside) {
     for (int d = 0; d < D; d++) {
@@ -797,10 +804,12 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
       for (int v = 0; v < NV; v++) Fh[v] = T(0);
       if (exists) {
         const long long cR = cell_at(g, gx, gy, gz), cL = cR - g.st[d];
-        Af = face_aperture(g, b, cL, cR, d, m);
+        Af = anyband ? face_aperture(g, b, cL, cR, d, m) : 1.0;
         if (Af > 0.0) {
-          const bool lin = interior_c(g, cL), rin = interior_c(g, cR);
-          if ((lin && !((b.smask[cL] >> m) & 1u)) || (rin && !((b.smask[cR] >> m) & 1u))) err |= ERR_BAND;
+          if (anyband) {
+            const bool lin = qR[d] - 1 >= g.off[d], rin = qR[d] < g.off[d] + g.n[d];
+            if ((lin && !((b.smask[cL] >> m) & 1u)) || (rin && !((b.smask[cR] >> m) & 1u))) err |= ERR_BAND;
+          }
           const int sR = (fx + 3) + SX * ((fy + S::HY) + SY * (fz + S::HZ));
           const int sstride = d == 0 ? 1 : (d == 1 ? SX : SX * SY);
           const int sL = sR - sstride;
@@ -870,16 +879,21 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
   if (tid == 0 && s_err) atomicOr(&b.ctl->err, s_err);
 }
 
-// sum the boundary-face fluxes of the stage in face order and add them to the ledger
+// sum the boundary-face fluxes of the stage (one block per material and
+// variable, fixed-order tree reduction) and add them to the ledger
 __global__ void k_ledger(Grid g, Bufs b, int nbnd, double w) {
   if (!ctl_active(b)) return;
-  const int N = g.N, NV = g.NV;
-  for (int mv = threadIdx.x; mv < N * NV; mv += blockDim.x) {
-    // inflow through low faces, outflow through high faces
-    double s = 0.0;
-    for (int f = 0; f < nbnd; f++) s += b.bflux[(long long)f * N * NV + mv];
-    b.ctl->ledger[mv / NV][mv % NV] += w * b.ctl->dt * s;
+  const int NMV = g.N * g.NV, mv = blockIdx.x;
+  double s = 0.0;
+  for (int f = threadIdx.x; f < nbnd; f += blockDim.x) s += b.bflux[(long long)f * NMV + mv];
+  __shared__ double red[NTHREADS];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) b.ctl->ledger[mv / g.NV][mv % g.NV] += w * b.ctl->dt * red[0];
 }
 
 // --------------------------------------------- level-set stage (a9) + R
@@ -1036,83 +1050,89 @@ __global__ void k_mix_mark(Grid g, Bufs b, const double* Qc) {
   if (nsmall) atomicAdd(&b.ctl->cnt[C_SMALL], nsmall);
 }
 
-// new state of every band cell: own exchanges minus the exchanges its small
-// neighbours send to it (lexicographic neighbour order), then merges
+// new state of material m of every band cell: own exchanges minus the
+// exchanges its small neighbours send to it (lexicographic neighbour order)
 __global__ void k_mix_compute(Grid g, Bufs b, const double* Qc) {
   if (!ctl_active(b)) return;
   const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
-  unsigned long long nfail = 0, nmerge = 0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+  unsigned long long nfail = 0;
+  const int total = nb * N;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
+    double* out = b.mixq + ((long long)k * N + m) * NV;
+    for (int v = 0; v < NV; v++) out[v] = Qc[qidx(g, m, v, c)];
+    if (!((b.smask[c] >> m) & 1u)) continue;
     int q[3];
     coords(g, c, q);
-    double* out = b.mixq + (long long)k * N * NV;
-    unsigned mergebits = 0;
-    for (int m = 0; m < N; m++) {
-      for (int v = 0; v < NV; v++) out[m * NV + v] = Qc[qidx(g, m, v, c)];
-      if (!((b.smask[c] >> m) & 1u)) continue;
-      double acc[5] = {0, 0, 0, 0, 0};
-      if ((b.small[c] >> m) & 1u) {
-        const double as = b.alpha[midx(g, m, c)];
-        long long tc[MIX_MAXT];
-        double tw[MIX_MAXT], sw;
-        const int nt = mix_targets(g, b, c, m, as, tc, tw, &sw);
-        if (nt == 0) {
-          nfail++;
-          if (as == 0.0 && m != b.chi[c]) mergebits |= 1u << m;
-        }
-        for (int t = 0; t < nt; t++) {
-          const double beta = tw[t] / sw;
-          const double at = b.alpha[midx(g, m, tc[t])];
-          for (int v = 0; v < NV; v++)
-            acc[v] += beta * (as * Qc[qidx(g, m, v, tc[t])] - at * Qc[qidx(g, m, v, c)]) / (as + at);
-        }
+    double acc[5] = {0, 0, 0, 0, 0};
+    if ((b.small[c] >> m) & 1u) {
+      const double as = b.alpha[midx(g, m, c)];
+      long long tc[MIX_MAXT];
+      double tw[MIX_MAXT], sw;
+      const int nt = mix_targets(g, b, c, m, as, tc, tw, &sw);
+      if (nt == 0) {
+        nfail++;
+        if (as == 0.0 && m != b.chi[c]) atomicOr(&b.mixmerge[k], 1u << m);
       }
-      const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
-      for (int dz = -rz; dz <= rz; dz++)
-        for (int dy = -ry; dy <= ry; dy++)
-          for (int dx = -1; dx <= 1; dx++) {
-            if (dx == 0 && dy == 0 && dz == 0) continue;
-            const int sx = q[0] - dx, sy = q[1] - dy, sz = q[2] - dz;
-            if (!in_array(g, sx, sy, sz)) continue;
-            const long long s = cell_at(g, sx, sy, sz);
-            if (!((b.small[s] >> m) & 1u)) continue;
-            const double as = b.alpha[midx(g, m, s)];
-            long long tc[MIX_MAXT];
-            double tw[MIX_MAXT], sw;
-            const int nt = mix_targets(g, b, s, m, as, tc, tw, &sw);
-            for (int t = 0; t < nt; t++) {
-              if (tc[t] != c) continue;
-              const double beta = tw[t] / sw;
-              const double at = b.alpha[midx(g, m, c)];
-              for (int v = 0; v < NV; v++)
-                acc[v] -= beta * (as * Qc[qidx(g, m, v, c)] - at * Qc[qidx(g, m, v, s)]) / (as + at);
-            }
+      for (int t = 0; t < nt; t++) {
+        const double beta = tw[t] / sw;
+        const double at = b.alpha[midx(g, m, tc[t])];
+        for (int v = 0; v < NV; v++)
+          acc[v] += beta * (as * Qc[qidx(g, m, v, tc[t])] - at * Qc[qidx(g, m, v, c)]) / (as + at);
+      }
+    }
+    const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
+    for (int dz = -rz; dz <= rz; dz++)
+      for (int dy = -ry; dy <= ry; dy++)
+        for (int dx = -1; dx <= 1; dx++) {
+          if (dx == 0 && dy == 0 && dz == 0) continue;
+          const int sx = q[0] - dx, sy = q[1] - dy, sz = q[2] - dz;
+          if (!in_array(g, sx, sy, sz)) continue;
+          const long long s = cell_at(g, sx, sy, sz);
+          if (!((b.small[s] >> m) & 1u)) continue;
+          const double as = b.alpha[midx(g, m, s)];
+          long long tc[MIX_MAXT];
+          double tw[MIX_MAXT], sw;
+          const int nt = mix_targets(g, b, s, m, as, tc, tw, &sw);
+          for (int t = 0; t < nt; t++) {
+            if (tc[t] != c) continue;
+            const double beta = tw[t] / sw;
+            const double at = b.alpha[midx(g, m, c)];
+            for (int v = 0; v < NV; v++)
+              acc[v] -= beta * (as * Qc[qidx(g, m, v, c)] - at * Qc[qidx(g, m, v, s)]) / (as + at);
           }
-      for (int v = 0; v < NV; v++) out[m * NV + v] = Qc[qidx(g, m, v, c)] + acc[v];
-    }
-    for (int m = 0; m < N; m++) {
-      if (!((mergebits >> m) & 1u)) continue;
-      const int pm = b.chi[c];
-      for (int v = 0; v < NV; v++) {
-        out[pm * NV + v] = out[pm * NV + v] + out[m * NV + v];
-        out[m * NV + v] = 0.0;
-      }
-      nmerge++;
-    }
+        }
+    for (int v = 0; v < NV; v++) out[v] = Qc[qidx(g, m, v, c)] + acc[v];
   }
   if (nfail) atomicAdd(&b.ctl->cnt[C_MIXFAIL], nfail);
-  if (nmerge) atomicAdd(&b.ctl->cnt[C_MERGE], nmerge);
 }
+// write the mixed states back; a material that lost all volume and has no
+// same-material neighbour is merged into the cell's primary material
 __global__ void k_mix_scatter(Grid g, Bufs b, double* Qc) {
   if (!ctl_active(b)) return;
   const int nb = b.ctl->nband, N = g.N, NV = g.NV;
+  unsigned long long nmerge = 0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
     const long long c = b.band[k];
-    const double* in = b.mixq + (long long)k * N * NV;
+    double* in = b.mixq + (long long)k * N * NV;
+    const unsigned mb = b.mixmerge[k];
+    if (mb) {
+      const int pm = b.chi[c];
+      for (int m = 0; m < N; m++) {
+        if (!((mb >> m) & 1u)) continue;
+        for (int v = 0; v < NV; v++) {
+          in[pm * NV + v] = in[pm * NV + v] + in[m * NV + v];
+          in[m * NV + v] = 0.0;
+        }
+        nmerge++;
+      }
+      b.mixmerge[k] = 0;
+    }
     for (int m = 0; m < N; m++)
       for (int v = 0; v < NV; v++) Qc[qidx(g, m, v, c)] = in[m * NV + v];
   }
+  if (nmerge) atomicAdd(&b.ctl->cnt[C_MERGE], nmerge);
 }
 
 // ------------------------------------------------- scale separation (a12)
@@ -1241,13 +1261,7 @@ __global__ void k_totals(Grid g, const double* Q, double* out) {
   const int m = mv / g.NV, v = mv % g.NV;
   double s = 0.0;
   for (long long idx = threadIdx.x; idx < g.n_interior; idx += blockDim.x) {
-    long long r = idx;
-    int q[3] = {0, 0, 0};
-    for (int d = 0; d < g.D; d++) {
-      q[d] = (int)(g.off[d] + r % g.n[d]);
-      r /= g.n[d];
-    }
-    s += Q[qidx(g, m, v, cell_at(g, q[0], q[1], q[2]))];
+    s += Q[qidx(g, m, v, interior_cell(g, idx))];
   }
   __shared__ double red[NTHREADS];
   red[threadIdx.x] = s;

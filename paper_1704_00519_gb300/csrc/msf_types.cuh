@@ -29,6 +29,7 @@ struct Bufs {
   double* phit;             // [nbandmax] scratch
   uint8_t* chit;            // [nbandmax] scratch
   double* mixq;             // [nbandmax][N][NV] mixed state scratch
+  unsigned* mixmerge;       // [nbandmax] materials to merge into the primary
   double* bflux;            // [nbnd][N][NV] boundary-face fluxes of the stage
   Ctl* ctl;
 };
