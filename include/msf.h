@@ -188,6 +188,31 @@ msf_status msf_launches_per_step(msf_ctx* ctx, int64_t* n);
  * Synchronises. MSF_EINVAL when profiling is off. */
 msf_status msf_profile_read(msf_ctx* ctx, double* flux_ms);
 
+/* Largest state msf_cfl_dt_noalloc accepts: its scratch holds one partial
+ * maximum per 256 cells, 16384 doubles (128 KiB) on every device. */
+#define MSF_NOALLOC_MAX_CELLS 4194304
+
+/* CFL time step of a single-material state, for callers that must not
+ * allocate device memory. The paper has no counterpart: this is a service of
+ * the library, the same bound msf_step applies to a cell with one material
+ * (dt = cfl / max over cells of sum_d (|u_d| + c) / h_d, c^2 = gamma (p + pinf) / rho).
+ *   U       device [dim + 2][cells] conservative state (rho, rho u_d, rho E)
+ *   cells   1 .. MSF_NOALLOC_MAX_CELLS (larger: MSF_EINVAL)
+ *   eos     host pointer, the material; h host [dim] cell sizes
+ *   dt_out  device pointer to one double, written asynchronously
+ *   stream  cudaStream_t for the two kernels (NULL: legacy default stream)
+ * Calls no cudaMalloc/cudaFree and no allocating library routine: its scratch
+ * is a fixed array compiled into the library, present on every device that
+ * loads it until the process exits. The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current; make
+ * that first call before any stream capture. Every call shares the array and
+ * writes every slot it reads, so nothing needs clearing between calls; calls
+ * that overlap on the GPU (other streams, other threads) race on it and must
+ * be ordered by the caller. Errors: MSF_EINVAL (message via
+ * msf_last_error(NULL)), MSF_ECUDA. */
+msf_status msf_cfl_dt_noalloc(const double* U, int64_t cells, int32_t dim, const msf_eos* eos, const double* h,
+                              double cfl, double* dt_out, void* stream);
+
 /* Human-readable message for the last non-OK status of this context
  * (or of msf_create when ctx is NULL). Never NULL. */
 const char* msf_last_error(const msf_ctx* ctx);

@@ -689,6 +689,9 @@ extern "C" msf_status msf_adjoint_step(msf_ctx* c, const void* lam_out, void* la
   return fail(c, MSF_EUNSUPPORTED, "the adjoint step is not provided by this build");
 }
 
+// message slot of calls without a context (used by msf_cfl_dt_noalloc)
+extern "C" void msf_internal_set_error(const char* msg) { g_create_err = msg ? msg : ""; }
+
 extern "C" const char* msf_last_error(const msf_ctx* c) {
   if (!c) return g_create_err.c_str();
   return c->err.c_str();

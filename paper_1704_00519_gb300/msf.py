@@ -75,6 +75,7 @@ def _load():
         "msf_debug_field": ([P, C.c_int32, C.c_int32, dp], C.c_int),
         "msf_launches_per_step": ([P, C.POINTER(C.c_int64)], C.c_int),
         "msf_profile_read": ([P, dp], C.c_int),
+        "msf_cfl_dt_noalloc": ([P, C.c_int64, C.c_int32, C.POINTER(msf_eos), dp, C.c_double, P, P], C.c_int),
         "msf_last_error": ([P], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -101,6 +102,7 @@ msf_last_dt = _lib.msf_last_dt
 msf_debug_field = _lib.msf_debug_field
 msf_launches_per_step = _lib.msf_launches_per_step
 msf_profile_read = _lib.msf_profile_read
+msf_cfl_dt_noalloc = _lib.msf_cfl_dt_noalloc
 msf_last_error = _lib.msf_last_error
 
 
