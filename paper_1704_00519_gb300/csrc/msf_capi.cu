@@ -7,6 +7,7 @@
 // time step, the end time and every branch on them live on the device, so a
 // replayed graph needs no host round trip; the only readback of msf_step is
 // the 4-byte error word when the caller asks for synchronisation.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -92,8 +93,10 @@ extern "C" msf_status msf_default_options(int32_t dim, msf_options* opt) {
 }
 
 static int band_blocks(const Grid& g) {
-  long long b = (g.n_interior + NTHREADS - 1) / NTHREADS;
-  if (b > 608) b = 608;  // 152 SMs x 4 CTAs; band kernels stride over the list
+  // band kernels stride over (band cell, material) items with 64-thread
+  // blocks: up to 16 blocks per SM of the 152 SMs
+  long long b = (g.n_interior * g.N + BAND_THREADS - 1) / BAND_THREADS;
+  if (b > 152 * 16) b = 152 * 16;
   if (b < 1) b = 1;
   return (int)b;
 }
@@ -245,7 +248,7 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
     ALLOC(b.smask, uint8_t, nc);
     ALLOC(b.xsS, uint8_t, nc);
     ALLOC(b.gflag, uint8_t, nc);
-    ALLOC(b.small, uint8_t, nc);
+    ALLOC(b.nrm, double, N * 3 * nc);
     ALLOC(b.alpha, double, N * nc);
     ALLOC(b.Alo, double, dim * N * nc);
     ALLOC(b.Ahi, double, dim * N * nc);
@@ -270,6 +273,10 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
     ALLOC(b.chit, uint8_t, nbmax);
     ALLOC(b.mixq, double, nbmax * N * NV);
     ALLOC(b.mixmerge, unsigned, nbmax);
+    ALLOC(b.mixn, uint8_t, nbmax * N);
+    ALLOC(b.mixoff, uint8_t, nbmax * N * MIX_MAXT);
+    ALLOC(b.mixbeta, double, nbmax * N * MIX_MAXT);
+    ALLOC(b.phir, double, nbmax * N);
     ALLOC(b.bflux, double, std::max<long long>(1, nb) * N * NV);
     ALLOC(b.ctl, Ctl, 1);
     cudaMemsetAsync(b.bandidx, 0xff, sizeof(int) * nc, c->stream);
@@ -296,6 +303,20 @@ extern "C" msf_status msf_destroy(msf_ctx* c) {
 }
 
 // ---------------------------------------------------------------- stepping
+// kernels one step enqueues (keep in step with enqueue_step)
+static long long count_launches(const msf_ctx* c) {
+  long long n = 0;
+  for (const Inst& in : c->inst) {
+    const Grid& g = in.g;
+    const long long ext = g.ext_sweeps, vel = g.vel_sweeps, re = 2LL * g.reinit_iters;
+    const long long per_stage = 1 + ext + 1 + 1 + 1 + vel + 1 + 1 + 1 + 1 + 1 + 2 + 3;
+    n += 1 + 1 + (2 + g.D) + 2 + 1 + 3 * per_stage + 2 + 1;
+    if (g.scale_sep) n += 2 + 1;
+    if (g.reinit) n += re + 1;
+  }
+  return n;
+}
+
 static msf_status enqueue_step(msf_ctx* c) {
   const cudaStream_t s = c->stream;
   for (Inst& in : c->inst) {
@@ -341,7 +362,6 @@ static msf_status enqueue_step(msf_ctx* c) {
       if (prof) cudaEventRecord(c->ev[2 * st + 1], s);
       launch_ledger(g, b, in.nbnd, LW[st], s);
       launch_levelset(g, b, V[vc], BETA[st], 1.0 - BETA[st], nb, s);
-      launch_scatter_phichi(g, b, nb, s);
       launch_bc_phichi(g, b, s);
       launch_geometry(g, b, Qo, nullptr, nb, s);
       launch_mix(g, b, Qo, nb, s);
@@ -357,15 +377,7 @@ static msf_status enqueue_step(msf_ctx* c) {
     }
   }
   // kernels enqueued above (keep in step with the sequence)
-  long long n = 0;
-  for (Inst& in : c->inst) {
-    const Grid& g = in.g;
-    const long long per_stage = 1 + g.ext_sweeps + 1 + 1 + 1 + g.vel_sweeps + 1 + 1 + 1 + 1 + 1 + 1 + 3;
-    n += 1 + 1 + (2 + g.D) + 1 + 1 + 3 * per_stage + 2 + 1;
-    if (g.scale_sep) n += 2 + 1;
-    if (g.reinit) n += 2LL * g.reinit_iters + 1;
-  }
-  c->launches = n;
+  c->launches = count_launches(c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(c, MSF_ECUDA, std::string("step launch: ") + cudaGetErrorString(e));
   return MSF_OK;
@@ -652,20 +664,7 @@ extern "C" msf_status msf_debug_field(msf_ctx* c, int32_t i, int32_t which, doub
 
 extern "C" msf_status msf_launches_per_step(msf_ctx* c, int64_t* n) {
   if (!c || !n) return MSF_EINVAL;
-  if (!c->launches) {
-    // count without launching: the formula of enqueue_step
-    long long k = 0;
-    for (Inst& in : c->inst) {
-      const Grid& g = in.g;
-      const long long per_stage = 1 + g.ext_sweeps + 1 + 1 + 1 + g.vel_sweeps + 1 + 1 + 1 + 1 + 1 + 1 + 3;
-      k += 1 + 1 + (2 + g.D) + 1 + 1 + 3 * per_stage + 2 + 1;
-      if (g.scale_sep) k += 2 + 1;
-      if (g.reinit) k += 2LL * g.reinit_iters + 1;
-    }
-    *n = k;
-    return MSF_OK;
-  }
-  *n = c->launches;
+  *n = count_launches(c);
   return MSF_OK;
 }
 

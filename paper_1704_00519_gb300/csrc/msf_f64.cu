@@ -22,7 +22,7 @@ static int grid_blocks(long long n) {
 }
 
 // ------------------------------------------------------------ start-up
-__global__ void k_init_levelset(Grid g, Bufs b, const double* phi_in, const int32_t* chi_in) {
+__global__ void k_init_levelset(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* phi_in, const int32_t* chi_in) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.n_interior;
        idx += (long long)gridDim.x * blockDim.x) {
     const long long c = interior_cell(g, idx);
@@ -32,7 +32,7 @@ __global__ void k_init_levelset(Grid g, Bufs b, const double* phi_in, const int3
     b.chi[c] = (uint8_t)chi_in[idx];
   }
 }
-__global__ void k_init_mass(Grid g, Bufs b, const double* prim, double* mass) {
+__global__ void k_init_mass(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* prim, double* mass) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.n_interior;
        idx += (long long)gridDim.x * blockDim.x) {
     const long long c = interior_cell(g, idx);
@@ -40,7 +40,7 @@ __global__ void k_init_mass(Grid g, Bufs b, const double* prim, double* mass) {
       mass[qidx(g, m, 0, c)] = alpha_of(g, b, c, m) * prim[((long long)m * g.NV) * g.n_interior + idx];
   }
 }
-__global__ void k_init_state(Grid g, Bufs b, const double* prim) {
+__global__ void k_init_state(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* prim) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.n_interior;
        idx += (long long)gridDim.x * blockDim.x) {
     const long long c = interior_cell(g, idx);
@@ -53,7 +53,7 @@ __global__ void k_init_state(Grid g, Bufs b, const double* prim) {
     }
   }
 }
-__global__ void k_check_inputs(Grid g, const double* phi, const int32_t* chi, const double* prim, unsigned* flag) {
+__global__ void k_check_inputs(const __grid_constant__ Grid g, const double* phi, const int32_t* chi, const double* prim, unsigned* flag) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.n_interior;
        idx += (long long)gridDim.x * blockDim.x) {
     unsigned f = 0;
@@ -77,7 +77,7 @@ __global__ void k_check_inputs(Grid g, const double* phi, const int32_t* chi, co
 }
 
 // -------------------------------------------------------- state transfer
-__global__ void k_gather(Grid g, Bufs b, int which, double* out, int32_t* iout) {
+__global__ void k_gather(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, int which, double* out, int32_t* iout) {
   const int N = g.N, NV = g.NV;
   const long long ni = g.n_interior;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < ni;
@@ -117,7 +117,7 @@ __global__ void k_gather(Grid g, Bufs b, int which, double* out, int32_t* iout) 
 // stencil state of the last stage: band cells from Uh, bulk cells from the
 // stage's Q (the material of the cell) or NaN
 template <typename T>
-__global__ void k_gather_uh(Grid g, Bufs b, const double* Qs, double* out) {
+__global__ void k_gather_uh(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs, double* out) {
   const int N = g.N, NV = g.NV;
   const long long ni = g.n_interior;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < ni;
@@ -130,7 +130,7 @@ __global__ void k_gather_uh(Grid g, Bufs b, const double* Qs, double* out) {
     }
   }
 }
-__global__ void k_gather_vel(Grid g, Bufs b, const double* vel, double* out) {
+__global__ void k_gather_vel(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* vel, double* out) {
   const long long ni = g.n_interior;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < ni;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -138,7 +138,7 @@ __global__ void k_gather_vel(Grid g, Bufs b, const double* vel, double* out) {
     for (int d = 0; d < 3; d++) out[d * ni + idx] = (b.bandidx[c] >= 0 && d < g.D) ? vel[d * g.ncell + c] : 0.0;
   }
 }
-__global__ void k_scatter_state(Grid g, Bufs b, const double* Q, const double* phi, const int32_t* chi) {
+__global__ void k_scatter_state(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Q, const double* phi, const int32_t* chi) {
   const long long ni = g.n_interior;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < ni;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -171,39 +171,41 @@ void launch_masks(const Grid& g, const Bufs& b, cudaStream_t s) {
   k_band<<<nb, NTHREADS, 0, s>>>(g, b, src);
 }
 void launch_geometry(const Grid& g, const Bufs& b, const double* Qs, const double* mass, int nblk, cudaStream_t s) {
-  k_geometry<<<nblk, NTHREADS, 0, s>>>(g, b, Qs, mass);
+  k_geom_mat<<<nblk, BAND_THREADS, 0, s>>>(g, b);
+  k_geom_cell<<<nblk, BAND_THREADS, 0, s>>>(g, b, Qs, mass);
 }
 void launch_band_save(const Grid& g, const Bufs& b, int nblk, cudaStream_t s) {
-  k_band_save<<<nblk, NTHREADS, 0, s>>>(g, b);
+  k_band_save<<<nblk, BAND_THREADS, 0, s>>>(g, b);
 }
 void launch_dt_finalize(const Grid& g, const Bufs& b, cudaStream_t s) { k_dt_finalize<<<1, 1, 0, s>>>(g, b); }
 void launch_step_end(const Bufs& b, cudaStream_t s) { k_step_end<<<1, 1, 0, s>>>(b); }
 void launch_extend_vel(const Grid& g, const Bufs& b, const double* vin, double* vout, const uint8_t* fin,
                        uint8_t* fout, int nblk, cudaStream_t s) {
-  k_extend_vel<<<nblk, NTHREADS, 0, s>>>(g, b, vin, vout, fin, fout);
+  k_extend_vel<<<nblk, BAND_THREADS, 0, s>>>(g, b, vin, vout, fin, fout);
 }
 void launch_ledger(const Grid& g, const Bufs& b, int nbnd, double w, cudaStream_t s) {
   k_ledger<<<g.N * g.NV, NTHREADS, 0, s>>>(g, b, nbnd, w);
 }
 void launch_levelset(const Grid& g, const Bufs& b, const double* vel, double beta, double omb, int nblk,
                      cudaStream_t s) {
-  k_levelset<<<nblk, NTHREADS, 0, s>>>(g, b, vel, beta, omb);
+  k_levelset<<<nblk, BAND_THREADS, 0, s>>>(g, b, vel, beta, omb);
+  k_levelset_R<<<nblk, BAND_THREADS, 0, s>>>(g, b);
 }
 void launch_scatter_phichi(const Grid& g, const Bufs& b, int nblk, cudaStream_t s) {
-  k_scatter_phichi<<<nblk, NTHREADS, 0, s>>>(g, b);
+  k_scatter_phichi<<<nblk, BAND_THREADS, 0, s>>>(g, b);
 }
 void launch_mix(const Grid& g, const Bufs& b, double* Qc, int nblk, cudaStream_t s) {
-  k_mix_mark<<<nblk, NTHREADS, 0, s>>>(g, b, Qc);
-  k_mix_compute<<<nblk, NTHREADS, 0, s>>>(g, b, Qc);
-  k_mix_scatter<<<nblk, NTHREADS, 0, s>>>(g, b, Qc);
+  k_mix_mark<<<nblk, BAND_THREADS, 0, s>>>(g, b, Qc);
+  k_mix_compute<<<nblk, BAND_THREADS, 0, s>>>(g, b, Qc);
+  k_mix_scatter<<<nblk, BAND_THREADS, 0, s>>>(g, b, Qc);
 }
 void launch_scale_sep(const Grid& g, const Bufs& b, int nblk, cudaStream_t s) {
-  k_scale_sep<<<nblk, NTHREADS, 0, s>>>(g, b);
-  k_scatter_phichi<<<nblk, NTHREADS, 0, s>>>(g, b);
+  k_scale_sep<<<nblk, BAND_THREADS, 0, s>>>(g, b);
+  k_scatter_phichi<<<nblk, BAND_THREADS, 0, s>>>(g, b);
 }
 void launch_reinit(const Grid& g, const Bufs& b, int nblk, cudaStream_t s) {
-  k_reinit<<<nblk, NTHREADS, 0, s>>>(g, b);
-  k_scatter_phichi<<<nblk, NTHREADS, 0, s>>>(g, b);
+  k_reinit<<<nblk, BAND_THREADS, 0, s>>>(g, b);
+  k_scatter_phichi<<<nblk, BAND_THREADS, 0, s>>>(g, b);
 }
 void launch_totals(const Grid& g, const double* Q, double* out, cudaStream_t s) {
   k_totals<<<g.N * g.NV, NTHREADS, 0, s>>>(g, Q, out);

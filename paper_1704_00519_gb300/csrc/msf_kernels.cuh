@@ -69,7 +69,7 @@ __device__ inline void halo_coords(const Grid& g, long long idx_, int* q) {
 }
 
 // halo cells of phi, chi: every out-of-range axis mapped to its boundary source
-__global__ void k_bc_phichi(Grid g, Bufs b) {
+__global__ void k_bc_phichi(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
   long long nh = halo_count(g);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nh;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -86,7 +86,7 @@ __global__ void k_bc_phichi(Grid g, Bufs b) {
 
 // -------------------------------------------------- step masks and the band
 // xs = material bits of the 3^d block (clamped to the array)
-__global__ void k_xs(Grid g, Bufs b) {
+__global__ void k_xs(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
   if (!ctl_active(b)) return;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
        c += (long long)gridDim.x * blockDim.x) {
@@ -103,7 +103,7 @@ __global__ void k_xs(Grid g, Bufs b) {
   }
 }
 // OR-dilation by +-4 along axis d (separable box of the step mask)
-__global__ void k_dilate(Grid g, Bufs b, const uint8_t* src, uint8_t* dst, int d) {
+__global__ void k_dilate(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const uint8_t* src, uint8_t* dst, int d) {
   if (!ctl_active(b)) return;
   const int R = 4;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
@@ -120,7 +120,7 @@ __global__ void k_dilate(Grid g, Bufs b, const uint8_t* src, uint8_t* dst, int d
   }
 }
 // final step mask on interior cells, band compaction, per-step resets
-__global__ void k_band(Grid g, Bufs b, const uint8_t* dil) {
+__global__ void k_band(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const uint8_t* dil) {
   if (!ctl_active(b)) return;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
        c += (long long)gridDim.x * blockDim.x) {
@@ -129,7 +129,6 @@ __global__ void k_band(Grid g, Bufs b, const uint8_t* dil) {
     if (inner) m = dil[c];
     b.smask[c] = m;
     b.gflag[c] = 0;
-    b.small[c] = 0;
     int bi = -1;
     if (inner && popcount8(m) >= 2) {
       bi = atomicAdd(&b.ctl->nband, 1);
@@ -140,7 +139,7 @@ __global__ void k_band(Grid g, Bufs b, const uint8_t* dil) {
 }
 
 // step start: activity flag, band counter reset
-__global__ void k_step_begin(Bufs b) {
+__global__ void k_step_begin(const __grid_constant__ Bufs b) {
   Ctl* t = b.ctl;
   t->active = (t->t < t->t_end && t->err == 0) ? 1 : 0;
   t->nband = 0;
@@ -148,7 +147,7 @@ __global__ void k_step_begin(Bufs b) {
 }
 
 // save phi^n, chi^n of band cells (used pointwise by the level-set RK stages)
-__global__ void k_band_save(Grid g, Bufs b) {
+__global__ void k_band_save(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
   if (!ctl_active(b)) return;
   const int nb = b.ctl->nband;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
@@ -159,8 +158,54 @@ __global__ void k_band_save(Grid g, Bufs b) {
 }
 
 // --------------------------------------------- geometry + correction (a3, a4)
-// Qs == nullptr: raw volume fractions (start-up), no correction
-__global__ void k_geometry(Grid g, Bufs b, const double* Qs, const double* mass) {
+__device__ inline unsigned block_bits(const Grid& g, const uint8_t* chi, const int* q) {
+  unsigned bits = 0;
+  const int rz = g.D >= 3 ? 1 : 0, ry = g.D >= 2 ? 1 : 0;
+  for (int dz = -rz; dz <= rz; dz++)
+    for (int dy = -ry; dy <= ry; dy++)
+      for (int dx = -1; dx <= 1; dx++)
+        if (in_array(g, q[0] + dx, q[1] + dy, q[2] + dz)) bits |= 1u << chi[cell_at(g, q[0] + dx, q[1] + dy, q[2] + dz)];
+  return bits;
+}
+
+// per (band cell, material): unit normal of phi^m for the materials the cell
+// carries this step, volume fraction and raw face apertures
+__global__ void k_geom_mat(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, N = g.N, D = g.D;
+  const int total = nb * N;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int m = it / nb, k = it - m * nb;
+    const long long c = b.band[k];
+    int q[3];
+    coords(g, c, q);
+    const unsigned bits = block_bits(g, b.chi, q);
+    if ((b.smask[c] >> m) & 1u) {
+      double n[3];
+      normal_m(g, b.phi, b.chi, c, m, n);
+      for (int d = 0; d < 3; d++) b.nrm[((long long)m * 3 + d) * g.ncell + c] = n[d];
+    }
+    double a = 0.0, alo[3] = {0, 0, 0}, ahi[3] = {0, 0, 0};
+    if (popcount8(bits) < 2) {
+      if (b.chi[c] == m) {
+        a = 1.0;
+        for (int d = 0; d < D; d++) alo[d] = ahi[d] = 1.0;
+      }
+    } else if ((bits >> m) & 1u) {
+      cell_geom(g, b.phi, b.chi, c, m, &a, alo, ahi);
+    }
+    b.alpha[midx(g, m, c)] = a;
+    for (int d = 0; d < D; d++) {
+      b.Alo[aidx(g, d, m, c)] = alo[d];
+      b.Ahi[aidx(g, d, m, c)] = ahi[d];
+    }
+  }
+}
+
+// per band cell: flags, partition of each face among the local materials and
+// the conservation correction (Sec. 2.3.1, Eq. vol_corr2).
+// Qs == nullptr and mass == nullptr: raw volume fractions (start-up)
+__global__ void k_geom_cell(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs, const double* mass) {
   if (!ctl_active(b)) return;
   const int nb = b.ctl->nband;
   const int N = g.N, D = g.D;
@@ -169,36 +214,13 @@ __global__ void k_geometry(Grid g, Bufs b, const double* Qs, const double* mass)
     const long long c = b.band[k];
     int q[3];
     coords(g, c, q);
-    unsigned bits = 0;
-    const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
-    for (int dz = -rz; dz <= rz; dz++)
-      for (int dy = -ry; dy <= ry; dy++)
-        for (int dx = -1; dx <= 1; dx++)
-          if (in_array(g, q[0] + dx, q[1] + dy, q[2] + dz))
-            bits |= 1u << b.chi[cell_at(g, q[0] + dx, q[1] + dy, q[2] + dz)];
+    const unsigned bits = block_bits(g, b.chi, q);
     b.xsS[c] = (uint8_t)bits;
-    for (int m = 0; m < N; m++) {
-      b.alpha[midx(g, m, c)] = 0.0;
-      for (int d = 0; d < D; d++) b.Alo[aidx(g, d, m, c)] = b.Ahi[aidx(g, d, m, c)] = 0.0;
-    }
     if (popcount8(bits) < 2) {
-      const int m = b.chi[c];
-      b.alpha[midx(g, m, c)] = 1.0;
-      for (int d = 0; d < D; d++) b.Alo[aidx(g, d, m, c)] = b.Ahi[aidx(g, d, m, c)] = 1.0;
       b.gflag[c] = 0;
       continue;
     }
     b.gflag[c] = GF_MIXED;
-    for (int m = 0; m < N; m++) {
-      if (!((bits >> m) & 1u)) continue;
-      double a, alo[3] = {0, 0, 0}, ahi[3] = {0, 0, 0};
-      cell_geom(g, b.phi, b.chi, c, m, &a, alo, ahi);
-      b.alpha[midx(g, m, c)] = a;
-      for (int d = 0; d < D; d++) {
-        b.Alo[aidx(g, d, m, c)] = alo[d];
-        b.Ahi[aidx(g, d, m, c)] = ahi[d];
-      }
-    }
     // the materials partition every face
     for (int d = 0; d < D; d++)
       for (int side = 0; side < 2; side++) {
@@ -210,7 +232,6 @@ __global__ void k_geometry(Grid g, Bufs b, const double* Qs, const double* mass)
           for (int m = 0; m < N; m++)
             if ((bits >> m) & 1u) A[aidx(g, d, m, c)] = A[aidx(g, d, m, c)] / s;
       }
-    // conservation correction (Sec. 2.3.1, Eq. vol_corr2)
     const double* Mref = Qs ? Qs : mass;
     if (!Mref) continue;
     int np = 0;
@@ -248,6 +269,11 @@ __global__ void k_geometry(Grid g, Bufs b, const double* Qs, const double* mass)
   }
 }
 
+// stored unit normal of material m at a band cell (written by k_geom_mat)
+__device__ inline void stored_normal(const Grid& g, const Bufs& b, long long c, int m, double* n) {
+  for (int d = 0; d < 3; d++) n[d] = b.nrm[((long long)m * 3 + d) * g.ncell + c];
+}
+
 // interior test of the face neighbour of a cell with coordinates q (side 0: -e_d)
 __device__ inline bool nb_interior(const Grid& g, const int* q, int d, int side) {
   const int p = q[d] + (side ? 1 : -1);
@@ -278,7 +304,7 @@ __device__ inline double alpha_of(const Grid& g, const Bufs& b, long long c, int
 
 // -------------------------------------- primitive recovery + ghosts (a5, a6)
 template <typename T>
-__global__ void k_prim(Grid g, Bufs b, const double* Qs) {
+__global__ void k_prim(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
   if (!ctl_active(b)) return;
   const int nb = b.ctl->nband, N = g.N, NV = g.NV;
   T* W0 = (T*)b.W0;
@@ -293,7 +319,7 @@ __global__ void k_prim(Grid g, Bufs b, const double* Qs) {
     const double a = b.alpha[midx(g, m, c)];
     if (b.chi[c] == m && a > 0.0) {
       T u[5], w[5];
-      for (int v = 0; v < NV; v++) u[v] = (T)(Qs[qidx(g, m, v, c)] / a);
+      for (int v = 0; v < NV; v++) u[v] = (T)Qs[qidx(g, m, v, c)] / (T)a;
       cons_to_prim<T>(g, m, g.D, u, w);
       for (int v = 0; v < NV; v++) W0[qidx(g, m, v, c)] = W1[qidx(g, m, v, c)] = w[v];
       b.f0[midx(g, m, c)] = 1;
@@ -305,13 +331,13 @@ __global__ void k_prim(Grid g, Bufs b, const double* Qs) {
 // one Jacobi sweep: targets take the upwind-weighted mean of filled face
 // neighbours (weights max(0, n . e)), else the plain mean of filled neighbours
 template <typename T>
-__global__ void k_extend(Grid g, Bufs b, const void* Win, void* Wout, const uint8_t* fin, uint8_t* fout) {
-  if (!ctl_active(b)) return;
+__device__ __forceinline__ void extend_items(const Grid& g, const Bufs& b, const void* Win, void* Wout,
+                                             const uint8_t* fin, uint8_t* fout, int first, int stride) {
   const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
   const T* Wi = (const T*)Win;
   T* Wo = (T*)Wout;
   const int total = nb * N;
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+  for (int it = first; it < total; it += stride) {
     const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
     if (!((b.smask[c] >> m) & 1u)) continue;
@@ -322,7 +348,7 @@ __global__ void k_extend(Grid g, Bufs b, const void* Win, void* Wout, const uint
     int q[3];
     coords(g, c, q);
     double n[3];
-    normal_m(g, b.phi, b.chi, c, m, n);
+    stored_normal(g, b, c, m, n);
     T acc[5] = {T(0), T(0), T(0), T(0), T(0)}, acc2[5] = {T(0), T(0), T(0), T(0), T(0)};
     T sw = T(0);
     int cnt = 0;
@@ -354,9 +380,18 @@ __global__ void k_extend(Grid g, Bufs b, const void* Win, void* Wout, const uint
   }
 }
 
+// one Jacobi sweep: targets take the upwind-weighted mean of filled face
+// neighbours (weights max(0, n . e)), else the plain mean of filled neighbours
+template <typename T>
+__global__ void k_extend(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const void* Win,
+                         void* Wout, const uint8_t* fin, uint8_t* fout) {
+  if (!ctl_active(b)) return;
+  extend_items<T>(g, b, Win, Wout, fin, fout, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
 // stencil state of band cells: real Q/alpha, ghost cons(W), else NaN
 template <typename T>
-__global__ void k_cons(Grid g, Bufs b, const double* Qs, const void* Wfin, const uint8_t* ffin) {
+__global__ void k_cons(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs, const void* Wfin, const uint8_t* ffin) {
   if (!ctl_active(b)) return;
   const int nb = b.ctl->nband, N = g.N, NV = g.NV;
   const T* W = (const T*)Wfin;
@@ -372,7 +407,7 @@ __global__ void k_cons(Grid g, Bufs b, const double* Qs, const void* Wfin, const
         for (int v = 0; v < NV; v++) u[v] = nanv;
       } else if (b.isreal[midx(g, m, c)]) {
         const double a = b.alpha[midx(g, m, c)];
-        for (int v = 0; v < NV; v++) u[v] = (T)(Qs[qidx(g, m, v, c)] / a);
+        for (int v = 0; v < NV; v++) u[v] = (T)Qs[qidx(g, m, v, c)] / (T)a;
       } else if (ffin[midx(g, m, c)]) {
         T w[5];
         for (int v = 0; v < NV; v++) w[v] = W[qidx(g, m, v, c)];
@@ -387,7 +422,7 @@ __global__ void k_cons(Grid g, Bufs b, const double* Qs, const void* Wfin, const
 
 // stencil state of an interior cell (bulk: Q; band: Uh; otherwise NaN)
 template <typename T>
-__device__ inline void interior_uhat(const Grid& g, const Bufs& b, const double* Qs, long long c, int m, T* u) {
+__device__ __forceinline__ void interior_uhat(const Grid& g, const Bufs& b, const double* Qs, long long c, int m, T* u) {
   const T nanv = (T)__longlong_as_double(0x7ff8000000000000LL);
   const T* Uh = (const T*)b.Uh;
   if (b.bandidx[c] >= 0) {
@@ -404,7 +439,7 @@ __device__ inline void interior_uhat(const Grid& g, const Bufs& b, const double*
 
 // halo cells of the stencil state (one axis out of range at a time)
 template <typename T>
-__global__ void k_bc_uhat(Grid g, Bufs b, const double* Qs) {
+__global__ void k_bc_uhat(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
   if (!ctl_active(b)) return;
   const int N = g.N, NV = g.NV, D = g.D;
   long long per[3] = {0, 0, 0}, total = 0;
@@ -454,7 +489,7 @@ __global__ void k_bc_uhat(Grid g, Bufs b, const double* Qs) {
 
 // ----------------------------------------------------------- CFL step (a2)
 template <typename T>
-__global__ void k_dt(Grid g, Bufs b, const double* Qs) {
+__global__ void k_dt(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
   if (!ctl_active(b)) return;
   const int N = g.N, D = g.D;
   double lam = 0.0;
@@ -485,7 +520,7 @@ __global__ void k_dt(Grid g, Bufs b, const double* Qs) {
   if (threadIdx.x == 0) atomic_max_pos_double(&b.ctl->lam_bits, red[0]);
   if (err) atomicOr(&b.ctl->err, err);
 }
-__global__ void k_dt_finalize(Grid g, Bufs b) {
+__global__ void k_dt_finalize(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
   Ctl* t = b.ctl;
   if (!t->active) return;
   const double lam = __longlong_as_double((long long)t->lam_bits);
@@ -499,7 +534,7 @@ __global__ void k_dt_finalize(Grid g, Bufs b) {
   t->dt = dt;
   t->last = last;
 }
-__global__ void k_step_end(Bufs b) {
+__global__ void k_step_end(const __grid_constant__ Bufs b) {
   Ctl* t = b.ctl;
   if (!t->active) return;
   t->t = t->last ? t->t_end : t->t + t->dt;
@@ -508,7 +543,7 @@ __global__ void k_step_end(Bufs b) {
 
 // ----------------------------------------- reduced interface interaction (a7)
 template <typename T>
-__global__ void k_interface(Grid g, Bufs b, const double* Qs) {
+__global__ void k_interface(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
   if (!ctl_active(b)) return;
   const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
   const T* Uh = (const T*)b.Uh;
@@ -535,7 +570,7 @@ __global__ void k_interface(Grid g, Bufs b, const double* Qs) {
     if (Qs[qidx(g, xi, 0, c)] < Qs[qidx(g, eta, 0, c)]) { L = xi; R = eta; }
     else { L = eta; R = xi; }
     double n[3];
-    normal_m(g, b.phi, b.chi, c, R, n);
+    stored_normal(g, b, c, R, n);
     T uL[5], uR[5], wL[5], wR[5];
     for (int v = 0; v < NV; v++) {
       uL[v] = Uh[qidx(g, L, v, c)];
@@ -579,10 +614,10 @@ __global__ void k_interface(Grid g, Bufs b, const double* Qs) {
 }
 
 // one sweep of the interface-velocity extension into the band
-__global__ void k_extend_vel(Grid g, Bufs b, const double* vin, double* vout, const uint8_t* fin, uint8_t* fout) {
-  if (!ctl_active(b)) return;
+__device__ __forceinline__ void extend_vel_items(const Grid& g, const Bufs& b, const double* vin, double* vout,
+                                                 const uint8_t* fin, uint8_t* fout, int first, int stride) {
   const int nb = b.ctl->nband, D = g.D;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+  for (int k = first; k < nb; k += stride) {
     const long long c = b.band[k];
     if (b.gflag[c] & GF_CUT) {
       for (int e = 0; e < 3; e++) vout[e * g.ncell + c] = vin[e * g.ncell + c];
@@ -619,7 +654,11 @@ __global__ void k_extend_vel(Grid g, Bufs b, const double* vin, double* vout, co
     fout[c] = filled;
   }
 }
-
+__global__ void k_extend_vel(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* vin,
+                             double* vout, const uint8_t* fin, uint8_t* fout) {
+  if (!ctl_active(b)) return;
+  extend_vel_items(g, b, vin, vout, fin, fout, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
 // --------------------------------------- fluxes and the RK stage update (a8)
 // One CTA owns a tile of interior cells. For each material of the tile it
 // stages the stencil state (tile + 3-cell halo) and its primitive quantities
@@ -656,20 +695,31 @@ __device__ inline void face_flux_smem(const T* U, const T* P, int s0, int sstrid
   // U[v*NS + s], P[e*NS + s] with e: 0..D-1 velocities, D pressure, D+1 sound speed
   constexpr int NV = D + 2;
   T a = T(0);
+#pragma unroll
   for (int q = 0; q < 6; q++) {
     const int s = s0 + (q - 2) * sstride;
     const T sp = fabs(P[d * NS + s]) + P[(D + 1) * NS + s];
     if (sp > a) a = sp;
   }
+  T un[6], pr[6], mom[6];
+#pragma unroll
+  for (int q = 0; q < 6; q++) {
+    const int s = s0 + (q - 2) * sstride;
+    un[q] = P[d * NS + s];
+    pr[q] = P[D * NS + s];
+    mom[q] = U[(1 + d) * NS + s];
+  }
+#pragma unroll
   for (int v = 0; v < NV; v++) {
     T fp[6], fm[6];
+#pragma unroll
     for (int q = 0; q < 6; q++) {
       const int s = s0 + (q - 2) * sstride;
-      const T un = P[d * NS + s], p = P[D * NS + s], uu = U[v * NS + s];
+      const T uu = U[v * NS + s];
       T F;
-      if (v == 0) F = U[(1 + d) * NS + s];
-      else if (v == NV - 1) F = un * (uu + p);
-      else F = (v - 1 == d) ? uu * un + p : uu * un;
+      if (v == 0) F = mom[q];
+      else if (v == NV - 1) F = un[q] * (uu + pr[q]);
+      else F = (v - 1 == d) ? uu * un[q] + pr[q] : uu * un[q];
       fp[q] = T(0.5) * (F + a * uu);
       fm[q] = T(0.5) * (F - a * uu);
     }
@@ -677,10 +727,85 @@ __device__ inline void face_flux_smem(const T* U, const T* P, int s0, int sstrid
   }
 }
 
+// one face of a flux tile: aperture, WENO5-LLF flux and the boundary ledger.
+// DIR is the face normal axis; r indexes the faces of that axis in the tile.
+template <int D, typename T, int DIR>
+__device__ inline void flux_face(const Grid& g, const Bufs& b, const T* U, const T* P, T* F, double* A,
+                                 const uint8_t* bad, const BndBase& bb, int f, int r, int x0, int y0, int z0, int m,
+                                 bool anyband, T eps, unsigned& err) {
+  using S = FluxSmem<D, T>;
+  constexpr int NV = D + 2, TX = S::TX, TY = S::TY, SX = S::SX, SY = S::SY, NS = S::NS;
+  int fx, fy, fz;
+  if (DIR == 0) {
+    fx = r % (TX + 1); fy = (r / (TX + 1)) % TY; fz = r / ((TX + 1) * TY);
+  } else if (DIR == 1) {
+    fx = r % TX; fy = (r / TX) % (TY + 1); fz = r / (TX * (TY + 1));
+  } else {
+    fx = r % TX; fy = (r / TX) % TY; fz = r / (TX * TY);
+  }
+  // the face is the lower face of tile cell (fx, fy, fz)
+  const int gx = x0 + fx, gy = y0 + fy, gz = z0 + fz;
+  const int qd = DIR == 0 ? gx : (DIR == 1 ? gy : gz);
+  // the face exists when its upper cell lies in [off, off + n] along DIR and
+  // the other coordinates are interior
+  bool exists = gx < g.off[0] + g.n[0] + (DIR == 0 ? 1 : 0);
+  if (D >= 2) exists = exists && gy < g.off[1] + g.n[1] + (DIR == 1 ? 1 : 0);
+  if (D >= 3) exists = exists && gz < g.off[2] + g.n[2] + (DIR == 2 ? 1 : 0);
+  double Af = 0.0;
+  T Fh[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) Fh[v] = T(0);
+  if (exists) {
+    const long long cR = cell_at(g, gx, gy, gz), cL = cR - g.st[DIR];
+    Af = anyband ? face_aperture(g, b, cL, cR, DIR, m) : 1.0;
+    if (Af > 0.0) {
+      if (anyband) {
+        const bool lin = qd - 1 >= g.off[DIR], rin = qd < g.off[DIR] + g.n[DIR];
+        if ((lin && !((b.smask[cL] >> m) & 1u)) || (rin && !((b.smask[cR] >> m) & 1u))) err |= ERR_BAND;
+      }
+      const int sR = (fx + 3) + SX * ((fy + S::HY) + SY * (fz + S::HZ));
+      constexpr int sstride = DIR == 0 ? 1 : (DIR == 1 ? SX : SX * SY);
+      const int sL = sR - sstride;
+      bool avail = true, isbad = false;
+#pragma unroll
+      for (int q = 0; q < 6; q++) {
+        if (isnan(U[sL + (q - 2) * sstride])) avail = false;
+        if (bad[sL + (q - 2) * sstride]) isbad = true;
+      }
+      if (!avail) {
+        err |= ERR_BAND;
+      } else {
+        if (isbad) err |= ERR_NEGATIVE;
+        face_flux_smem<D, T>(U, P, sL, sstride, DIR, NS, eps, Fh);
+      }
+    }
+    // boundary ledger: net inflow through the domain boundary
+    const int rr = qd - g.off[DIR];
+    if (rr == 0 || rr == g.n[DIR]) {
+      // face id: base[DIR][side] + interior index of the other coordinates
+      long long lin_id = 0, mul = 1;
+      const int qv[3] = {gx, gy, gz};
+#pragma unroll
+      for (int e = 0; e < D; e++) {
+        if (e == DIR) continue;
+        lin_id += (long long)(qv[e] - g.off[e]) * mul;
+        mul *= g.n[e];
+      }
+      const long long fid = (rr == 0 ? bb.base[2 * DIR] : bb.base[2 * DIR + 1]) + lin_id;
+      const double sgn = rr == 0 ? 1.0 : -1.0;
+#pragma unroll
+      for (int v = 0; v < NV; v++) b.bflux[((fid * g.N) + m) * NV + v] = sgn * (Af * (double)Fh[v] * g.farea[DIR]);
+    }
+  }
+  A[f] = Af;
+#pragma unroll
+  for (int v = 0; v < NV; v++) F[v * S::NF + f] = Fh[v];
+}
+
 template <int D, typename T>
 __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
-    k_flux_update(Grid g, Bufs b, const double* Qs, const double* Qn, double* Qout, double beta, double omb,
-                  BndBase bb) {
+    k_flux_update(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs,
+                  const double* Qn, double* Qout, double beta, double omb, const __grid_constant__ BndBase bb) {
   using S = FluxSmem<D, T>;
   constexpr int NV = D + 2, TX = S::TX, TY = S::TY, TZ = S::TZ, SX = S::SX, SY = S::SY, NS = S::NS;
   if (!ctl_active(b)) return;
@@ -724,7 +849,7 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
           lin_id += (long long)(qq[e] - g.off[e]) * mul;
           mul *= g.n[e];
         }
-        const long long fid = bb.base[2 * d + side] + lin_id;
+        const long long fid = (side ? bb.base[2 * d + 1] : bb.base[2 * d]) + lin_id;
         for (int mv = 0; mv < g.N * NV; mv++) b.bflux[fid * g.N * NV + mv] = 0.0;
       }
     }
@@ -737,7 +862,9 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
 
   for (int m = 0; m < g.N; m++) {
     if (!((uni >> m) & 1u)) continue;
+    const T mgm1 = T(g.gm1[m]), mgpi = T(g.gpi[m]), mgam = T(g.gamma[m]), mpinf = T(g.pinf[m]);
     // stage the stencil state and its primitive quantities
+#pragma unroll 1
     for (int s = tid; s < NS; s += blockDim.x) {
       const int sx = s % SX, sy = (s / SX) % SY, sz = s / (SX * SY);
       const int gx = x0 - 3 + sx, gy = y0 - S::HY + sy, gz = z0 - S::HZ + sz;
@@ -751,25 +878,43 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
       ok = ok && outs <= 1;
       if (ok) {
         const long long gc = cell_at(g, gx, gy, gz);
-        int qq[3] = {gx, gy, gz};
-        if (interior_q(g, qq)) {
+        bool inner = gx >= g.off[0] && gx < g.off[0] + g.n[0];
+        if (D >= 2) inner = inner && gy >= g.off[1] && gy < g.off[1] + g.n[1];
+        if (D >= 3) inner = inner && gz >= g.off[2] && gz < g.off[2] + g.n[2];
+        if (inner) {
           interior_uhat<T>(g, b, Qs, gc, m, u);
         } else {
           const T* Uh = (const T*)b.Uh;
+#pragma unroll
           for (int v = 0; v < NV; v++) u[v] = Uh[qidx(g, m, v, gc)];
         }
       } else {
+#pragma unroll
         for (int v = 0; v < NV; v++) u[v] = (T)__longlong_as_double(0x7ff8000000000000LL);
       }
+#pragma unroll
       for (int v = 0; v < NV; v++) U[v * NS + s] = u[v];
       bad[s] = 0;
       if (!isnan(u[0])) {
+        // primitive state (same arithmetic as cons_to_prim)
+        const T rho = u[0];
+        T vel[D];
+        T qsum = T(0);
+#pragma unroll
+        for (int e = 0; e < D; e++) vel[e] = u[1 + e] / rho;
+#pragma unroll
+        for (int e = 0; e < D; e++) qsum += vel[e] * vel[e];
+        const T ke = T(0.5) * rho * qsum;
+        const T pres = mgm1 * (u[D + 1] - ke) - mgpi;
+#pragma unroll
+        for (int e = 0; e < D; e++) P[e * NS + s] = vel[e];
+        P[D * NS + s] = pres;
+        T c2 = (mgam * (pres + mpinf)) / rho;
+        const T w0 = rho;
         T w[NV];
-        cons_to_prim<T>(g, m, D, u, w);
-        for (int e = 0; e < D; e++) P[e * NS + s] = w[1 + e];
-        P[D * NS + s] = w[D + 1];
-        T c2 = (T(g.gamma[m]) * (w[D + 1] + T(g.pinf[m]))) / w[0];
-        if (!(w[0] > T(0)) || !(c2 > T(0))) {
+        w[0] = w0;
+        (void)w;
+        if (!(w0 > T(0)) || !(c2 > T(0))) {
           bad[s] = 1;  // reported only if a used face reads it
           c2 = c2 > T(0) ? c2 : T(0);
         }
@@ -779,69 +924,12 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
     __syncthreads();
     // face apertures and fluxes: x faces, then y, then z
     for (int f = tid; f < S::NF; f += blockDim.x) {
-      int d, fx, fy, fz;
-      if (f < S::NFX) {
-        d = 0; fx = f % (TX + 1); fy = (f / (TX + 1)) % TY; fz = f / ((TX + 1) * TY);
-      } else if (f < S::NFX + S::NFY) {
-        int r = f - S::NFX;
-        d = 1; fx = r % TX; fy = (r / TX) % (TY + 1); fz = r / (TX * (TY + 1));
-      } else {
-        int r = f - S::NFX - S::NFY;
-        d = 2; fx = r % TX; fy = (r / TX) % TY; fz = r / (TX * TY);
-      }
-      // the face is the lower face of tile cell (fx, fy, fz)
-      const int gx = x0 + fx, gy = y0 + fy, gz = z0 + fz;
-      int qR[3] = {gx, gy, gz};
-      // the face exists when its upper cell index lies in [off, off + n] along d
-      // and the other coordinates are interior
-      bool exists = true;
-      for (int e = 0; e < D; e++) {
-        const int lim = g.off[e] + g.n[e] + (e == d ? 1 : 0);
-        if (qR[e] >= lim) exists = false;
-      }
-      double Af = 0.0;
-      T Fh[NV];
-      for (int v = 0; v < NV; v++) Fh[v] = T(0);
-      if (exists) {
-        const long long cR = cell_at(g, gx, gy, gz), cL = cR - g.st[d];
-        Af = anyband ? face_aperture(g, b, cL, cR, d, m) : 1.0;
-        if (Af > 0.0) {
-          if (anyband) {
-            const bool lin = qR[d] - 1 >= g.off[d], rin = qR[d] < g.off[d] + g.n[d];
-            if ((lin && !((b.smask[cL] >> m) & 1u)) || (rin && !((b.smask[cR] >> m) & 1u))) err |= ERR_BAND;
-          }
-          const int sR = (fx + 3) + SX * ((fy + S::HY) + SY * (fz + S::HZ));
-          const int sstride = d == 0 ? 1 : (d == 1 ? SX : SX * SY);
-          const int sL = sR - sstride;
-          bool avail = true, isbad = false;
-          for (int q = 0; q < 6; q++) {
-            if (isnan(U[sL + (q - 2) * sstride])) avail = false;
-            if (bad[sL + (q - 2) * sstride]) isbad = true;
-          }
-          if (!avail) {
-            err |= ERR_BAND;
-          } else {
-            if (isbad) err |= ERR_NEGATIVE;
-            face_flux_smem<D, T>(U, P, sL, sstride, d, NS, eps, Fh);
-          }
-        }
-        // boundary ledger: net inflow through the domain boundary
-        const int r = qR[d] - g.off[d];
-        if (r == 0 || r == g.n[d]) {
-          // face id: base[d][side] + interior index of the other coordinates
-          long long lin_id = 0, mul = 1;
-          for (int e = 0; e < D; e++) {
-            if (e == d) continue;
-            lin_id += (long long)(qR[e] - g.off[e]) * mul;
-            mul *= g.n[e];
-          }
-          const long long fid = bb.base[2 * d + (r == 0 ? 0 : 1)] + lin_id;
-          const double sgn = r == 0 ? 1.0 : -1.0;
-          for (int v = 0; v < NV; v++) b.bflux[((fid * g.N) + m) * NV + v] = sgn * (Af * (double)Fh[v] * g.farea[d]);
-        }
-      }
-      A[f] = Af;
-      for (int v = 0; v < NV; v++) F[v * S::NF + f] = Fh[v];
+      if (f < S::NFX)
+        flux_face<D, T, 0>(g, b, U, P, F, A, bad, bb, f, f, x0, y0, z0, m, anyband, eps, err);
+      else if (D >= 2 && f < S::NFX + S::NFY)
+        flux_face<D, T, 1>(g, b, U, P, F, A, bad, bb, f, f - S::NFX, x0, y0, z0, m, anyband, eps, err);
+      else if (D >= 3)
+        flux_face<D, T, 2>(g, b, U, P, F, A, bad, bb, f, f - S::NFX - S::NFY, x0, y0, z0, m, anyband, eps, err);
     }
     __syncthreads();
     // cell update
@@ -858,8 +946,10 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
         flo[2] = S::NFX + S::NFY + tx + TX * (ty + TY * tz);
         fhi[2] = flo[2] + TX * TY;
       }
+#pragma unroll
       for (int v = 0; v < NV; v++) {
         double L = 0.0;
+#pragma unroll
         for (int d = 0; d < D; d++) {
           const double fl = (double)F[v * S::NF + flo[d]], fh = (double)F[v * S::NF + fhi[d]];
           L = L + (A[flo[d]] * fl - A[fhi[d]] * fh) * g.rh[d];
@@ -881,7 +971,7 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
 
 // sum the boundary-face fluxes of the stage (one block per material and
 // variable, fixed-order tree reduction) and add them to the ledger
-__global__ void k_ledger(Grid g, Bufs b, int nbnd, double w) {
+__global__ void k_ledger(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, int nbnd, double w) {
   if (!ctl_active(b)) return;
   const int NMV = g.N * g.NV, mv = blockIdx.x;
   double s = 0.0;
@@ -899,10 +989,47 @@ __global__ void k_ledger(Grid g, Bufs b, int nbnd, double w) {
 // --------------------------------------------- level-set stage (a9) + R
 __device__ inline double phir_stage(const Bufs& b, long long c, int r) { return phi_m(b.phi, b.chi, c, r); }
 
-__global__ void k_levelset(Grid g, Bufs b, const double* vel, double beta, double omb) {
+__global__ void k_levelset(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* vel, double beta, double omb) {
   if (!ctl_active(b)) return;
   const int nb = b.ctl->nband, N = g.N, D = g.D;
   const double dt = b.ctl->dt, eps = g.weno_eps;
+  const int total = nb * N;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int r = it / nb, k = it - r * nb;
+    const long long c = b.band[k];
+    if (!((b.xsS[c] >> r) & 1u)) continue;
+    double adv = 0.0;
+    for (int d = 0; d < D; d++) {
+      const double vd = vel[d * g.ncell + c];
+      if (vd == 0.0) continue;
+      const long long st = g.st[d];
+      const double rh = g.rh[d];
+      double gd;
+      if (vd > 0.0) {
+        double v1 = (phir_stage(b, c - 2 * st, r) - phir_stage(b, c - 3 * st, r)) * rh;
+        double v2 = (phir_stage(b, c - st, r) - phir_stage(b, c - 2 * st, r)) * rh;
+        double v3 = (phir_stage(b, c, r) - phir_stage(b, c - st, r)) * rh;
+        double v4 = (phir_stage(b, c + st, r) - phir_stage(b, c, r)) * rh;
+        double v5 = (phir_stage(b, c + 2 * st, r) - phir_stage(b, c + st, r)) * rh;
+        gd = weno5<double>(v1, v2, v3, v4, v5, eps);
+      } else {
+        double v1 = (phir_stage(b, c + 3 * st, r) - phir_stage(b, c + 2 * st, r)) * rh;
+        double v2 = (phir_stage(b, c + 2 * st, r) - phir_stage(b, c + st, r)) * rh;
+        double v3 = (phir_stage(b, c + st, r) - phir_stage(b, c, r)) * rh;
+        double v4 = (phir_stage(b, c, r) - phir_stage(b, c - st, r)) * rh;
+        double v5 = (phir_stage(b, c - st, r) - phir_stage(b, c - 2 * st, r)) * rh;
+        gd = weno5<double>(v1, v2, v3, v4, v5, eps);
+      }
+      adv = adv + vd * gd;
+    }
+    const double phn = b.chin[c] == r ? b.phin[c] : -b.phin[c];
+    b.phir[(long long)k * N + r] = beta * phn + omb * (phir_stage(b, c, r) - dt * adv);
+  }
+}
+// reconstruction R: |max_r phi^r| and argmax (lowest index on ties), clamped
+__global__ void k_levelset_R(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, N = g.N;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
     const long long c = b.band[k];
     const unsigned bits = b.xsS[c];
@@ -910,32 +1037,7 @@ __global__ void k_levelset(Grid g, Bufs b, const double* vel, double beta, doubl
     int arg = -1;
     for (int r = 0; r < N; r++) {
       if (!((bits >> r) & 1u)) continue;
-      double adv = 0.0;
-      for (int d = 0; d < D; d++) {
-        const double vd = vel[d * g.ncell + c];
-        if (vd == 0.0) continue;
-        const long long st = g.st[d];
-        const double rh = g.rh[d];
-        double gd;
-        if (vd > 0.0) {
-          double v1 = (phir_stage(b, c - 2 * st, r) - phir_stage(b, c - 3 * st, r)) * rh;
-          double v2 = (phir_stage(b, c - st, r) - phir_stage(b, c - 2 * st, r)) * rh;
-          double v3 = (phir_stage(b, c, r) - phir_stage(b, c - st, r)) * rh;
-          double v4 = (phir_stage(b, c + st, r) - phir_stage(b, c, r)) * rh;
-          double v5 = (phir_stage(b, c + 2 * st, r) - phir_stage(b, c + st, r)) * rh;
-          gd = weno5<double>(v1, v2, v3, v4, v5, eps);
-        } else {
-          double v1 = (phir_stage(b, c + 3 * st, r) - phir_stage(b, c + 2 * st, r)) * rh;
-          double v2 = (phir_stage(b, c + 2 * st, r) - phir_stage(b, c + st, r)) * rh;
-          double v3 = (phir_stage(b, c + st, r) - phir_stage(b, c, r)) * rh;
-          double v4 = (phir_stage(b, c, r) - phir_stage(b, c - st, r)) * rh;
-          double v5 = (phir_stage(b, c - st, r) - phir_stage(b, c - 2 * st, r)) * rh;
-          gd = weno5<double>(v1, v2, v3, v4, v5, eps);
-        }
-        adv = adv + vd * gd;
-      }
-      const double phn = b.chin[c] == r ? b.phin[c] : -b.phin[c];
-      const double val = beta * phn + omb * (phir_stage(b, c, r) - dt * adv);
+      const double val = b.phir[(long long)k * N + r];
       if (arg < 0 || val > best) {
         best = val;
         arg = r;
@@ -943,12 +1045,12 @@ __global__ void k_levelset(Grid g, Bufs b, const double* vel, double beta, doubl
     }
     double ph = fabs(best);
     if (ph > g.cap) ph = g.cap;
-    b.phit[k] = ph;
-    b.chit[k] = (uint8_t)arg;
+    b.phi[c] = ph;
+    b.chi[c] = (uint8_t)arg;
   }
 }
 // scatter band-indexed (phi, chi) back; flag selects which cells are written
-__global__ void k_scatter_phichi(Grid g, Bufs b) {
+__global__ void k_scatter_phichi(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
   if (!ctl_active(b)) return;
   const int nb = b.ctl->nband;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
@@ -966,42 +1068,48 @@ __device__ inline int mix_axes(int D, int k) {
   return D <= 2 ? ax2[k] : ax3[k];
 }
 
-// targets and weights of small cell c of material m; returns the count
-// (0: no target). toff[] are the target cells.
-__device__ inline int mix_targets(const Grid& g, const Bufs& b, long long c, int m, double as, long long* tc,
+// offset code of a 3^d neighbour (dz, dy, dx in -1..1)
+__device__ inline uint8_t off_code(int dx, int dy, int dz) { return (uint8_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)); }
+
+// targets (offset codes) and weights of small cell c of material m; returns
+// the count (0: no target)
+__device__ inline int mix_targets(const Grid& g, const Bufs& b, long long c, int m, double as, uint8_t* toff,
                                   double* tw, double* swout) {
   const int D = g.D;
   double n[3];
-  normal_m(g, b.phi, b.chi, c, m, n);
+  stored_normal(g, b, c, m, n);
+  int q[3];
+  coords(g, c, q);
   int sg[3];
   for (int d = 0; d < 3; d++) sg[d] = n[d] > 0.0 ? 1 : (n[d] < 0.0 ? -1 : 0);
   const int nk = D == 1 ? 1 : (D == 2 ? 3 : 7);
   int nt = 0;
   double sw = 0.0;
-  for (int k = 0; k < nk; k++) {
-    const int ax = mix_axes(D, k);
+  for (int kk = 0; kk < nk; kk++) {
+    const int ax = mix_axes(D, kk);
     bool ok = true;
     double wk = 1.0;
     int na = 0;
-    long long t = c;
+    int o[3] = {0, 0, 0};
     for (int d = 0; d < D; d++)
       if ((ax >> d) & 1) {
         if (sg[d] == 0) ok = false;
-        t += sg[d] * g.st[d];
+        o[d] = sg[d];
         wk = na == 0 ? fabs(n[d]) : wk * fabs(n[d]);
         na++;
       }
     if (na == 1) wk = wk * wk;
     if (!ok) continue;
-    if (!interior_c(g, t) || b.bandidx[t] < 0 || !((b.smask[t] >> m) & 1u) || !(b.alpha[midx(g, m, t)] > as)) continue;
-    tc[nt] = t;
+    int p[3] = {q[0] + o[0], q[1] + o[1], q[2] + o[2]};
+    if (!interior_q(g, p)) continue;
+    const long long t = cell_at(g, p[0], p[1], p[2]);
+    if (b.bandidx[t] < 0 || !((b.smask[t] >> m) & 1u) || !(b.alpha[midx(g, m, t)] > as)) continue;
+    toff[nt] = off_code(o[0], o[1], o[2]);
     tw[nt] = wk;
     nt++;
     sw += wk;
   }
   if (!(sw > 0.0)) {
-    int q[3];
-    coords(g, c, q);
     nt = 0;
     sw = 0.0;
     const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
@@ -1013,7 +1121,7 @@ __device__ inline int mix_targets(const Grid& g, const Bufs& b, long long c, int
           if (!interior_q(g, p)) continue;
           const long long t = cell_at(g, p[0], p[1], p[2]);
           if (b.bandidx[t] < 0 || !((b.smask[t] >> m) & 1u) || !(b.alpha[midx(g, m, t)] > as)) continue;
-          tc[nt] = t;
+          toff[nt] = off_code(dx, dy, dz);
           tw[nt] = b.alpha[midx(g, m, t)];
           sw += tw[nt];
           nt++;
@@ -1021,6 +1129,11 @@ __device__ inline int mix_targets(const Grid& g, const Bufs& b, long long c, int
   }
   *swout = sw;
   return (sw > 0.0) ? nt : 0;
+}
+
+__device__ inline long long off_cell(const Grid& g, long long c, uint8_t code) {
+  const int dz = code / 9 - 1, dy = (code / 3) % 3 - 1, dx = code % 3 - 1;
+  return c + dx + g.st[1] * dy + g.st[2] * dz;
 }
 
 __device__ inline bool is_small(const Grid& g, const Bufs& b, const double* Qc, long long c, int m, double as) {
@@ -1031,55 +1144,64 @@ __device__ inline bool is_small(const Grid& g, const Bufs& b, const double* Qc, 
   return false;
 }
 
-__global__ void k_mix_mark(Grid g, Bufs b, const double* Qc) {
+// per (band cell, material): small-cell test and, for a small cell, its
+// targets and normalised weights (mixn: 0xff not small, else target count)
+__global__ void k_mix_mark(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qc) {
   if (!ctl_active(b)) return;
   const int nb = b.ctl->nband, N = g.N;
-  unsigned long long nsmall = 0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
-    const long long c = b.band[k];
-    unsigned bits = 0;
-    for (int m = 0; m < N; m++) {
-      if (!((b.smask[c] >> m) & 1u)) continue;
-      if (is_small(g, b, Qc, c, m, b.alpha[midx(g, m, c)])) {
-        bits |= 1u << m;
-        nsmall++;
-      }
-    }
-    b.small[c] = (uint8_t)bits;
-  }
-  if (nsmall) atomicAdd(&b.ctl->cnt[C_SMALL], nsmall);
-}
-
-// new state of material m of every band cell: own exchanges minus the
-// exchanges its small neighbours send to it (lexicographic neighbour order)
-__global__ void k_mix_compute(Grid g, Bufs b, const double* Qc) {
-  if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
-  unsigned long long nfail = 0;
+  unsigned long long nsmall = 0, nfail = 0;
   const int total = nb * N;
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
     const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
-    double* out = b.mixq + ((long long)k * N + m) * NV;
-    for (int v = 0; v < NV; v++) out[v] = Qc[qidx(g, m, v, c)];
+    const long long r = (long long)k * N + m;
+    b.mixn[r] = 0xff;
     if (!((b.smask[c] >> m) & 1u)) continue;
+    const double as = b.alpha[midx(g, m, c)];
+    if (!is_small(g, b, Qc, c, m, as)) continue;
+    nsmall++;
+    uint8_t toff[MIX_MAXT];
+    double tw[MIX_MAXT], sw;
+    const int nt = mix_targets(g, b, c, m, as, toff, tw, &sw);
+    if (nt == 0) nfail++;
+    for (int t = 0; t < nt; t++) {
+      b.mixoff[r * MIX_MAXT + t] = toff[t];
+      b.mixbeta[r * MIX_MAXT + t] = tw[t] / sw;
+    }
+    b.mixn[r] = (uint8_t)nt;
+  }
+  if (nsmall) atomicAdd(&b.ctl->cnt[C_SMALL], nsmall);
+  if (nfail) atomicAdd(&b.ctl->cnt[C_MIXFAIL], nfail);
+}
+
+// new state of material m of every band cell: own exchanges minus the
+// exchanges its small neighbours send to it (lexicographic neighbour order)
+__global__ void k_mix_compute(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qc) {
+  if (!ctl_active(b)) return;
+  const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
+  const int total = nb * N;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int m = it / nb, k = it - m * nb;
+    const long long c = b.band[k];
+    const long long r = (long long)k * N + m;
+    double* out = b.mixq + r * NV;
+    if (!((b.smask[c] >> m) & 1u)) {
+      for (int v = 0; v < NV; v++) out[v] = Qc[qidx(g, m, v, c)];
+      continue;
+    }
     int q[3];
     coords(g, c, q);
     double acc[5] = {0, 0, 0, 0, 0};
-    if ((b.small[c] >> m) & 1u) {
+    const int nown = b.mixn[r];
+    if (nown != 0xff) {
       const double as = b.alpha[midx(g, m, c)];
-      long long tc[MIX_MAXT];
-      double tw[MIX_MAXT], sw;
-      const int nt = mix_targets(g, b, c, m, as, tc, tw, &sw);
-      if (nt == 0) {
-        nfail++;
-        if (as == 0.0 && m != b.chi[c]) atomicOr(&b.mixmerge[k], 1u << m);
-      }
-      for (int t = 0; t < nt; t++) {
-        const double beta = tw[t] / sw;
-        const double at = b.alpha[midx(g, m, tc[t])];
+      if (nown == 0 && as == 0.0 && m != b.chi[c]) atomicOr(&b.mixmerge[k], 1u << m);
+      for (int t = 0; t < (nown == 0xff ? 0 : nown); t++) {
+        const long long tc = off_cell(g, c, b.mixoff[r * MIX_MAXT + t]);
+        const double beta = b.mixbeta[r * MIX_MAXT + t];
+        const double at = b.alpha[midx(g, m, tc)];
         for (int v = 0; v < NV; v++)
-          acc[v] += beta * (as * Qc[qidx(g, m, v, tc[t])] - at * Qc[qidx(g, m, v, c)]) / (as + at);
+          acc[v] += beta * (as * Qc[qidx(g, m, v, tc)] - at * Qc[qidx(g, m, v, c)]) / (as + at);
       }
     }
     const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
@@ -1090,14 +1212,16 @@ __global__ void k_mix_compute(Grid g, Bufs b, const double* Qc) {
           const int sx = q[0] - dx, sy = q[1] - dy, sz = q[2] - dz;
           if (!in_array(g, sx, sy, sz)) continue;
           const long long s = cell_at(g, sx, sy, sz);
-          if (!((b.small[s] >> m) & 1u)) continue;
-          const double as = b.alpha[midx(g, m, s)];
-          long long tc[MIX_MAXT];
-          double tw[MIX_MAXT], sw;
-          const int nt = mix_targets(g, b, s, m, as, tc, tw, &sw);
-          for (int t = 0; t < nt; t++) {
-            if (tc[t] != c) continue;
-            const double beta = tw[t] / sw;
+          const int ks = b.bandidx[s];
+          if (ks < 0) continue;
+          const long long rs = (long long)ks * N + m;
+          const int ns = b.mixn[rs];
+          if (ns == 0xff) continue;
+          const uint8_t code = off_code(dx, dy, dz);
+          for (int t = 0; t < ns; t++) {
+            if (b.mixoff[rs * MIX_MAXT + t] != code) continue;
+            const double beta = b.mixbeta[rs * MIX_MAXT + t];
+            const double as = b.alpha[midx(g, m, s)];
             const double at = b.alpha[midx(g, m, c)];
             for (int v = 0; v < NV; v++)
               acc[v] -= beta * (as * Qc[qidx(g, m, v, c)] - at * Qc[qidx(g, m, v, s)]) / (as + at);
@@ -1105,11 +1229,10 @@ __global__ void k_mix_compute(Grid g, Bufs b, const double* Qc) {
         }
     for (int v = 0; v < NV; v++) out[v] = Qc[qidx(g, m, v, c)] + acc[v];
   }
-  if (nfail) atomicAdd(&b.ctl->cnt[C_MIXFAIL], nfail);
 }
 // write the mixed states back; a material that lost all volume and has no
 // same-material neighbour is merged into the cell's primary material
-__global__ void k_mix_scatter(Grid g, Bufs b, double* Qc) {
+__global__ void k_mix_scatter(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, double* Qc) {
   if (!ctl_active(b)) return;
   const int nb = b.ctl->nband, N = g.N, NV = g.NV;
   unsigned long long nmerge = 0;
@@ -1136,7 +1259,7 @@ __global__ void k_mix_scatter(Grid g, Bufs b, double* Qc) {
 }
 
 // ------------------------------------------------- scale separation (a12)
-__global__ void k_scale_sep(Grid g, Bufs b) {
+__global__ void k_scale_sep(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
   if (!ctl_active(b)) return;
   const int nb = b.ctl->nband, N = g.N, D = g.D;
   const double eps = g.eps_ss;
@@ -1205,10 +1328,9 @@ __global__ void k_scale_sep(Grid g, Bufs b) {
 }
 
 // --------------------------------------------- band distance maintenance
-__global__ void k_reinit(Grid g, Bufs b) {
-  if (!ctl_active(b)) return;
+__device__ __forceinline__ void reinit_items(const Grid& g, const Bufs& b, int first, int stride) {
   const int nb = b.ctl->nband, D = g.D;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+  for (int k = first; k < nb; k += stride) {
     const long long c = b.band[k];
     b.phit[k] = b.phi[c];
     b.chit[k] = b.chi[c];
@@ -1253,10 +1375,21 @@ __global__ void k_reinit(Grid g, Bufs b) {
     b.phit[k] = ph;
   }
 }
-
+__device__ __forceinline__ void scatter_items(const Bufs& b, int first, int stride) {
+  const int nb = b.ctl->nband;
+  for (int k = first; k < nb; k += stride) {
+    const long long c = b.band[k];
+    b.phi[c] = b.phit[k];
+    b.chi[c] = b.chit[k];
+  }
+}
+__global__ void k_reinit(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+  if (!ctl_active(b)) return;
+  reinit_items(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
 // ------------------------------------------------------- totals and init
 // one block per (m, v): fixed-order block reduction over interior cells
-__global__ void k_totals(Grid g, const double* Q, double* out) {
+__global__ void k_totals(const __grid_constant__ Grid g, const double* Q, double* out) {
   const int mv = blockIdx.x;
   const int m = mv / g.NV, v = mv % g.NV;
   double s = 0.0;

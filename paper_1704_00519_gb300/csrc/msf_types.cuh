@@ -15,7 +15,7 @@ struct Bufs {
   uint8_t* smask;           // step mask: materials carried by an interior cell this step
   uint8_t* xsS;             // 3^d material bits of the stage indicator (band cells)
   uint8_t* gflag;           // GF_MIXED | GF_CUT (band cells; 0 elsewhere)
-  uint8_t* small;           // mixing sources: bit m = small cell of material m
+  double* nrm;              // [N][3][ncell] unit normals of the local level sets (band cells)
   double* alpha;            // [N][ncell]
   double *Alo, *Ahi;        // [D][N][ncell] face apertures (mixed cells)
   void *W0, *W1;            // T [N][NV][ncell] primitive states, ping-pong
@@ -30,11 +30,18 @@ struct Bufs {
   uint8_t* chit;            // [nbandmax] scratch
   double* mixq;             // [nbandmax][N][NV] mixed state scratch
   unsigned* mixmerge;       // [nbandmax] materials to merge into the primary
+  uint8_t* mixn;            // [nbandmax][N] 0xff: not small, else mixing target count
+  uint8_t* mixoff;          // [nbandmax][N][MIX_MAXT] target offset codes
+  double* mixbeta;          // [nbandmax][N][MIX_MAXT] normalised mixing weights
+  double* phir;             // [nbandmax][N] new local level-set values
   double* bflux;            // [nbnd][N][NV] boundary-face fluxes of the stage
   Ctl* ctl;
 };
 
 constexpr int NTHREADS = 256;
+// narrow-band kernels: small blocks so that a few thousand band items spread
+// over every SM instead of filling the first few hundred wide blocks
+constexpr int BAND_THREADS = 64;
 
 // first boundary-face id of each (axis, side): faces are numbered per side in
 // interior order of the other coordinates
