@@ -179,6 +179,41 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def batched_rates(msf, torch, stream, K_persistent, K_sequence):
+    """256 seeded 1D multi-material Riemann problems (FP32-bulk): one
+    persistent launch per call (one CTA per instance, autotuned CTA size)
+    against the per-instance kernel sequences, both device-timed."""
+    import paper_1704_00519_gb300.cases as cs
+    cases = cs.batched_1d(256, 20170403)
+    cells = [c.cells for c in cases]
+
+    def run(mode, K, warm):
+        b = msf.Batch(cases, precision=msf.MSF_FP32_BULK, batch_mode=mode, stream=stream)
+        b.step(warm, 0.1, sync=False)
+        before = [b.info(i)[1] for i in range(len(cases))]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        b.step(K, 0.1, sync=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        info = [b.info(i) for i in range(len(cases))]
+        work = sum(cells[i] * 3 * (info[i][1] - before[i]) for i in range(len(cases)))
+        bad = sum(1 for x in info if x[2] != 0)
+        bs = b.block_size()
+        b.close()
+        return work / (ms / 1e3), ms / K, bad, bs
+
+    v1, ms1, bad1, bs = run(0, K_persistent, 5)
+    v2, ms2, bad2, _ = run(1, K_sequence, 1)
+    return {"workload": "256 seeded 1D Riemann problems (seed 20170403), 200-20000 cells, 2-4 stiffened gases",
+            "cells": int(sum(cells)), "instances": len(cases), "precision": "fp32_bulk",
+            "value": v1, "unit": UNIT, "ms_per_step": ms1, "cta_threads": bs, "steps": K_persistent,
+            "per_instance_launches": {"value": v2, "unit": UNIT, "ms_per_step": ms2, "steps": K_sequence},
+            "speedup_vs_per_instance": v1 / v2, "instances_with_device_error": max(bad1, bad2)}
+
+
 def pairs_per_cell(s):
     """(cell, material) pairs the flux update processes: popcount of the step mask."""
     vals, counts = np.unique(s.debug(5).astype(np.int64), return_counts=True)
@@ -286,6 +321,7 @@ def run_gpu(args):
     d2h = st["Q"].nbytes + st["alpha"].nbytes + st["phi"].nbytes + st["chi"].nbytes
 
     launches = s32.launches_per_step() * K
+    batched = batched_rates(msf, torch, sptr, max(K, 10), 3)
     if rank != 0:
         return 0
 
@@ -317,6 +353,7 @@ def run_gpu(args):
                 "how": "wall clock: msf_set_levelset from host arrays, K steps, msf_get_state to host"},
         "gpu_launches": launches,
         "clocks": clk,
+        "batched_1d": batched,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

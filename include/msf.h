@@ -88,6 +88,10 @@ typedef struct {
  *   use_graph    1: replay each step as a captured CUDA graph
  *   profile      1: record CUDA events around the flux-update kernel of each
  *                stage (read back with msf_profile_read)
+ *   batch_mode   for n_instances > 1 of dimension 1: 0 = one persistent launch
+ *                per msf_step call, one CTA per instance (largest first, CTA
+ *                size autotuned on the first steps); 1 = the per-instance
+ *                kernel sequence of a single instance, instance after instance
  *   stream       cudaStream_t for all work of this context */
 typedef struct {
   int32_t precision;
@@ -95,7 +99,7 @@ typedef struct {
   int32_t ext_sweeps, vel_sweeps, reinit_iters;
   int32_t scale_sep, reinit;
   double scale_eps_h, phi_cap_h;
-  int32_t use_graph, profile;
+  int32_t use_graph, profile, batch_mode;
   void* stream;
 } msf_options;
 
@@ -179,6 +183,17 @@ msf_status msf_last_dt(msf_ctx* ctx, int32_t instance, double* dt);
  * 4 mixed-cell flag [cells], 5 step material mask [cells]. out: host double array.
  * Cells outside the narrow band hold 0 for fields 1-3. Synchronises. */
 msf_status msf_debug_field(msf_ctx* ctx, int32_t instance, int32_t which, double* out);
+
+/* Progress of one instance: simulated time t, steps taken since
+ * msf_set_levelset, and the device-detected error of that instance
+ * (MSF_OK, MSF_ENONFINITE, MSF_ENEGATIVE or MSF_EBAND). Host outputs, any may
+ * be NULL. Synchronises. An instance with an error stops stepping; the
+ * others continue. */
+msf_status msf_instance_info(msf_ctx* ctx, int32_t instance, double* t, int64_t* steps, int32_t* status);
+
+/* CTA size the batched persistent kernel uses (0 before the first batched
+ * step or when the context does not run batched). */
+msf_status msf_batch_block_size(msf_ctx* ctx, int32_t* block_size);
 
 /* Number of kernel launches one step enqueues (all instances). */
 msf_status msf_launches_per_step(msf_ctx* ctx, int64_t* n);

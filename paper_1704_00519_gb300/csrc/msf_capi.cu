@@ -28,6 +28,8 @@ struct Inst {
   BndBase bb;
   int nbnd = 0;
   int nblk_band = 1;
+  void* Fface = nullptr;     // batched stepping: face fluxes of a stage
+  double* Aface = nullptr;   // batched stepping: face apertures of a stage
 };
 
 }  // namespace
@@ -45,6 +47,12 @@ struct msf_ctx {
   bool graph_tried = false;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   long long launches = 0;  // kernel launches of the last enqueued step
+  void* arena = nullptr;   // every device array of every instance
+  bool batched = false;    // persistent one-CTA-per-instance stepping
+  BatchEntry* d_tab = nullptr;
+  int* d_order = nullptr;
+  int bs = 0;              // autotuned CTA size of the batched kernel (0: not tuned yet)
+  cudaEvent_t tev[2] = {nullptr, nullptr};
   bool sticky = false;
   std::string err;
 };
@@ -88,6 +96,7 @@ extern "C" msf_status msf_default_options(int32_t dim, msf_options* opt) {
   opt->phi_cap_h = 8.0;
   opt->use_graph = 1;
   opt->profile = 0;
+  opt->batch_mode = 0;
   opt->stream = nullptr;
   return MSF_OK;
 }
@@ -141,7 +150,6 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
         return fail(nullptr, MSF_EINVAL, "EOS parameters");
     }
   }
-  if (n_instances > 1) return fail(nullptr, MSF_EUNSUPPORTED, "several instances per context are not supported");
 
   msf_ctx* c = new msf_ctx();
   c->dim = dim;
@@ -234,54 +242,110 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
       }
     in.nbnd = (int)nb;
     in.nblk_band = band_blocks(g);
-
-    const long long nc = g.ncell, N = n_mat, NV = g.NV, nbmax = g.n_interior;
-    Bufs& b = in.b;
-    std::memset(&b, 0, sizeof(b));
-    for (int k = 0; k < 3; k++) ALLOC(b.Q[k], double, N * NV * nc);
-    ALLOC(b.phi, double, nc);
-    ALLOC(b.phin, double, nc);
-    ALLOC(b.chi, uint8_t, nc);
-    ALLOC(b.chin, uint8_t, nc);
-    ALLOC(b.xs, uint8_t, nc);
-    ALLOC(b.mtmp, uint8_t, nc);
-    ALLOC(b.smask, uint8_t, nc);
-    ALLOC(b.xsS, uint8_t, nc);
-    ALLOC(b.gflag, uint8_t, nc);
-    ALLOC(b.nrm, double, N * 3 * nc);
-    ALLOC(b.alpha, double, N * nc);
-    ALLOC(b.Alo, double, dim * N * nc);
-    ALLOC(b.Ahi, double, dim * N * nc);
-    b.W0 = dalloc(c, ts * N * NV * nc, &ce);
-    b.W1 = dalloc(c, ts * N * NV * nc, &ce);
-    b.Uh = dalloc(c, ts * N * NV * nc, &ce);
-    if (!b.W0 || !b.W1 || !b.Uh) {
-      msf_destroy(c);
-      return fail(nullptr, MSF_ENOMEM, "cudaMalloc (stage states)");
-    }
-    ALLOC(b.f0, uint8_t, N * nc);
-    ALLOC(b.f1, uint8_t, N * nc);
-    ALLOC(b.isreal, uint8_t, N * nc);
-    ALLOC(b.X, double, N * NV * nc);
-    ALLOC(b.vel0, double, 3 * nc);
-    ALLOC(b.vel1, double, 3 * nc);
-    ALLOC(b.vf0, uint8_t, nc);
-    ALLOC(b.vf1, uint8_t, nc);
-    ALLOC(b.band, int, nbmax);
-    ALLOC(b.bandidx, int, nc);
-    ALLOC(b.phit, double, nbmax);
-    ALLOC(b.chit, uint8_t, nbmax);
-    ALLOC(b.mixq, double, nbmax * N * NV);
-    ALLOC(b.mixmerge, unsigned, nbmax);
-    ALLOC(b.mixn, uint8_t, nbmax * N);
-    ALLOC(b.mixoff, uint8_t, nbmax * N * MIX_MAXT);
-    ALLOC(b.mixbeta, double, nbmax * N * MIX_MAXT);
-    ALLOC(b.phir, double, nbmax * N);
-    ALLOC(b.bflux, double, std::max<long long>(1, nb) * N * NV);
-    ALLOC(b.ctl, Ctl, 1);
-    cudaMemsetAsync(b.bandidx, 0xff, sizeof(int) * nc, c->stream);
   }
 #undef ALLOC
+  // all arrays of all instances carved from one allocation (two passes: size, then assign)
+  const bool batched = n_instances > 1 && dim == 1 && opt->batch_mode == 0;
+  c->batched = batched;
+  size_t total = 0;
+  for (int pass = 0; pass < 2; pass++) {
+    char* base = pass == 0 ? nullptr : (char*)c->arena;
+    size_t off = 0;
+    auto carve = [&](size_t bytes) -> void* {
+      off = (off + 255) & ~(size_t)255;
+      void* p = base ? (void*)(base + off) : nullptr;
+      off += bytes ? bytes : 16;
+      return p;
+    };
+    for (int i = 0; i < n_instances; i++) {
+      Inst& in = c->inst[i];
+      const Grid& g = in.g;
+      const long long nc = g.ncell, N = n_mat, NV = g.NV, nbmax = g.n_interior;
+      Bufs& b = in.b;
+      for (int k = 0; k < 3; k++) b.Q[k] = (double*)carve(8 * N * NV * nc);
+      b.phi = (double*)carve(8 * nc);
+      b.phin = (double*)carve(8 * nc);
+      b.chi = (uint8_t*)carve(nc);
+      b.chin = (uint8_t*)carve(nc);
+      b.xs = (uint8_t*)carve(nc);
+      b.mtmp = (uint8_t*)carve(nc);
+      b.smask = (uint8_t*)carve(nc);
+      b.xsS = (uint8_t*)carve(nc);
+      b.gflag = (uint8_t*)carve(nc);
+      b.nrm = (double*)carve(8 * N * 3 * nc);
+      b.alpha = (double*)carve(8 * N * nc);
+      b.Alo = (double*)carve(8 * dim * N * nc);
+      b.Ahi = (double*)carve(8 * dim * N * nc);
+      b.W0 = carve(ts * N * NV * nc);
+      b.W1 = carve(ts * N * NV * nc);
+      b.Uh = carve(ts * N * NV * nc);
+      b.f0 = (uint8_t*)carve(N * nc);
+      b.f1 = (uint8_t*)carve(N * nc);
+      b.isreal = (uint8_t*)carve(N * nc);
+      b.X = (double*)carve(8 * N * NV * nc);
+      b.vel0 = (double*)carve(8 * 3 * nc);
+      b.vel1 = (double*)carve(8 * 3 * nc);
+      b.vf0 = (uint8_t*)carve(nc);
+      b.vf1 = (uint8_t*)carve(nc);
+      b.band = (int*)carve(4 * nbmax);
+      b.bandidx = (int*)carve(4 * nc);
+      b.phit = (double*)carve(8 * nbmax);
+      b.chit = (uint8_t*)carve(nbmax);
+      b.mixq = (double*)carve(8 * nbmax * N * NV);
+      b.mixmerge = (unsigned*)carve(4 * nbmax);
+      b.mixn = (uint8_t*)carve(nbmax * N);
+      b.mixoff = (uint8_t*)carve(nbmax * N * MIX_MAXT);
+      b.mixbeta = (double*)carve(8 * nbmax * N * MIX_MAXT);
+      b.phir = (double*)carve(8 * nbmax * N);
+      b.bflux = (double*)carve(8 * std::max<long long>(1, in.nbnd) * N * NV);
+      b.ctl = (Ctl*)carve(sizeof(Ctl));
+      if (batched) {
+        in.Fface = carve(ts * N * NV * (g.n[0] + 1));
+        in.Aface = (double*)carve(8 * N * (g.n[0] + 1));
+      }
+    }
+    if (pass == 0) {
+      total = off;
+      ce = cudaMalloc(&c->arena, total);
+      if (ce != cudaSuccess) {
+        msf_destroy(c);
+        return fail(nullptr, MSF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(ce));
+      }
+      cudaMemsetAsync(c->arena, 0, total, c->stream);
+    }
+  }
+  for (Inst& in : c->inst) cudaMemsetAsync(in.b.bandidx, 0xff, sizeof(int) * in.g.ncell, c->stream);
+  if (batched) {
+    // instance table and largest-first order for the persistent kernel
+    std::vector<BatchEntry> tab(n_instances);
+    std::vector<int> order(n_instances);
+    for (int i = 0; i < n_instances; i++) {
+      Inst& in = c->inst[i];
+      tab[i].g = in.g;
+      tab[i].b = in.b;
+      tab[i].bb = in.bb;
+      tab[i].Fface = in.Fface;
+      tab[i].Aface = in.Aface;
+      tab[i].nbnd = in.nbnd;
+      order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int bb) { return c->inst[a].g.n_interior > c->inst[bb].g.n_interior; });
+    ce = cudaMalloc((void**)&c->d_tab, sizeof(BatchEntry) * n_instances);
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&c->d_order, sizeof(int) * n_instances);
+    if (ce == cudaSuccess) {
+      c->allocs.push_back(c->d_tab);
+      c->allocs.push_back(c->d_order);
+      ce = cudaMemcpy(c->d_tab, tab.data(), sizeof(BatchEntry) * n_instances, cudaMemcpyHostToDevice);
+    }
+    if (ce == cudaSuccess) ce = cudaMemcpy(c->d_order, order.data(), sizeof(int) * n_instances, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&c->tev[0]);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&c->tev[1]);
+    if (ce != cudaSuccess) {
+      msf_destroy(c);
+      return fail(nullptr, MSF_ECUDA, std::string("batch table: ") + cudaGetErrorString(ce));
+    }
+  }
   ce = cudaStreamSynchronize(c->stream);
   if (ce != cudaSuccess) {
     msf_destroy(c);
@@ -294,6 +358,9 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
 extern "C" msf_status msf_destroy(msf_ctx* c) {
   if (!c) return MSF_OK;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (int k = 0; k < 2; k++)
+    if (c->tev[k]) cudaEventDestroy(c->tev[k]);
+  if (c->arena) cudaFree(c->arena);
   for (int k = 0; k < 6; k++)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   for (void* p : c->allocs) cudaFree(p);
@@ -405,8 +472,35 @@ extern "C" msf_status msf_step(msf_ctx* c, int32_t n_steps, double t_end, int32_
   if (c->sticky) return fail(c, MSF_ESTATE, "context holds a device-detected error; reset with msf_set_state");
   if (n_steps < 0 || std::isnan(t_end)) return fail(c, MSF_EINVAL, "n_steps < 0 or t_end NaN");
   if (n_steps == 0) return MSF_OK;
+  if (c->batched) {
+    launch_set_tend_all(c->d_tab, c->ninst, t_end, c->stream);
+    int left = n_steps;
+    if (c->bs == 0) {
+      // autotune the CTA size on live steps (results do not depend on it)
+      const int cand[3] = {128, 256, 512};
+      float best = 0.0f;
+      int bestbs = 256;
+      for (int k = 0; k < 3 && left > 0; k++, left--) {
+        CUDA_TRY(c, cudaEventRecord(c->tev[0], c->stream));
+        CUDA_TRY(c, c->ops->batched(c->d_tab, c->d_order, c->ninst, 1, cand[k], c->stream));
+        CUDA_TRY(c, cudaEventRecord(c->tev[1], c->stream));
+        CUDA_TRY(c, cudaEventSynchronize(c->tev[1]));
+        float ms = 0.0f;
+        CUDA_TRY(c, cudaEventElapsedTime(&ms, c->tev[0], c->tev[1]));
+        if (k == 0 || ms < best) {
+          best = ms;
+          bestbs = cand[k];
+        }
+      }
+      c->bs = bestbs;
+    }
+    if (left > 0) CUDA_TRY(c, c->ops->batched(c->d_tab, c->d_order, c->ninst, left, c->bs, c->stream));
+    c->launches = 2;
+    if (sync) return read_error(c);
+    return MSF_OK;
+  }
   for (Inst& in : c->inst) k_set_tend<<<1, 1, 0, c->stream>>>(in.b.ctl, t_end);
-  bool use_graph = c->opt.use_graph != 0;
+  bool use_graph = c->opt.use_graph != 0 && c->ninst == 1;
   if (use_graph && !c->graph && !c->graph_tried) {
     c->graph_tried = true;
     cudaGraph_t graph;
@@ -664,7 +758,29 @@ extern "C" msf_status msf_debug_field(msf_ctx* c, int32_t i, int32_t which, doub
 
 extern "C" msf_status msf_launches_per_step(msf_ctx* c, int64_t* n) {
   if (!c || !n) return MSF_EINVAL;
-  *n = count_launches(c);
+  // batched: one persistent launch (plus the end-time kernel) covers every step of a call
+  *n = c->batched ? 1 : count_launches(c);
+  return MSF_OK;
+}
+
+extern "C" msf_status msf_instance_info(msf_ctx* c, int32_t i, double* t, int64_t* steps, int32_t* status) {
+  msf_status st = check_instance(c, i);
+  if (st != MSF_OK) return st;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, c->inst[i].b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const Ctl& h = *c->h_ctl;
+  if (t) *t = h.t;
+  if (steps) *steps = (int64_t)h.cnt[C_STEPS];
+  if (status)
+    *status = (h.err & ERR_BAND) ? MSF_EBAND
+              : (h.err & ERR_NEGATIVE) ? MSF_ENEGATIVE
+              : (h.err & ERR_NONFINITE) ? MSF_ENONFINITE : MSF_OK;
+  return MSF_OK;
+}
+
+extern "C" msf_status msf_batch_block_size(msf_ctx* c, int32_t* block_size) {
+  if (!c || !block_size) return MSF_EINVAL;
+  *block_size = c->batched ? c->bs : 0;
   return MSF_OK;
 }
 

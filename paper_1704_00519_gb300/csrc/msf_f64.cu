@@ -183,6 +183,9 @@ void launch_extend_vel(const Grid& g, const Bufs& b, const double* vin, double* 
                        uint8_t* fout, int nblk, cudaStream_t s) {
   k_extend_vel<<<nblk, BAND_THREADS, 0, s>>>(g, b, vin, vout, fin, fout);
 }
+void launch_set_tend_all(const BatchEntry* tab, int n, double t_end, cudaStream_t s) {
+  k_set_tend_all<<<(n + 255) / 256, 256, 0, s>>>(tab, n, t_end);
+}
 void launch_ledger(const Grid& g, const Bufs& b, int nbnd, double w, cudaStream_t s) {
   k_ledger<<<g.N * g.NV, NTHREADS, 0, s>>>(g, b, nbnd, w);
 }

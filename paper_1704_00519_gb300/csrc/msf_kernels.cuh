@@ -69,10 +69,10 @@ __device__ inline void halo_coords(const Grid& g, long long idx_, int* q) {
 }
 
 // halo cells of phi, chi: every out-of-range axis mapped to its boundary source
-__global__ void k_bc_phichi(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+__device__ __forceinline__ void phase_bc_phichi(const Grid& g, const Bufs& b, int first_, int stride_) {
   long long nh = halo_count(g);
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nh;
-       idx += (long long)gridDim.x * blockDim.x) {
+  for (long long idx = (long long)first_; idx < nh;
+       idx += (long long)stride_) {
     int q[3], s[3], side, flip;
     halo_coords(g, idx, q);
     for (int d = 0; d < 3; d++) s[d] = q[d];
@@ -83,13 +83,15 @@ __global__ void k_bc_phichi(const __grid_constant__ Grid g, const __grid_constan
     b.chi[c] = b.chi[sc];
   }
 }
+__global__ void k_bc_phichi(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+  phase_bc_phichi(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
 
 // -------------------------------------------------- step masks and the band
 // xs = material bits of the 3^d block (clamped to the array)
-__global__ void k_xs(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
-  if (!ctl_active(b)) return;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
-       c += (long long)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void phase_xs(const Grid& g, const Bufs& b, int first_, int stride_) {
+    for (long long c = (long long)first_; c < g.ncell;
+       c += (long long)stride_) {
     int q[3];
     coords(g, c, q);
     unsigned bits = 0;
@@ -102,12 +104,15 @@ __global__ void k_xs(const __grid_constant__ Grid g, const __grid_constant__ Buf
     b.xs[c] = (uint8_t)bits;
   }
 }
-// OR-dilation by +-4 along axis d (separable box of the step mask)
-__global__ void k_dilate(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const uint8_t* src, uint8_t* dst, int d) {
+__global__ void k_xs(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
   if (!ctl_active(b)) return;
-  const int R = 4;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
-       c += (long long)gridDim.x * blockDim.x) {
+  phase_xs(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+// OR-dilation by +-4 along axis d (separable box of the step mask)
+__device__ __forceinline__ void phase_dilate(const Grid& g, const Bufs& b, const uint8_t* src, uint8_t* dst, int d, int first_, int stride_) {
+    const int R = 4;
+  for (long long c = (long long)first_; c < g.ncell;
+       c += (long long)stride_) {
     int q[3];
     coords(g, c, q);
     unsigned bits = 0;
@@ -119,11 +124,14 @@ __global__ void k_dilate(const __grid_constant__ Grid g, const __grid_constant__
     dst[c] = (uint8_t)bits;
   }
 }
-// final step mask on interior cells, band compaction, per-step resets
-__global__ void k_band(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const uint8_t* dil) {
+__global__ void k_dilate(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const uint8_t* src, uint8_t* dst, int d) {
   if (!ctl_active(b)) return;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.ncell;
-       c += (long long)gridDim.x * blockDim.x) {
+  phase_dilate(g, b, src, dst, d, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+// final step mask on interior cells, band compaction, per-step resets
+__device__ __forceinline__ void phase_band(const Grid& g, const Bufs& b, const uint8_t* dil, int first_, int stride_) {
+    for (long long c = (long long)first_; c < g.ncell;
+       c += (long long)stride_) {
     uint8_t m = 0;
     bool inner = interior_c(g, c);
     if (inner) m = dil[c];
@@ -137,6 +145,10 @@ __global__ void k_band(const __grid_constant__ Grid g, const __grid_constant__ B
     b.bandidx[c] = bi;
   }
 }
+__global__ void k_band(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const uint8_t* dil) {
+  if (!ctl_active(b)) return;
+  phase_band(g, b, dil, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
 
 // step start: activity flag, band counter reset
 __global__ void k_step_begin(const __grid_constant__ Bufs b) {
@@ -147,14 +159,17 @@ __global__ void k_step_begin(const __grid_constant__ Bufs b) {
 }
 
 // save phi^n, chi^n of band cells (used pointwise by the level-set RK stages)
-__global__ void k_band_save(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
-  if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void phase_band_save(const Grid& g, const Bufs& b, int first_, int stride_) {
+    const int nb = b.ctl->nband;
+  for (int k = first_; k < nb; k += stride_) {
     long long c = b.band[k];
     b.phin[c] = b.phi[c];
     b.chin[c] = b.chi[c];
   }
+}
+__global__ void k_band_save(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+  if (!ctl_active(b)) return;
+  phase_band_save(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // --------------------------------------------- geometry + correction (a3, a4)
@@ -170,11 +185,10 @@ __device__ inline unsigned block_bits(const Grid& g, const uint8_t* chi, const i
 
 // per (band cell, material): unit normal of phi^m for the materials the cell
 // carries this step, volume fraction and raw face apertures
-__global__ void k_geom_mat(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
-  if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband, N = g.N, D = g.D;
+__device__ __forceinline__ void phase_geom_mat(const Grid& g, const Bufs& b, int first_, int stride_) {
+    const int nb = b.ctl->nband, N = g.N, D = g.D;
   const int total = nb * N;
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+  for (int it = first_; it < total; it += stride_) {
     const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
     int q[3];
@@ -201,16 +215,19 @@ __global__ void k_geom_mat(const __grid_constant__ Grid g, const __grid_constant
     }
   }
 }
+__global__ void k_geom_mat(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+  if (!ctl_active(b)) return;
+  phase_geom_mat(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
 
 // per band cell: flags, partition of each face among the local materials and
 // the conservation correction (Sec. 2.3.1, Eq. vol_corr2).
 // Qs == nullptr and mass == nullptr: raw volume fractions (start-up)
-__global__ void k_geom_cell(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs, const double* mass) {
-  if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband;
+__device__ __forceinline__ void phase_geom_cell(const Grid& g, const Bufs& b, const double* Qs, const double* mass, int first_, int stride_) {
+    const int nb = b.ctl->nband;
   const int N = g.N, D = g.D;
   unsigned long long nmulti = 0, ncorr = 0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+  for (int k = first_; k < nb; k += stride_) {
     const long long c = b.band[k];
     int q[3];
     coords(g, c, q);
@@ -268,6 +285,10 @@ __global__ void k_geom_cell(const __grid_constant__ Grid g, const __grid_constan
     if (ncorr) atomicAdd(&b.ctl->cnt[C_CORRECTED], ncorr);
   }
 }
+__global__ void k_geom_cell(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs, const double* mass) {
+  if (!ctl_active(b)) return;
+  phase_geom_cell(g, b, Qs, mass, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
 
 // stored unit normal of material m at a band cell (written by k_geom_mat)
 __device__ inline void stored_normal(const Grid& g, const Bufs& b, long long c, int m, double* n) {
@@ -304,13 +325,12 @@ __device__ inline double alpha_of(const Grid& g, const Bufs& b, long long c, int
 
 // -------------------------------------- primitive recovery + ghosts (a5, a6)
 template <typename T>
-__global__ void k_prim(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
-  if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband, N = g.N, NV = g.NV;
+__device__ __forceinline__ void phase_prim(const Grid& g, const Bufs& b, const double* Qs, int first_, int stride_) {
+    const int nb = b.ctl->nband, N = g.N, NV = g.NV;
   T* W0 = (T*)b.W0;
   T* W1 = (T*)b.W1;
   const int total = nb * N;
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+  for (int it = first_; it < total; it += stride_) {
     const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
     b.f0[midx(g, m, c)] = 0;
@@ -326,6 +346,11 @@ __global__ void k_prim(const __grid_constant__ Grid g, const __grid_constant__ B
       b.isreal[midx(g, m, c)] = 1;
     }
   }
+}
+template <typename T>
+__global__ void k_prim(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
+  if (!ctl_active(b)) return;
+  phase_prim<T>(g, b, Qs, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // one Jacobi sweep: targets take the upwind-weighted mean of filled face
@@ -391,14 +416,13 @@ __global__ void k_extend(const __grid_constant__ Grid g, const __grid_constant__
 
 // stencil state of band cells: real Q/alpha, ghost cons(W), else NaN
 template <typename T>
-__global__ void k_cons(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs, const void* Wfin, const uint8_t* ffin) {
-  if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband, N = g.N, NV = g.NV;
+__device__ __forceinline__ void phase_cons(const Grid& g, const Bufs& b, const double* Qs, const void* Wfin, const uint8_t* ffin, int first_, int stride_) {
+    const int nb = b.ctl->nband, N = g.N, NV = g.NV;
   const T* W = (const T*)Wfin;
   T* Uh = (T*)b.Uh;
   const T nanv = (T)__longlong_as_double(0x7ff8000000000000LL);
   const int total = nb * N;
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+  for (int it = first_; it < total; it += stride_) {
     const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
     {
@@ -418,6 +442,11 @@ __global__ void k_cons(const __grid_constant__ Grid g, const __grid_constant__ B
       for (int v = 0; v < NV; v++) Uh[qidx(g, m, v, c)] = u[v];
     }
   }
+}
+template <typename T>
+__global__ void k_cons(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs, const void* Wfin, const uint8_t* ffin) {
+  if (!ctl_active(b)) return;
+  phase_cons<T>(g, b, Qs, Wfin, ffin, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // stencil state of an interior cell (bulk: Q; band: Uh; otherwise NaN)
@@ -439,17 +468,16 @@ __device__ __forceinline__ void interior_uhat(const Grid& g, const Bufs& b, cons
 
 // halo cells of the stencil state (one axis out of range at a time)
 template <typename T>
-__global__ void k_bc_uhat(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
-  if (!ctl_active(b)) return;
-  const int N = g.N, NV = g.NV, D = g.D;
+__device__ __forceinline__ void phase_bc_uhat(const Grid& g, const Bufs& b, const double* Qs, int first_, int stride_) {
+    const int N = g.N, NV = g.NV, D = g.D;
   long long per[3] = {0, 0, 0}, total = 0;
   for (int d = 0; d < D; d++) {
     per[d] = 2LL * G * (g.n_interior / g.n[d]);
     total += per[d];
   }
   T* Uh = (T*)b.Uh;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
+  for (long long idx = (long long)first_; idx < total;
+       idx += (long long)stride_) {
     int d = 0;
     long long r0 = idx;
     while (r0 >= per[d]) { r0 -= per[d]; d++; }
@@ -486,16 +514,20 @@ __global__ void k_bc_uhat(const __grid_constant__ Grid g, const __grid_constant_
     }
   }
 }
+template <typename T>
+__global__ void k_bc_uhat(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
+  if (!ctl_active(b)) return;
+  phase_bc_uhat<T>(g, b, Qs, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
 
 // ----------------------------------------------------------- CFL step (a2)
+// largest sum_d (|u_d| + c) / h_d over the items [first, n_interior) with stride
 template <typename T>
-__global__ void k_dt(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
-  if (!ctl_active(b)) return;
+__device__ __forceinline__ double dt_items(const Grid& g, const Bufs& b, const double* Qs, long long first,
+                                           long long stride, unsigned& err) {
   const int N = g.N, D = g.D;
   double lam = 0.0;
-  unsigned err = 0;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.n_interior;
-       idx += (long long)gridDim.x * blockDim.x) {
+  for (long long idx = first; idx < g.n_interior; idx += stride) {
     const long long c = interior_cell(g, idx);
     const bool inb = b.bandidx[c] >= 0;
     for (int m = 0; m < N; m++) {
@@ -509,15 +541,29 @@ __global__ void k_dt(const __grid_constant__ Grid g, const __grid_constant__ Buf
       if ((double)s > lam) lam = (double)s;
     }
   }
-  // block max, then one atomic
-  __shared__ double red[NTHREADS];
-  red[threadIdx.x] = lam;
+  return lam;
+}
+// block maximum of per-thread values (blockDim.x a power of two <= 1024)
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double red[1024];
+  red[threadIdx.x] = v;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomic_max_pos_double(&b.ctl->lam_bits, red[0]);
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+template <typename T>
+__global__ void k_dt(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
+  if (!ctl_active(b)) return;
+  unsigned err = 0;
+  const double lam = dt_items<T>(g, b, Qs, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                                 (long long)gridDim.x * blockDim.x, err);
+  const double bm = block_max(lam);
+  if (threadIdx.x == 0) atomic_max_pos_double(&b.ctl->lam_bits, bm);
   if (err) atomicOr(&b.ctl->err, err);
 }
 __global__ void k_dt_finalize(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
@@ -543,13 +589,12 @@ __global__ void k_step_end(const __grid_constant__ Bufs b) {
 
 // ----------------------------------------- reduced interface interaction (a7)
 template <typename T>
-__global__ void k_interface(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
-  if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
+__device__ __forceinline__ void phase_interface(const Grid& g, const Bufs& b, const double* Qs, int first_, int stride_) {
+    const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
   const T* Uh = (const T*)b.Uh;
   unsigned err = 0;
   unsigned long long ncut = 0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+  for (int k = first_; k < nb; k += stride_) {
     const long long c = b.band[k];
     for (int d = 0; d < 3; d++) b.vel0[d * g.ncell + c] = 0.0;
     b.vf0[c] = 0;
@@ -611,6 +656,11 @@ __global__ void k_interface(const __grid_constant__ Grid g, const __grid_constan
   }
   if (ncut) atomicAdd(&b.ctl->cnt[C_CUT], ncut);
   if (err) atomicOr(&b.ctl->err, err);
+}
+template <typename T>
+__global__ void k_interface(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
+  if (!ctl_active(b)) return;
+  phase_interface<T>(g, b, Qs, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // one sweep of the interface-velocity extension into the band
@@ -690,34 +740,45 @@ struct FluxSmem {
       sizeof(T) * ((size_t)NS * (NV + NP) + (size_t)NF * NV) + sizeof(double) * NF + (size_t)NS;
 };
 
+// primitive velocity, pressure and sound speed of a stencil state (same
+// arithmetic as cons_to_prim and sound); isbad: rho <= 0 or c^2 <= 0
 template <int D, typename T>
-__device__ inline void face_flux_smem(const T* U, const T* P, int s0, int sstride, int d, int NS, T eps, T* Fh) {
-  // U[v*NS + s], P[e*NS + s] with e: 0..D-1 velocities, D pressure, D+1 sound speed
+__device__ __forceinline__ void stencil_prim(const T* u, T gm1, T gpi, T gam, T pinf, T* vel, T& pres, T& cs,
+                                             bool& isbad) {
+  const T rho = u[0];
+  T qsum = T(0);
+#pragma unroll
+  for (int e = 0; e < D; e++) vel[e] = u[1 + e] / rho;
+#pragma unroll
+  for (int e = 0; e < D; e++) qsum += vel[e] * vel[e];
+  const T ke = T(0.5) * rho * qsum;
+  pres = gm1 * (u[D + 1] - ke) - gpi;
+  T c2 = (gam * (pres + pinf)) / rho;
+  isbad = !(rho > T(0)) || !(c2 > T(0));
+  if (isbad) c2 = c2 > T(0) ? c2 : T(0);
+  cs = sqrt(c2);
+}
+
+// WENO5 of the Lax-Friedrichs split fluxes through one face along axis d from
+// its 6-cell stencil: U[q][v] states, un normal velocity, pr pressure, cs sound speed
+template <int D, typename T>
+__device__ __forceinline__ void face_flux_regs(const T (&U)[6][D + 2], const T (&un)[6], const T (&pr)[6],
+                                               const T (&cs)[6], int d, T eps, T* Fh) {
   constexpr int NV = D + 2;
   T a = T(0);
 #pragma unroll
   for (int q = 0; q < 6; q++) {
-    const int s = s0 + (q - 2) * sstride;
-    const T sp = fabs(P[d * NS + s]) + P[(D + 1) * NS + s];
+    const T sp = fabs(un[q]) + cs[q];
     if (sp > a) a = sp;
-  }
-  T un[6], pr[6], mom[6];
-#pragma unroll
-  for (int q = 0; q < 6; q++) {
-    const int s = s0 + (q - 2) * sstride;
-    un[q] = P[d * NS + s];
-    pr[q] = P[D * NS + s];
-    mom[q] = U[(1 + d) * NS + s];
   }
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     T fp[6], fm[6];
 #pragma unroll
     for (int q = 0; q < 6; q++) {
-      const int s = s0 + (q - 2) * sstride;
-      const T uu = U[v * NS + s];
+      const T uu = U[q][v];
       T F;
-      if (v == 0) F = mom[q];
+      if (v == 0) F = U[q][1 + d];
       else if (v == NV - 1) F = un[q] * (uu + pr[q]);
       else F = (v - 1 == d) ? uu * un[q] + pr[q] : uu * un[q];
       fp[q] = T(0.5) * (F + a * uu);
@@ -725,6 +786,23 @@ __device__ inline void face_flux_smem(const T* U, const T* P, int s0, int sstrid
     }
     Fh[v] = weno5<T>(fp[0], fp[1], fp[2], fp[3], fp[4], eps) + weno5<T>(fm[5], fm[4], fm[3], fm[2], fm[1], eps);
   }
+}
+
+template <int D, typename T>
+__device__ inline void face_flux_smem(const T* U, const T* P, int s0, int sstride, int d, int NS, T eps, T* Fh) {
+  // U[v*NS + s], P[e*NS + s] with e: 0..D-1 velocities, D pressure, D+1 sound speed
+  constexpr int NV = D + 2;
+  T u[6][NV], un[6], pr[6], cs[6];
+#pragma unroll
+  for (int q = 0; q < 6; q++) {
+    const int s = s0 + (q - 2) * sstride;
+#pragma unroll
+    for (int v = 0; v < NV; v++) u[q][v] = U[v * NS + s];
+    un[q] = P[d * NS + s];
+    pr[q] = P[D * NS + s];
+    cs[q] = P[(D + 1) * NS + s];
+  }
+  face_flux_regs<D, T>(u, un, pr, cs, d, eps, Fh);
 }
 
 // one face of a flux tile: aperture, WENO5-LLF flux and the boundary ledger.
@@ -896,29 +974,14 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
       for (int v = 0; v < NV; v++) U[v * NS + s] = u[v];
       bad[s] = 0;
       if (!isnan(u[0])) {
-        // primitive state (same arithmetic as cons_to_prim)
-        const T rho = u[0];
-        T vel[D];
-        T qsum = T(0);
-#pragma unroll
-        for (int e = 0; e < D; e++) vel[e] = u[1 + e] / rho;
-#pragma unroll
-        for (int e = 0; e < D; e++) qsum += vel[e] * vel[e];
-        const T ke = T(0.5) * rho * qsum;
-        const T pres = mgm1 * (u[D + 1] - ke) - mgpi;
+        T vel[D], pres, cs;
+        bool isbad;
+        stencil_prim<D, T>(u, mgm1, mgpi, mgam, mpinf, vel, pres, cs, isbad);
 #pragma unroll
         for (int e = 0; e < D; e++) P[e * NS + s] = vel[e];
         P[D * NS + s] = pres;
-        T c2 = (mgam * (pres + mpinf)) / rho;
-        const T w0 = rho;
-        T w[NV];
-        w[0] = w0;
-        (void)w;
-        if (!(w0 > T(0)) || !(c2 > T(0))) {
-          bad[s] = 1;  // reported only if a used face reads it
-          c2 = c2 > T(0) ? c2 : T(0);
-        }
-        P[(D + 1) * NS + s] = sqrt(c2);
+        P[(D + 1) * NS + s] = cs;
+        bad[s] = isbad ? 1 : 0;  // reported only if a used face reads it
       }
     }
     __syncthreads();
@@ -989,12 +1052,11 @@ __global__ void k_ledger(const __grid_constant__ Grid g, const __grid_constant__
 // --------------------------------------------- level-set stage (a9) + R
 __device__ inline double phir_stage(const Bufs& b, long long c, int r) { return phi_m(b.phi, b.chi, c, r); }
 
-__global__ void k_levelset(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* vel, double beta, double omb) {
-  if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband, N = g.N, D = g.D;
+__device__ __forceinline__ void phase_levelset(const Grid& g, const Bufs& b, const double* vel, double beta, double omb, int first_, int stride_) {
+    const int nb = b.ctl->nband, N = g.N, D = g.D;
   const double dt = b.ctl->dt, eps = g.weno_eps;
   const int total = nb * N;
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+  for (int it = first_; it < total; it += stride_) {
     const int r = it / nb, k = it - r * nb;
     const long long c = b.band[k];
     if (!((b.xsS[c] >> r) & 1u)) continue;
@@ -1026,11 +1088,14 @@ __global__ void k_levelset(const __grid_constant__ Grid g, const __grid_constant
     b.phir[(long long)k * N + r] = beta * phn + omb * (phir_stage(b, c, r) - dt * adv);
   }
 }
-// reconstruction R: |max_r phi^r| and argmax (lowest index on ties), clamped
-__global__ void k_levelset_R(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+__global__ void k_levelset(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* vel, double beta, double omb) {
   if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband, N = g.N;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+  phase_levelset(g, b, vel, beta, omb, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+// reconstruction R: |max_r phi^r| and argmax (lowest index on ties), clamped
+__device__ __forceinline__ void phase_levelset_R(const Grid& g, const Bufs& b, int first_, int stride_) {
+    const int nb = b.ctl->nband, N = g.N;
+  for (int k = first_; k < nb; k += stride_) {
     const long long c = b.band[k];
     const unsigned bits = b.xsS[c];
     double best = 0.0;
@@ -1049,15 +1114,22 @@ __global__ void k_levelset_R(const __grid_constant__ Grid g, const __grid_consta
     b.chi[c] = (uint8_t)arg;
   }
 }
-// scatter band-indexed (phi, chi) back; flag selects which cells are written
-__global__ void k_scatter_phichi(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+__global__ void k_levelset_R(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
   if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+  phase_levelset_R(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+// scatter band-indexed (phi, chi) back; flag selects which cells are written
+__device__ __forceinline__ void phase_scatter_phichi(const Grid& g, const Bufs& b, int first_, int stride_) {
+    const int nb = b.ctl->nband;
+  for (int k = first_; k < nb; k += stride_) {
     const long long c = b.band[k];
     b.phi[c] = b.phit[k];
     b.chi[c] = b.chit[k];
   }
+}
+__global__ void k_scatter_phichi(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+  if (!ctl_active(b)) return;
+  phase_scatter_phichi(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // ------------------------------------------------------------ mixing (a11)
@@ -1146,12 +1218,11 @@ __device__ inline bool is_small(const Grid& g, const Bufs& b, const double* Qc, 
 
 // per (band cell, material): small-cell test and, for a small cell, its
 // targets and normalised weights (mixn: 0xff not small, else target count)
-__global__ void k_mix_mark(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qc) {
-  if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband, N = g.N;
+__device__ __forceinline__ void phase_mix_mark(const Grid& g, const Bufs& b, const double* Qc, int first_, int stride_) {
+    const int nb = b.ctl->nband, N = g.N;
   unsigned long long nsmall = 0, nfail = 0;
   const int total = nb * N;
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+  for (int it = first_; it < total; it += stride_) {
     const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
     const long long r = (long long)k * N + m;
@@ -1173,14 +1244,17 @@ __global__ void k_mix_mark(const __grid_constant__ Grid g, const __grid_constant
   if (nsmall) atomicAdd(&b.ctl->cnt[C_SMALL], nsmall);
   if (nfail) atomicAdd(&b.ctl->cnt[C_MIXFAIL], nfail);
 }
+__global__ void k_mix_mark(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qc) {
+  if (!ctl_active(b)) return;
+  phase_mix_mark(g, b, Qc, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
 
 // new state of material m of every band cell: own exchanges minus the
 // exchanges its small neighbours send to it (lexicographic neighbour order)
-__global__ void k_mix_compute(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qc) {
-  if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
+__device__ __forceinline__ void phase_mix_compute(const Grid& g, const Bufs& b, const double* Qc, int first_, int stride_) {
+    const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
   const int total = nb * N;
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+  for (int it = first_; it < total; it += stride_) {
     const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
     const long long r = (long long)k * N + m;
@@ -1230,13 +1304,16 @@ __global__ void k_mix_compute(const __grid_constant__ Grid g, const __grid_const
     for (int v = 0; v < NV; v++) out[v] = Qc[qidx(g, m, v, c)] + acc[v];
   }
 }
+__global__ void k_mix_compute(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qc) {
+  if (!ctl_active(b)) return;
+  phase_mix_compute(g, b, Qc, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
 // write the mixed states back; a material that lost all volume and has no
 // same-material neighbour is merged into the cell's primary material
-__global__ void k_mix_scatter(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, double* Qc) {
-  if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband, N = g.N, NV = g.NV;
+__device__ __forceinline__ void phase_mix_scatter(const Grid& g, const Bufs& b, double* Qc, int first_, int stride_) {
+    const int nb = b.ctl->nband, N = g.N, NV = g.NV;
   unsigned long long nmerge = 0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+  for (int k = first_; k < nb; k += stride_) {
     const long long c = b.band[k];
     double* in = b.mixq + (long long)k * N * NV;
     const unsigned mb = b.mixmerge[k];
@@ -1257,14 +1334,17 @@ __global__ void k_mix_scatter(const __grid_constant__ Grid g, const __grid_const
   }
   if (nmerge) atomicAdd(&b.ctl->cnt[C_MERGE], nmerge);
 }
+__global__ void k_mix_scatter(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, double* Qc) {
+  if (!ctl_active(b)) return;
+  phase_mix_scatter(g, b, Qc, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
 
 // ------------------------------------------------- scale separation (a12)
-__global__ void k_scale_sep(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
-  if (!ctl_active(b)) return;
-  const int nb = b.ctl->nband, N = g.N, D = g.D;
+__device__ __forceinline__ void phase_scale_sep(const Grid& g, const Bufs& b, int first_, int stride_) {
+    const int nb = b.ctl->nband, N = g.N, D = g.D;
   const double eps = g.eps_ss;
   unsigned long long nodd = 0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+  for (int k = first_; k < nb; k += stride_) {
     const long long c = b.band[k];
     b.phit[k] = b.phi[c];
     b.chit[k] = b.chi[c];
@@ -1325,6 +1405,10 @@ __global__ void k_scale_sep(const __grid_constant__ Grid g, const __grid_constan
     b.chit[k] = (uint8_t)chs;
   }
   if (nodd) atomicAdd(&b.ctl->cnt[C_ODDBALL], nodd);
+}
+__global__ void k_scale_sep(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+  if (!ctl_active(b)) return;
+  phase_scale_sep(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // --------------------------------------------- band distance maintenance
@@ -1404,6 +1488,234 @@ __global__ void k_totals(const __grid_constant__ Grid g, const double* Q, double
     __syncthreads();
   }
   if (threadIdx.x == 0) out[mv] = red[0] * g.V;
+}
+
+
+// --------------------------------------------------- batched 1D instances
+// One CTA owns one 1D instance and runs whole steps with block barriers
+// between the phases: every phase calls the same per-item functions as the
+// grid kernels, so each instance gets the grid path's arithmetic.
+
+// aperture and WENO5-LLF flux of every face of a 1D instance (global-memory
+// stencils; same arithmetic as the tiled kernel)
+template <typename T>
+__device__ __forceinline__ void flux1d_faces(const Grid& g, const Bufs& b, const double* Qs, T* Ff, double* Af,
+                                             const BndBase& bb, int first, int stride, unsigned& err) {
+  constexpr int NV = 3;
+  const int N = g.N, n = g.n[0], nf = n + 1, off = g.off[0];
+  const T eps = (T)g.weno_eps;
+  for (int it = first; it < nf * N; it += stride) {
+    const int m = it / nf, f = it - m * nf;
+    const long long cR = off + f, cL = cR - 1;
+    const bool lin = f >= 1, rin = f < n;
+    const unsigned um = (lin ? b.smask[cL] : 0u) | (rin ? b.smask[cR] : 0u);
+    double Af_ = 0.0;
+    T Fh[NV] = {T(0), T(0), T(0)};
+    if ((um >> m) & 1u) {
+      Af_ = face_aperture(g, b, cL, cR, 0, m);
+      if (Af_ > 0.0) {
+        if ((lin && !((b.smask[cL] >> m) & 1u)) || (rin && !((b.smask[cR] >> m) & 1u))) err |= ERR_BAND;
+        const T mgm1 = T(g.gm1[m]), mgpi = T(g.gpi[m]), mgam = T(g.gamma[m]), mpinf = T(g.pinf[m]);
+        T u[6][NV], un[6], pr[6], cs[6];
+        bool avail = true, isbad = false;
+        for (int q = 0; q < 6; q++) {
+          const long long k = cL + (q - 2);
+          const bool inner = k >= off && k < off + n;
+          if (inner) {
+            interior_uhat<T>(g, b, Qs, k, m, u[q]);
+          } else {
+            const T* Uh = (const T*)b.Uh;
+            for (int v = 0; v < NV; v++) u[q][v] = Uh[qidx(g, m, v, k)];
+          }
+          if (isnan(u[q][0])) {
+            avail = false;
+            continue;
+          }
+          T vel[1];
+          bool bq;
+          stencil_prim<1, T>(u[q], mgm1, mgpi, mgam, mpinf, vel, pr[q], cs[q], bq);
+          un[q] = vel[0];
+          isbad = isbad || bq;
+        }
+        if (!avail) {
+          err |= ERR_BAND;
+        } else {
+          if (isbad) err |= ERR_NEGATIVE;
+          face_flux_regs<1, T>(u, un, pr, cs, 0, eps, Fh);
+        }
+      }
+    }
+    Af[(long long)m * nf + f] = Af_;
+    for (int v = 0; v < NV; v++) Ff[((long long)m * NV + v) * nf + f] = Fh[v];
+    if (f == 0 || f == n) {
+      const long long fid = f == 0 ? bb.base[0] : bb.base[1];
+      const double sgn = f == 0 ? 1.0 : -1.0;
+      for (int v = 0; v < NV; v++) b.bflux[((fid * g.N) + m) * NV + v] = sgn * (Af_ * (double)Fh[v] * g.farea[0]);
+    }
+  }
+}
+
+// RK stage update of every (cell, material) of a 1D instance
+template <typename T>
+__device__ __forceinline__ void flux1d_update(const Grid& g, const Bufs& b, const double* Qs, const double* Qn,
+                                              double* Qout, double beta, double omb, const T* Ff, const double* Af,
+                                              int first, int stride, unsigned& err) {
+  constexpr int NV = 3;
+  const int N = g.N, n = g.n[0], nf = n + 1, off = g.off[0];
+  const double dt = b.ctl->dt;
+  for (int it = first; it < n * N; it += stride) {
+    const int m = it / n, i = it - m * n;
+    const long long c = off + i;
+    if (!((b.smask[c] >> m) & 1u)) continue;
+    const bool cut = (b.gflag[c] & GF_CUT) != 0;
+    for (int v = 0; v < NV; v++) {
+      double L = 0.0;
+      const double fl = (double)Ff[((long long)m * NV + v) * nf + i], fh = (double)Ff[((long long)m * NV + v) * nf + i + 1];
+      L = L + (Af[(long long)m * nf + i] * fl - Af[(long long)m * nf + i + 1] * fh) * g.rh[0];
+      if (cut) L = L + b.X[qidx(g, m, v, c)] * g.rV;
+      const long long qi = qidx(g, m, v, c);
+      const double qv = beta * Qn[qi] + omb * (Qs[qi] + dt * L);
+      if (!isfinite(qv)) err |= ERR_NONFINITE;
+      Qout[qi] = qv;
+    }
+  }
+}
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int* order, int n_steps) {
+  const BatchEntry& E = tab[order[blockIdx.x]];
+  const Grid& g = E.g;
+  const Bufs& b = E.b;
+  const int t = threadIdx.x, nt = BS;
+  T* Ff = (T*)E.Fface;
+  double* Af = E.Aface;
+  const double BETA[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double LW[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+  for (int step = 0; step < n_steps; step++) {
+    if (t == 0) {
+      Ctl* c = b.ctl;
+      c->active = (c->t < c->t_end && c->err == 0) ? 1 : 0;
+      c->nband = 0;
+      c->lam_bits = 0ull;
+    }
+    __syncthreads();
+    if (!*(volatile int*)&b.ctl->active) break;
+    phase_bc_phichi(g, b, t, nt);
+    __syncthreads();
+    phase_xs(g, b, t, nt);
+    __syncthreads();
+    phase_dilate(g, b, b.xs, b.mtmp, 0, t, nt);
+    __syncthreads();
+    phase_band(g, b, b.mtmp, t, nt);
+    __syncthreads();
+    phase_geom_mat(g, b, t, nt);
+    __syncthreads();
+    phase_geom_cell(g, b, b.Q[0], (const double*)nullptr, t, nt);
+    __syncthreads();
+    phase_band_save(g, b, t, nt);
+    __syncthreads();
+    for (int s = 0; s < 3; s++) {
+      const double* Qs = b.Q[s];
+      double* Qo = b.Q[(s + 1) % 3];
+      phase_prim<T>(g, b, Qs, t, nt);
+      __syncthreads();
+      int cur = 0;
+      for (int k = 0; k < g.ext_sweeps; k++) {
+        if (cur) extend_items<T>(g, b, b.W1, b.W0, b.f1, b.f0, t, nt);
+        else extend_items<T>(g, b, b.W0, b.W1, b.f0, b.f1, t, nt);
+        cur ^= 1;
+        __syncthreads();
+      }
+      phase_cons<T>(g, b, Qs, cur ? b.W1 : b.W0, cur ? b.f1 : b.f0, t, nt);
+      __syncthreads();
+      phase_bc_uhat<T>(g, b, Qs, t, nt);
+      __syncthreads();
+      if (s == 0) {
+        unsigned err = 0;
+        const double lam = block_max(dt_items<T>(g, b, Qs, t, nt, err));
+        if (err) atomicOr(&b.ctl->err, err);
+        if (t == 0) {
+          Ctl* c = b.ctl;
+          c->lam = lam;
+          double dt = g.cfl / lam;
+          int last = 0;
+          if (c->t + dt >= c->t_end) {
+            dt = c->t_end - c->t;
+            last = 1;
+          }
+          c->dt = dt;
+          c->last = last;
+        }
+        __syncthreads();
+      }
+      phase_interface<T>(g, b, Qs, t, nt);
+      __syncthreads();
+      int vc = 0;
+      for (int k = 0; k < g.vel_sweeps; k++) {
+        if (vc) extend_vel_items(g, b, b.vel1, b.vel0, b.vf1, b.vf0, t, nt);
+        else extend_vel_items(g, b, b.vel0, b.vel1, b.vf0, b.vf1, t, nt);
+        vc ^= 1;
+        __syncthreads();
+      }
+      unsigned err = 0;
+      flux1d_faces<T>(g, b, Qs, Ff, Af, E.bb, t, nt, err);
+      __syncthreads();
+      flux1d_update<T>(g, b, Qs, b.Q[0], Qo, BETA[s], 1.0 - BETA[s], Ff, Af, t, nt, err);
+      if (err) atomicOr(&b.ctl->err, err);
+      __syncthreads();
+      for (int mv = t; mv < g.N * g.NV; mv += nt) {
+        double sum = 0.0;
+        for (int f = 0; f < E.nbnd; f++) sum += b.bflux[(long long)f * g.N * g.NV + mv];
+        b.ctl->ledger[mv / g.NV][mv % g.NV] += LW[s] * b.ctl->dt * sum;
+      }
+      __syncthreads();
+      phase_levelset(g, b, vc ? b.vel1 : b.vel0, BETA[s], 1.0 - BETA[s], t, nt);
+      __syncthreads();
+      phase_levelset_R(g, b, t, nt);
+      __syncthreads();
+      phase_bc_phichi(g, b, t, nt);
+      __syncthreads();
+      phase_geom_mat(g, b, t, nt);
+      __syncthreads();
+      phase_geom_cell(g, b, (const double*)Qo, (const double*)nullptr, t, nt);
+      __syncthreads();
+      phase_mix_mark(g, b, (const double*)Qo, t, nt);
+      __syncthreads();
+      phase_mix_compute(g, b, (const double*)Qo, t, nt);
+      __syncthreads();
+      phase_mix_scatter(g, b, Qo, t, nt);
+      __syncthreads();
+    }
+    if (t == 0) {
+      Ctl* c = b.ctl;
+      c->t = c->last ? c->t_end : c->t + c->dt;
+      c->cnt[C_STEPS] += 1;
+    }
+    __syncthreads();
+    if (g.scale_sep) {
+      phase_scale_sep(g, b, t, nt);
+      __syncthreads();
+      phase_scatter_phichi(g, b, t, nt);
+      __syncthreads();
+      phase_bc_phichi(g, b, t, nt);
+      __syncthreads();
+    }
+    if (g.reinit) {
+      for (int k = 0; k < g.reinit_iters; k++) {
+        reinit_items(g, b, t, nt);
+        __syncthreads();
+        scatter_items(b, t, nt);
+        __syncthreads();
+      }
+      phase_bc_phichi(g, b, t, nt);
+      __syncthreads();
+    }
+  }
+}
+
+// end times of every instance of a batch
+__global__ void k_set_tend_all(const BatchEntry* tab, int n, double t_end) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) tab[i].b.ctl->t_end = t_end;
 }
 
 }  // namespace

@@ -6,6 +6,7 @@
 #include "msf_types.cuh"
 
 namespace msf {
+struct BatchEntry;
 
 // launchers of the kernels whose bulk arithmetic type depends on the precision
 struct Ops {
@@ -19,7 +20,10 @@ struct Ops {
   void (*interface)(const Grid&, const Bufs&, const double* Qs, int nblk, cudaStream_t);
   cudaError_t (*flux)(const Grid&, const Bufs&, const double* Qs, const double* Qn, double* Qout, double beta,
                       double omb, const BndBase&, cudaStream_t);
+  // n_steps steps of every 1D instance of a batch, one CTA of bs threads per instance
+  cudaError_t (*batched)(const BatchEntry* tab, const int* order, int n_inst, int n_steps, int bs, cudaStream_t);
 };
+void launch_set_tend_all(const BatchEntry* tab, int n, double t_end, cudaStream_t);
 const Ops* ops_f64();
 const Ops* ops_f32();
 

@@ -49,4 +49,14 @@ struct BndBase {
   long long base[6];
 };
 
+// one instance of a batch of 1D problems run by the persistent kernel
+struct BatchEntry {
+  Grid g;
+  Bufs b;
+  BndBase bb;
+  void* Fface;    // T [N][NV][n + 1] face fluxes of the stage
+  double* Aface;  // [N][n + 1] face apertures of the stage
+  int nbnd;
+};
+
 }  // namespace msf

@@ -44,7 +44,7 @@ class msf_options(C.Structure):
                 ("ext_sweeps", C.c_int32), ("vel_sweeps", C.c_int32), ("reinit_iters", C.c_int32),
                 ("scale_sep", C.c_int32), ("reinit", C.c_int32), ("scale_eps_h", C.c_double),
                 ("phi_cap_h", C.c_double), ("use_graph", C.c_int32), ("profile", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("batch_mode", C.c_int32), ("stream", C.c_void_p)]
 
 
 class MsfError(RuntimeError):
@@ -75,6 +75,8 @@ def _load():
         "msf_debug_field": ([P, C.c_int32, C.c_int32, dp], C.c_int),
         "msf_launches_per_step": ([P, C.POINTER(C.c_int64)], C.c_int),
         "msf_profile_read": ([P, dp], C.c_int),
+        "msf_batch_block_size": ([P, C.POINTER(C.c_int32)], C.c_int),
+        "msf_instance_info": ([P, C.c_int32, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)], C.c_int),
         "msf_cfl_dt_noalloc": ([P, C.c_int64, C.c_int32, C.POINTER(msf_eos), dp, C.c_double, P, P], C.c_int),
         "msf_last_error": ([P], C.c_char_p),
     }
@@ -102,6 +104,8 @@ msf_last_dt = _lib.msf_last_dt
 msf_debug_field = _lib.msf_debug_field
 msf_launches_per_step = _lib.msf_launches_per_step
 msf_profile_read = _lib.msf_profile_read
+msf_batch_block_size = _lib.msf_batch_block_size
+msf_instance_info = _lib.msf_instance_info
 msf_cfl_dt_noalloc = _lib.msf_cfl_dt_noalloc
 msf_last_error = _lib.msf_last_error
 
@@ -243,3 +247,93 @@ class Solver:
         out = np.zeros(sizes[which] * self.cells)
         _check(msf_debug_field(self.h, 0, int(which), out.ctypes.data_as(C.POINTER(C.c_double))), self.h)
         return out
+
+
+def pad_materials(case, nmat):
+    """The same case with unused materials appended (EOS of an ideal gas, a
+    resting unit state); they never appear in chi, so nothing changes."""
+    import copy
+    c = copy.copy(case)
+    extra = nmat - case.nmat
+    if extra <= 0:
+        return c
+    c.gamma = list(case.gamma) + [1.4] * extra
+    c.pinf = list(case.pinf) + [0.0] * extra
+    pad = np.zeros((extra, case.nv, case.cells))
+    pad[:, 0] = 1.0
+    pad[:, -1] = 1.0
+    c.prim = np.concatenate([case.prim, pad], axis=0)
+    return c
+
+
+class Batch:
+    """One context holding many instances of the same dimension (the batched
+    form: one persistent launch per msf_step call for 1D instances)."""
+
+    def __init__(self, cases, precision=MSF_FP64, batch_mode=0, stream=None, **opts):
+        self.nmat = max(c.nmat for c in cases)
+        self.cases = [pad_materials(c, self.nmat) for c in cases]
+        self.n = len(cases)
+        ps = [c.params(**opts) for c in self.cases]
+        grids = (msf_grid * self.n)(*[make_grid(p) for p in ps])
+        eos = (msf_eos * (self.n * self.nmat))(*[msf_eos(p["gamma"][m], p["pinf"][m]) for p in ps
+                                                 for m in range(self.nmat)])
+        self._keep = (grids, eos)
+        self._opt = make_options(ps[0], precision, stream, 1, 0)
+        self._opt.batch_mode = int(batch_mode)
+        h = C.c_void_p()
+        st = msf_create(grids, self.n, self.nmat, eos, C.byref(self._opt), C.byref(h))
+        if st != MSF_OK:
+            raise MsfError(st, msf_last_error(None).decode())
+        self.h = h
+        for i, c in enumerate(self.cases):
+            phi = np.ascontiguousarray(c.phi, np.float64).ravel()
+            chi = np.ascontiguousarray(c.chi, np.int32).ravel()
+            prim = np.ascontiguousarray(c.prim, np.float64)
+            _check(msf_set_levelset(h, i, C.c_void_p(phi.ctypes.data), C.c_void_p(chi.ctypes.data),
+                                    C.c_void_p(prim.ctypes.data), MSF_HOST), h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            msf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def step(self, n_steps, t_end=float("inf"), sync=True):
+        _check(msf_step(self.h, int(n_steps), float(t_end), 1 if sync else 0), self.h)
+
+    def state(self, i):
+        c = self.cases[i]
+        Q = np.zeros((self.nmat, c.nv, c.cells))
+        alpha = np.zeros((self.nmat, c.cells))
+        phi = np.zeros(c.cells)
+        chi = np.zeros(c.cells, np.int32)
+        t = C.c_double()
+        _check(msf_get_state(self.h, int(i), C.c_void_p(Q.ctypes.data), C.c_void_p(alpha.ctypes.data),
+                             C.c_void_p(phi.ctypes.data), C.c_void_p(chi.ctypes.data), C.byref(t), MSF_HOST), self.h)
+        return dict(Q=Q, alpha=alpha, phi=phi, chi=chi, t=t.value)
+
+    def totals(self, i):
+        c = self.cases[i]
+        tot = np.zeros((self.nmat, c.nv))
+        led = np.zeros((self.nmat, c.nv))
+        _check(msf_totals(self.h, int(i), tot.ctypes.data_as(C.POINTER(C.c_double)),
+                          led.ctypes.data_as(C.POINTER(C.c_double))), self.h)
+        return tot, led
+
+    def info(self, i):
+        t, steps, status = C.c_double(), C.c_int64(), C.c_int32()
+        _check(msf_instance_info(self.h, int(i), C.byref(t), C.byref(steps), C.byref(status)), self.h)
+        return t.value, steps.value, status.value
+
+    def block_size(self):
+        bs = C.c_int32()
+        _check(msf_batch_block_size(self.h, C.byref(bs)), self.h)
+        return bs.value
+
+    def launches_per_step(self):
+        n = C.c_int64()
+        _check(msf_launches_per_step(self.h, C.byref(n)), self.h)
+        return n.value
