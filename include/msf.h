@@ -152,10 +152,60 @@ msf_status msf_step(msf_ctx* ctx, int32_t n_steps, double t_end, int32_t sync);
  * exchange moves between materials). Host arrays [n_mat][dim + 2]. Synchronises. */
 msf_status msf_totals(msf_ctx* ctx, int32_t instance, double* totals, double* ledger);
 
-/* Adjoint of one step (reverse-mode derivative of the state after the last
- * step with respect to the state before it). Not provided by this build:
- * returns MSF_EUNSUPPORTED. */
-msf_status msf_adjoint_step(msf_ctx* ctx, const void* lam_out, void* lam_in, double* d_eos);
+/* ---------------------------------------------------------------------------
+ * Differentiation at frozen interface evolution (single-instance contexts).
+ *
+ * A tape records one step: the time t and time step dt of the step, the
+ * conserved state Q^n, and the level set (phi, chi) after the boundary fill at
+ * the start of each of the three stages and after the level-set stage of the
+ * last stage. Replaying a tape advances the current conserved state by one
+ * step with the interface evolution frozen to the tape: the level set of each
+ * stage is the recorded one instead of the advected one (Sec. 2.2), the time
+ * step is the recorded one, band maintenance and scale separation are left
+ * out, and every discrete choice made from the state (interface pair, the
+ * correction's material of Eq. vol_corr2, small cells and mixing targets) is
+ * re-made from the replayed state. What the replay computes from the
+ * conserved state and the EOS parameters is the flow part of the step
+ * (Sec. 2.3: primitive recovery, ghost extension, reduced interface exchange,
+ * aperture-weighted WENO5-LLF fluxes, the RK combination of Eq.
+ * local-advection, mixing); the adjoint step is its exact reverse-mode
+ * derivative (up to the discrete choices, which it holds fixed).
+ * Tape memory is device memory owned by the caller, 256-byte aligned, of
+ * msf_tape_bytes bytes; a tape is independent of the context that wrote it
+ * (a context with the same grid and options but other EOS parameters or
+ * inflow states may replay it).
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of one tape. MSF_EUNSUPPORTED for several instances. */
+msf_status msf_tape_bytes(const msf_ctx* ctx, int64_t* bytes);
+
+/* One full step (as msf_step with n_steps = 1, sync = 1) that also writes its
+ * tape. MSF_EINVAL if t >= t_end (no step) or the tape pointer is not aligned. */
+msf_status msf_step_taped(msf_ctx* ctx, void* tape, double t_end);
+
+/* One step from the current conserved state (see msf_set_conserved) with the
+ * interface evolution frozen to the tape. Sets t = tape t + tape dt; phi and
+ * chi end as the tape's level set after the last level-set stage. Synchronises. */
+msf_status msf_replay_step(msf_ctx* ctx, const void* tape);
+
+/* Replace the conserved state of the interior cells (SoA [n_mat][dim+2][cells],
+ * x fastest; host or device per mem), keeping phi, chi, t, ledger, counters. */
+msf_status msf_set_conserved(msf_ctx* ctx, int32_t instance, const double* Q, int32_t mem);
+
+/* Adjoint of the replayed step of a tape: given lam_out = dJ/dQ^{n+1} (device,
+ * SoA [n_mat][dim+2][cells] of the interior cells), writes lam_in = dJ/dQ^n
+ * (device, same layout; may not alias lam_out) and ADDS dJ/d(gamma_m, pinf_m)
+ * to d_eos[m][2] and dJ/d(inflow primitive state) to d_inflow[3][2][5] (host
+ * arrays; either may be NULL), for J(Q^{n+1}) and the replay map
+ * Q^{n+1}(Q^n, gamma, pinf, inflow). Recomputes the stages from the tape
+ * (stage checkpointing), then pulls lam back through mixing, the RK
+ * combination, fluxes and exchange, boundary states, stencil states,
+ * extension sweeps and primitive recovery of each stage in reverse order.
+ * Leaves the context at the tape's starting state (Q^n, phi, chi, t of the
+ * tape). Synchronises. Errors: MSF_EINVAL (alignment, empty tape),
+ * MSF_EUNSUPPORTED (several instances), device errors as msf_step. */
+msf_status msf_adjoint_step(msf_ctx* ctx, const void* tape, const double* lam_out, double* lam_in, double* d_eos,
+                            double* d_inflow);
 
 /* Copy one instance's state out (all outputs optional, NULL skips):
  *   Q [n_mat][dim+2][cells] conserved alpha U, alpha [n_mat][cells] volume

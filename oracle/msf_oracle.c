@@ -1224,45 +1224,99 @@ static void reinit(orc* o) {
 /* ------------------------------------------------------------------ */
 /* driver                                                               */
 /* ------------------------------------------------------------------ */
+/* One full step. Record mode (tphi != NULL, replay == 0): the level set after
+ * the boundary fill at the start of every stage and after the level-set stage
+ * of the last stage is copied to tape slots 0..3 and the time step to *tdt.
+ * Replay mode (replay == 1): the interface evolution is frozen to a recorded
+ * tape. Slot s replaces the level set at the start of stage s, slot s+1 the
+ * level-set stage of stage s, and the time step is *tdt; band maintenance
+ * and scale separation are skipped (the next step's tape brings their result).
+ * What remains a function of the conserved state is the flow part of the
+ * step: primitive recovery, ghost extension, interface exchange, fluxes,
+ * RK combination and mixing, with every volume fraction, aperture and normal
+ * taken from the recorded interface. */
+static int step_once(orc* o, double t_end, double* tphi, uint8_t* tchi, double* tdt, int replay) {
+  const long nc = o->ncell;
+  if (replay) {
+    memcpy(o->phi, tphi, sizeof(double) * nc);
+    memcpy(o->chi, tchi, nc);
+  } else {
+    bc_phichi(o);
+    if (tphi) {
+      memcpy(tphi, o->phi, sizeof(double) * nc);
+      memcpy(tchi, o->chi, nc);
+    }
+  }
+  step_band(o);
+  geometry(o, o->Q);
+  memcpy(o->phin, o->phi, sizeof(double) * nc);
+  memcpy(o->chin, o->chi, nc);
+  int last = 0;
+  for (int s = 0; s < 3; s++) {
+    double* Qs = s == 0 ? o->Q : (s == 1 ? o->Q1 : o->Q2);
+    double* Qo = s == 0 ? o->Q1 : (s == 1 ? o->Q2 : o->Q);
+    prim_extend(o, Qs);
+    bc_uhat(o);
+    if (s == 0) {
+      if (replay) {
+        o->dt = *tdt;
+      } else {
+        compute_dt(o, t_end);
+        last = o->t + o->dt >= t_end;
+        if (tdt) *tdt = o->dt;
+      }
+    }
+    interface_exchange(o, Qs);
+    if (!replay) extend_velocity(o);
+    flux_update(o, s, Qs, Qo);
+    if (replay) {
+      memcpy(o->phi, tphi + (long)(s + 1) * nc, sizeof(double) * nc);
+      memcpy(o->chi, tchi + (long)(s + 1) * nc, nc);
+    } else {
+      levelset_stage(o, s);
+      bc_phichi(o);
+      if (tphi) {
+        memcpy(tphi + (long)(s + 1) * nc, o->phi, sizeof(double) * nc);
+        memcpy(tchi + (long)(s + 1) * nc, o->chi, nc);
+      }
+    }
+    geometry(o, Qo);
+    mixing(o, Qo);
+  }
+  o->t = last ? t_end : o->t + o->dt;
+  o->cnt[ORC_C_STEPS]++;
+  if (replay) return o->err;
+  if (o->p.scale_sep) {
+    scale_separation(o);
+    bc_phichi(o);
+  }
+  if (o->p.reinit) {
+    reinit(o);
+    bc_phichi(o);
+  }
+  return o->err;
+}
+
 int orc_step(orc* o, int32_t nsteps, double t_end) {
   for (int it = 0; it < nsteps; it++) {
     if (o->err) return o->err;
     if (!(o->t < t_end)) break;
-    bc_phichi(o);
-    step_band(o);
-    geometry(o, o->Q);
-    memcpy(o->phin, o->phi, sizeof(double) * o->ncell);
-    memcpy(o->chin, o->chi, o->ncell);
-    int last = 0;
-    for (int s = 0; s < 3; s++) {
-      double* Qs = s == 0 ? o->Q : (s == 1 ? o->Q1 : o->Q2);
-      double* Qo = s == 0 ? o->Q1 : (s == 1 ? o->Q2 : o->Q);
-      prim_extend(o, Qs);
-      bc_uhat(o);
-      if (s == 0) {
-        compute_dt(o, t_end);
-        last = o->t + o->dt >= t_end;
-      }
-      interface_exchange(o, Qs);
-      extend_velocity(o);
-      flux_update(o, s, Qs, Qo);
-      levelset_stage(o, s);
-      bc_phichi(o);
-      geometry(o, Qo);
-      mixing(o, Qo);
-    }
-    o->t = last ? t_end : o->t + o->dt;
-    o->cnt[ORC_C_STEPS]++;
-    if (o->p.scale_sep) {
-      scale_separation(o);
-      bc_phichi(o);
-    }
-    if (o->p.reinit) {
-      reinit(o);
-      bc_phichi(o);
-    }
+    step_once(o, t_end, NULL, NULL, NULL, 0);
   }
   return o->err;
+}
+
+long orc_ncell(const orc* o) { return o->ncell; }
+
+int orc_step_taped(orc* o, double t_end, double* tphi, uint8_t* tchi, double* tdt) {
+  if (o->err) return o->err;
+  if (!(o->t < t_end)) return -1;
+  return step_once(o, t_end, tphi, tchi, tdt, 0);
+}
+
+int orc_replay_step(orc* o, const double* tphi, const uint8_t* tchi, double dt) {
+  if (o->err) return o->err;
+  return step_once(o, 0.0, (double*)tphi, (uint8_t*)tchi, &dt, 1);
 }
 
 orc* orc_create(const orc_params* p) {
@@ -1438,6 +1492,22 @@ void orc_set_state(orc* o, const double* Q, const double* phi, const int32_t* ch
   bc_phichi(o);
   step_band(o);
   geometry(o, o->Q);
+}
+
+/* overwrite the conserved state of the interior cells (SoA [N][NV][cells]),
+ * keeping the level set, the time and the counters */
+void orc_set_conserved(orc* o, const double* Q) {
+  int N = o->N, NV = o->NV;
+  long ni = n_interior(o);
+  for (long c = 0; c < o->ncell; c++) {
+    int ijk[3];
+    coords(o, c, ijk);
+    if (!interior(o, ijk)) continue;
+    long q = interior_index(o, ijk);
+    for (int m = 0; m < N; m++)
+      for (int v = 0; v < NV; v++) o->Q[QI(o, m, v, c)] = Q[((long)m * NV + v) * ni + q];
+  }
+  o->err = 0;
 }
 
 void orc_totals(const orc* o, double* totals, double* ledger) {

@@ -43,6 +43,15 @@ orc* orc_create(const orc_params* p);
 void orc_destroy(orc* o);
 int orc_set_levelset(orc* o, const double* phi, const int32_t* chi, const double* prim);
 int orc_step(orc* o, int32_t nsteps, double t_end);
+/* replay tape of one step: level set (phi [4][ncell], chi [4][ncell], padded
+ * layout) at the start of each stage and after the last level-set stage, and
+ * the time step. orc_step_taped takes one step and records it (-1: t >= t_end);
+ * orc_replay_step takes one step from the current conserved state with the
+ * interface evolution frozen to the tape (the flow part of the step only). */
+long orc_ncell(const orc* o);
+int orc_step_taped(orc* o, double t_end, double* tphi, uint8_t* tchi, double* tdt);
+int orc_replay_step(orc* o, const double* tphi, const uint8_t* tchi, double dt);
+void orc_set_conserved(orc* o, const double* Q);
 void orc_get_state(const orc* o, double* Q, double* alpha, double* phi, int32_t* chi, double* t);
 void orc_set_state(orc* o, const double* Q, const double* phi, const int32_t* chi, double t);
 void orc_totals(const orc* o, double* totals, double* ledger);

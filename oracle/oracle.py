@@ -58,6 +58,12 @@ def lib():
         _lib.orc_step.argtypes = [P, C.c_int32, C.c_double]
         _lib.orc_get_state.argtypes = [P, dp, dp, dp, ip, dp]
         _lib.orc_set_state.argtypes = [P, dp, dp, ip, C.c_double]
+        u8p = C.POINTER(C.c_uint8)
+        _lib.orc_ncell.restype = C.c_long
+        _lib.orc_ncell.argtypes = [P]
+        _lib.orc_step_taped.argtypes = [P, C.c_double, dp, u8p, dp]
+        _lib.orc_replay_step.argtypes = [P, dp, u8p, C.c_double]
+        _lib.orc_set_conserved.argtypes = [P, dp]
         _lib.orc_totals.argtypes = [P, dp, dp]
         _lib.orc_counters.argtypes = [P, C.POINTER(C.c_int64)]
         _lib.orc_last_dt.restype = C.c_double
@@ -144,6 +150,31 @@ class Oracle:
         phi = np.ascontiguousarray(phi, np.float64).ravel()
         chi = np.ascontiguousarray(chi, np.int32).ravel()
         lib().orc_set_state(self.h, _dp(Q), _dp(phi), _ip(chi), float(t))
+
+    def set_conserved(self, Q):
+        """Replace the conserved state of the interior cells ([N][NV][cells])."""
+        Q = np.ascontiguousarray(Q, np.float64)
+        lib().orc_set_conserved(self.h, _dp(Q))
+
+    def step_taped(self, t_end=np.inf):
+        """One step that records its replay tape (the level set at the start of
+        each stage and after the last level-set stage, and the time step);
+        None when t >= t_end."""
+        nc = lib().orc_ncell(self.h)
+        phi = np.zeros((4, nc))
+        chi = np.zeros((4, nc), np.uint8)
+        dt = np.zeros(1)
+        rc = lib().orc_step_taped(self.h, float(t_end), _dp(phi),
+                                  chi.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(dt))
+        if rc < 0:
+            return None
+        return dict(phi=phi, chi=chi, dt=float(dt[0]), err=rc)
+
+    def replay_step(self, tape):
+        """One step from the current conserved state with the interface
+        evolution frozen to a tape of step_taped."""
+        return lib().orc_replay_step(self.h, _dp(tape["phi"]),
+                                     tape["chi"].ctypes.data_as(C.POINTER(C.c_uint8)), float(tape["dt"]))
 
     def totals(self):
         tot = np.zeros((self.N, self.NV))

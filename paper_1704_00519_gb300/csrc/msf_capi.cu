@@ -17,6 +17,7 @@
 #include "../../include/msf.h"
 #include "msf_types.cuh"
 #include "msf_ops.h"
+#include "msf_adjoint.h"
 
 using namespace msf;
 
@@ -55,6 +56,11 @@ struct msf_ctx {
   cudaEvent_t tev[2] = {nullptr, nullptr};
   bool sticky = false;
   std::string err;
+  // adjoint workspace (allocated by the first taped, replayed or adjoint step)
+  const AdjOps* aops = nullptr;
+  AdjBufs adj{};
+  bool adj_ready = false;
+  double* h_pin = nullptr;  // pinned readback of dt / t and the gradient accumulators
 };
 
 static thread_local std::string g_create_err = "";
@@ -365,6 +371,7 @@ extern "C" msf_status msf_destroy(msf_ctx* c) {
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  if (c->h_pin) cudaFreeHost(c->h_pin);
   delete c;
   return MSF_OK;
 }
@@ -384,7 +391,40 @@ static long long count_launches(const msf_ctx* c) {
   return n;
 }
 
-static msf_status enqueue_step(msf_ctx* c) {
+// replay tape of one step (device memory, caller-owned): header (t, dt of the
+// step), Q^n, and phi / chi after the boundary fill at the start of each
+// stage and after the level-set stage of the last stage
+struct TapeLayout {
+  size_t q, phi, chi, total;
+};
+static TapeLayout tape_layout(const Grid& g) {
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t nc = (size_t)g.ncell;
+  TapeLayout L;
+  size_t off = 256;
+  L.q = off;
+  off = up(off + sizeof(double) * g.N * g.NV * nc);
+  L.phi = off;
+  off = up(off + sizeof(double) * 4 * nc);
+  L.chi = off;
+  off = up(off + 4 * nc);
+  L.total = off;
+  return L;
+}
+static void tape_slot_save(const Inst& in, char* tape, int slot, cudaStream_t s) {
+  const TapeLayout L = tape_layout(in.g);
+  const size_t nc = (size_t)in.g.ncell;
+  cudaMemcpyAsync(tape + L.phi + sizeof(double) * nc * slot, in.b.phi, sizeof(double) * nc, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(tape + L.chi + nc * slot, in.b.chi, nc, cudaMemcpyDeviceToDevice, s);
+}
+static void tape_slot_load(const Inst& in, const char* tape, int slot, cudaStream_t s) {
+  const TapeLayout L = tape_layout(in.g);
+  const size_t nc = (size_t)in.g.ncell;
+  cudaMemcpyAsync(in.b.phi, tape + L.phi + sizeof(double) * nc * slot, sizeof(double) * nc, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(in.b.chi, tape + L.chi + nc * slot, nc, cudaMemcpyDeviceToDevice, s);
+}
+
+static msf_status enqueue_step(msf_ctx* c, char* tape = nullptr) {
   const cudaStream_t s = c->stream;
   for (Inst& in : c->inst) {
     const Grid& g = in.g;
@@ -392,6 +432,12 @@ static msf_status enqueue_step(msf_ctx* c) {
     const int nb = in.nblk_band;
     launch_step_begin(b, s);
     launch_bc_phichi(g, b, s);
+    if (tape) {
+      cudaMemcpyAsync(tape, &b.ctl->t, sizeof(double), cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(tape + tape_layout(g).q, b.Q[0], sizeof(double) * g.N * g.NV * g.ncell,
+                      cudaMemcpyDeviceToDevice, s);
+      tape_slot_save(in, tape, 0, s);
+    }
     launch_masks(g, b, s);
     launch_geometry(g, b, b.Q[0], nullptr, nb, s);
     launch_band_save(g, b, nb, s);
@@ -413,6 +459,7 @@ static msf_status enqueue_step(msf_ctx* c) {
       if (st == 0) {
         c->ops->dt(g, b, Qs, s);
         launch_dt_finalize(g, b, s);
+        if (tape) cudaMemcpyAsync(tape + sizeof(double), &b.ctl->dt, sizeof(double), cudaMemcpyDeviceToDevice, s);
       }
       c->ops->interface(g, b, Qs, nb, s);
       double* V[2] = {b.vel0, b.vel1};
@@ -430,6 +477,7 @@ static msf_status enqueue_step(msf_ctx* c) {
       launch_ledger(g, b, in.nbnd, LW[st], s);
       launch_levelset(g, b, V[vc], BETA[st], 1.0 - BETA[st], nb, s);
       launch_bc_phichi(g, b, s);
+      if (tape) tape_slot_save(in, tape, st + 1, s);
       launch_geometry(g, b, Qo, nullptr, nb, s);
       launch_mix(g, b, Qo, nb, s);
     }
@@ -796,12 +844,239 @@ extern "C" msf_status msf_profile_read(msf_ctx* c, double* flux_ms) {
   return MSF_OK;
 }
 
-extern "C" msf_status msf_adjoint_step(msf_ctx* c, const void* lam_out, void* lam_in, double* d_eos) {
-  (void)lam_out;
-  (void)lam_in;
-  (void)d_eos;
+// ------------------------------------------------ tapes, replay, adjoint
+static const double RK_BETA[3] = {0.0, 0.75, 1.0 / 3.0};
+
+static msf_status check_single(msf_ctx* c) {
   if (!c) return MSF_EINVAL;
-  return fail(c, MSF_EUNSUPPORTED, "the adjoint step is not provided by this build");
+  if (c->ninst != 1 || c->batched) return fail(c, MSF_EUNSUPPORTED, "tapes and the adjoint need a single-instance context");
+  if (c->sticky) return fail(c, MSF_ESTATE, "context holds a device-detected error; reset with msf_set_state");
+  return MSF_OK;
+}
+
+static msf_status ensure_adjoint(msf_ctx* c) {
+  if (c->adj_ready) return MSF_OK;
+  Inst& in = c->inst[0];
+  const Grid& g = in.g;
+  const size_t nc = (size_t)g.ncell, N = g.N, NV = g.NV, nbmax = (size_t)g.n_interior;
+  cudaError_t ce = cudaSuccess;
+  AdjBufs& a = c->adj;
+  auto take = [&](size_t bytes) -> void* {
+    void* p = dalloc(c, bytes, &ce);
+    return p;
+  };
+  a.LA = (double*)take(8 * N * NV * nc);
+  a.LN = (double*)take(8 * N * NV * nc);
+  a.LU = (double*)take(8 * N * NV * nc);
+  a.LQ = (double*)take(8 * N * NV * nc);
+  a.LW0 = (double*)take(8 * N * NV * nc);
+  a.LW1 = (double*)take(8 * N * NV * nc);
+  a.lvl = (uint8_t*)take(N * nc);
+  a.mixt = (double*)take(8 * nbmax * N * NV);
+  for (int k = 0; k < 3; k++) {
+    a.mixn[k] = (uint8_t*)take(nbmax * N);
+    a.mixoff[k] = (uint8_t*)take(nbmax * N * MIX_MAXT);
+    a.mixbeta[k] = (double*)take(8 * nbmax * N * MIX_MAXT);
+  }
+  for (int k = 0; k < 4; k++) a.aband[k] = (double*)take(8 * nbmax * N);
+  a.deos = (double*)take(8 * MAXM * 2);
+  a.dinf = (double*)take(8 * 3 * 2 * 5);
+  if (ce != cudaSuccess) return fail(c, MSF_ENOMEM, std::string("adjoint workspace: ") + cudaGetErrorString(ce));
+  if (!c->h_pin && cudaMallocHost((void**)&c->h_pin, sizeof(double) * 64) != cudaSuccess)
+    return fail(c, MSF_ENOMEM, "cudaMallocHost");
+  c->aops = c->ops->tsize == 8 ? adj_ops_f64() : adj_ops_f32();
+  c->adj_ready = true;
+  return MSF_OK;
+}
+
+static bool tape_aligned(const void* p) { return ((uintptr_t)p & 255u) == 0; }
+
+extern "C" msf_status msf_tape_bytes(const msf_ctx* c, int64_t* bytes) {
+  if (!c || !bytes) return MSF_EINVAL;
+  if (c->ninst != 1 || c->batched) return MSF_EUNSUPPORTED;
+  *bytes = (int64_t)tape_layout(c->inst[0].g).total;
+  return MSF_OK;
+}
+
+extern "C" msf_status msf_step_taped(msf_ctx* c, void* tape, double t_end) {
+  msf_status st = check_single(c);
+  if (st != MSF_OK) return st;
+  if (!tape || !tape_aligned(tape)) return fail(c, MSF_EINVAL, "tape must be a 256-byte aligned device buffer");
+  if (std::isnan(t_end)) return fail(c, MSF_EINVAL, "t_end NaN");
+  Inst& in = c->inst[0];
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, in.b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (!(c->h_ctl->t < t_end)) return fail(c, MSF_EINVAL, "no step to take: t >= t_end");
+  k_set_tend<<<1, 1, 0, c->stream>>>(in.b.ctl, t_end);
+  if ((st = enqueue_step(c, (char*)tape)) != MSF_OK) return st;
+  return read_error(c);
+}
+
+// one step of the recorded tape from the current Q[0]: the level set of
+// every stage is loaded from the tape instead of advected, the time step is
+// the tape's, band maintenance and scale separation are skipped. With rec,
+// the band volume fractions after each geometry pass and the mixing records
+// of each stage are kept in the adjoint workspace.
+static void enqueue_replay(msf_ctx* c, const char* tape, bool rec) {
+  const cudaStream_t s = c->stream;
+  Inst& in = c->inst[0];
+  const Grid& g = in.g;
+  const Bufs& b = in.b;
+  const int nb = in.nblk_band;
+  AdjBufs& a = c->adj;
+  launch_adj_begin(b, (const double*)(tape + sizeof(double)), s);
+  tape_slot_load(in, tape, 0, s);
+  launch_masks(g, b, s);
+  launch_geometry(g, b, b.Q[0], nullptr, nb, s);
+  launch_band_save(g, b, nb, s);
+  if (rec) launch_adj_alpha(g, b, a.aband[0], 1, nb, s);
+  for (int st = 0; st < 3; st++) {
+    double* Qs = b.Q[st];
+    double* Qo = b.Q[(st + 1) % 3];
+    c->ops->prim(g, b, Qs, nb, s);
+    void* W[2] = {b.W0, b.W1};
+    uint8_t* F[2] = {b.f0, b.f1};
+    int cur = 0;
+    for (int k = 0; k < g.ext_sweeps; k++) {
+      c->ops->extend(g, b, W[cur], W[cur ^ 1], F[cur], F[cur ^ 1], nb, s);
+      cur ^= 1;
+    }
+    c->ops->cons(g, b, Qs, W[cur], F[cur], nb, s);
+    c->ops->bc_uhat(g, b, Qs, s);
+    c->ops->interface(g, b, Qs, nb, s);
+    c->ops->flux(g, b, Qs, b.Q[0], Qo, RK_BETA[st], 1.0 - RK_BETA[st], in.bb, s);
+    launch_ledger(g, b, in.nbnd, st == 2 ? 2.0 / 3.0 : 1.0 / 6.0, s);
+    tape_slot_load(in, tape, st + 1, s);
+    launch_geometry(g, b, Qo, nullptr, nb, s);
+    if (rec) {
+      launch_adj_alpha(g, b, a.aband[st + 1], 1, nb, s);
+      Bufs br = b;
+      br.mixn = a.mixn[st];
+      br.mixoff = a.mixoff[st];
+      br.mixbeta = a.mixbeta[st];
+      launch_mix(g, br, Qo, nb, s);
+    } else {
+      launch_mix(g, b, Qo, nb, s);
+    }
+  }
+}
+
+__global__ void k_replay_end(Ctl* ctl, const double* tape_t) {
+  ctl->t = *tape_t + ctl->dt;
+  ctl->cnt[C_STEPS] += 1;
+}
+
+extern "C" msf_status msf_replay_step(msf_ctx* c, const void* tape) {
+  msf_status st = check_single(c);
+  if (st != MSF_OK) return st;
+  if (!tape || !tape_aligned(tape)) return fail(c, MSF_EINVAL, "tape must be a 256-byte aligned device buffer");
+  if ((st = ensure_adjoint(c)) != MSF_OK) return st;
+  enqueue_replay(c, (const char*)tape, false);
+  k_replay_end<<<1, 1, 0, c->stream>>>(c->inst[0].b.ctl, (const double*)tape);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, MSF_ECUDA, std::string("replay launch: ") + cudaGetErrorString(e));
+  return read_error(c);
+}
+
+extern "C" msf_status msf_set_conserved(msf_ctx* c, int32_t i, const double* Q, int32_t mem) {
+  msf_status st = check_instance(c, i);
+  if (st != MSF_OK) return st;
+  if (!Q) return fail(c, MSF_EINVAL, "Q is NULL");
+  if (mem != MSF_HOST && mem != MSF_DEVICE) return fail(c, MSF_EINVAL, "mem");
+  Inst& in = c->inst[i];
+  const Grid& g = in.g;
+  void* dQ = nullptr;
+  if ((st = stage_in(c, Q, sizeof(double) * g.n_interior * g.N * g.NV, mem, &dQ)) != MSF_OK) return st;
+  launch_adj_io(g, AdjBufs{}, (const double*)dQ, in.b.Q[0], 2, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  cudaFree(dQ);
+  if (e != cudaSuccess) return fail(c, MSF_ECUDA, std::string("set_conserved: ") + cudaGetErrorString(e));
+  return MSF_OK;
+}
+
+extern "C" msf_status msf_adjoint_step(msf_ctx* c, const void* tape_, const double* lam_out, double* lam_in,
+                                       double* d_eos, double* d_inflow) {
+  msf_status st = check_single(c);
+  if (st != MSF_OK) return st;
+  if (!tape_ || !tape_aligned(tape_)) return fail(c, MSF_EINVAL, "tape must be a 256-byte aligned device buffer");
+  if (!lam_out || !lam_in) return fail(c, MSF_EINVAL, "NULL adjoint array");
+  if ((st = ensure_adjoint(c)) != MSF_OK) return st;
+  const char* tape = (const char*)tape_;
+  const cudaStream_t s = c->stream;
+  Inst& in = c->inst[0];
+  const Grid& g = in.g;
+  const Bufs& b = in.b;
+  const int nb = in.nblk_band;
+  AdjBufs& a = c->adj;
+  const TapeLayout L = tape_layout(g);
+  const size_t qbytes = sizeof(double) * g.N * g.NV * g.ncell;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_pin, tape, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(c, cudaStreamSynchronize(s));
+  const double dt = c->h_pin[1];
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, MSF_EINVAL, "tape holds no step");
+  cudaMemsetAsync(a.deos, 0, sizeof(double) * MAXM * 2, s);
+  cudaMemsetAsync(a.dinf, 0, sizeof(double) * 30, s);
+  launch_adj_io(g, a, lam_out, nullptr, 0, s);
+  // recompute the stages from the tape: Q^(1), Q^(2), band volume fractions, mixing records
+  CUDA_TRY(c, cudaMemcpyAsync(b.Q[0], tape + L.q, qbytes, cudaMemcpyDeviceToDevice, s));
+  enqueue_replay(c, tape, true);
+  void* W[2] = {b.W0, b.W1};
+  uint8_t* F[2] = {b.f0, b.f1};
+  for (int sg = 2; sg >= 0; sg--) {
+    if (sg == 0) CUDA_TRY(c, cudaMemcpyAsync(b.Q[0], tape + L.q, qbytes, cudaMemcpyDeviceToDevice, s));
+    const double* Qs = b.Q[sg];
+    const double beta = RK_BETA[sg], omb = 1.0 - RK_BETA[sg];
+    // stage-s geometry and states of the forward step
+    tape_slot_load(in, tape, sg, s);
+    launch_geometry(g, b, Qs, nullptr, nb, s);
+    launch_adj_alpha(g, b, a.aband[sg], 0, nb, s);
+    c->ops->prim(g, b, Qs, nb, s);
+    launch_adj_level(g, b, a, b.f0, 0, nb, s);
+    int cur = 0;
+    for (int k = 1; k <= g.ext_sweeps; k++) {
+      c->ops->extend(g, b, W[cur], W[cur ^ 1], F[cur], F[cur ^ 1], nb, s);
+      cur ^= 1;
+      launch_adj_level(g, b, a, F[cur], k, nb, s);
+    }
+    c->ops->cons(g, b, Qs, W[cur], F[cur], nb, s);
+    c->ops->bc_uhat(g, b, Qs, s);
+    c->ops->interface(g, b, Qs, nb, s);
+    // reverse: mixing, fluxes and exchange, boundary states, stencil states,
+    // extension sweeps, primitive recovery, RK combination
+    cudaMemsetAsync(a.LU, 0, qbytes, s);
+    cudaMemsetAsync(a.LQ, 0, qbytes, s);
+    cudaMemsetAsync(a.LW0, 0, qbytes, s);
+    cudaMemsetAsync(a.LW1, 0, qbytes, s);
+    launch_adj_mix(g, b, a, sg, (const uint8_t*)(tape + L.chi + (size_t)g.ncell * (sg + 1)), nb, s);
+    c->aops->flux(g, b, a, Qs, omb * dt, s);
+    c->aops->interface(g, b, a, Qs, omb * dt, nb, s);
+    launch_adj_bc(g, b, a, s);
+    c->aops->cons(g, b, a, W[cur], F[cur], a.LW0, nb, s);
+    double* LW[2] = {a.LW0, a.LW1};
+    int lc = 0;
+    for (int k = g.ext_sweeps; k >= 1; k--) {
+      launch_adj_ext(g, b, a, LW[lc], LW[lc ^ 1], k, nb, s);
+      lc ^= 1;
+    }
+    launch_adj_prim(g, b, a, Qs, LW[lc], nb, s);
+    launch_adj_combine(g, b, a, beta, omb, sg == 2 ? 1 : 0, s);
+  }
+  launch_adj_io(g, a, nullptr, lam_in, 1, s);
+  // back to the state at the start of the tape's step
+  tape_slot_load(in, tape, 0, s);
+  launch_masks(g, b, s);
+  launch_geometry(g, b, b.Q[0], nullptr, nb, s);
+  launch_adj_end(b, (const double*)tape, s);
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_pin, a.deos, sizeof(double) * 2 * MAXM, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_pin + 2 * MAXM, a.dinf, sizeof(double) * 30, cudaMemcpyDeviceToHost, s));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, MSF_ECUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
+  if ((st = read_error(c)) != MSF_OK) return st;
+  if (d_eos)
+    for (int k = 0; k < 2 * g.N; k++) d_eos[k] += c->h_pin[k];
+  if (d_inflow)
+    for (int k = 0; k < 30; k++) d_inflow[k] += c->h_pin[2 * MAXM + k];
+  return MSF_OK;
 }
 
 // message slot of calls without a context (used by msf_cfl_dt_noalloc)

@@ -4,10 +4,15 @@
 #include "msf_kernels.cuh"
 #include "msf_ops.h"
 #include "msf_prec.inc"
+#include "msf_adjoint.cuh"
 
 namespace msf {
 const Ops* ops_f32() {
   static const Ops ops = make_ops<float>();
+  return &ops;
+}
+const AdjOps* adj_ops_f32() {
+  static const AdjOps ops = make_adj_ops<float>();
   return &ops;
 }
 }  // namespace msf

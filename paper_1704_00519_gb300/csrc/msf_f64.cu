@@ -6,11 +6,16 @@
 #include "msf_kernels.cuh"
 #include "msf_ops.h"
 #include "msf_prec.inc"
+#include "msf_adjoint_common.cuh"
 
 namespace msf {
 
 const Ops* ops_f64() {
   static const Ops ops = make_ops<double>();
+  return &ops;
+}
+const AdjOps* adj_ops_f64() {
+  static const AdjOps ops = make_adj_ops<double>();
   return &ops;
 }
 

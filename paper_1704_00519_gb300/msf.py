@@ -67,7 +67,11 @@ def _load():
         "msf_set_levelset": ([P, C.c_int32, P, P, P, C.c_int32], C.c_int),
         "msf_step": ([P, C.c_int32, C.c_double, C.c_int32], C.c_int),
         "msf_totals": ([P, C.c_int32, dp, dp], C.c_int),
-        "msf_adjoint_step": ([P, P, P, dp], C.c_int),
+        "msf_adjoint_step": ([P, P, P, P, dp, dp], C.c_int),
+        "msf_tape_bytes": ([P, C.POINTER(C.c_int64)], C.c_int),
+        "msf_step_taped": ([P, P, C.c_double], C.c_int),
+        "msf_replay_step": ([P, P], C.c_int),
+        "msf_set_conserved": ([P, C.c_int32, P, C.c_int32], C.c_int),
         "msf_get_state": ([P, C.c_int32, P, P, P, P, dp, C.c_int32], C.c_int),
         "msf_set_state": ([P, C.c_int32, P, P, P, C.c_double, C.c_int32], C.c_int),
         "msf_stats": ([P, C.POINTER(C.c_int64)], C.c_int),
@@ -97,6 +101,10 @@ msf_set_levelset = _lib.msf_set_levelset
 msf_step = _lib.msf_step
 msf_totals = _lib.msf_totals
 msf_adjoint_step = _lib.msf_adjoint_step
+msf_tape_bytes = _lib.msf_tape_bytes
+msf_step_taped = _lib.msf_step_taped
+msf_replay_step = _lib.msf_replay_step
+msf_set_conserved = _lib.msf_set_conserved
 msf_get_state = _lib.msf_get_state
 msf_set_state = _lib.msf_set_state
 msf_stats = _lib.msf_stats
@@ -247,6 +255,43 @@ class Solver:
         out = np.zeros(sizes[which] * self.cells)
         _check(msf_debug_field(self.h, 0, int(which), out.ctypes.data_as(C.POINTER(C.c_double))), self.h)
         return out
+
+    # ---- replay tapes and the adjoint step (frozen interface evolution)
+    def tape_bytes(self):
+        n = C.c_int64()
+        _check(msf_tape_bytes(self.h, C.byref(n)), self.h)
+        return n.value
+
+    def new_tape(self):
+        """A device buffer for one tape (torch uint8 tensor, 256-byte aligned)."""
+        import torch
+        nb = self.tape_bytes()
+        buf = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+        off = (-buf.data_ptr()) % 256
+        return buf[off:off + nb]
+
+    def step_taped(self, tape, t_end=float("inf")):
+        _check(msf_step_taped(self.h, C.c_void_p(tape.data_ptr()), float(t_end)), self.h)
+
+    def replay_step(self, tape):
+        _check(msf_replay_step(self.h, C.c_void_p(tape.data_ptr())), self.h)
+
+    def set_conserved(self, Q):
+        a, ma, ka = _ptr(Q, "f8")
+        _check(msf_set_conserved(self.h, 0, a, ma), self.h)
+
+    def adjoint_step(self, tape, lam_out):
+        """(lam_in, d_eos [N, 2], d_inflow [3, 2, 5]) of one tape for the
+        adjoint lam_out = dJ/dQ^{n+1} (torch float64 device [N, NV, cells])."""
+        import torch
+        lam_out = lam_out.contiguous()
+        lam_in = torch.empty_like(lam_out)
+        d_eos = np.zeros((self.N, 2))
+        d_inf = np.zeros((3, 2, 5))
+        _check(msf_adjoint_step(self.h, C.c_void_p(tape.data_ptr()), C.c_void_p(lam_out.data_ptr()),
+                                C.c_void_p(lam_in.data_ptr()), d_eos.ctypes.data_as(C.POINTER(C.c_double)),
+                                d_inf.ctypes.data_as(C.POINTER(C.c_double))), self.h)
+        return lam_in, d_eos, d_inf
 
 
 def pad_materials(case, nmat):

@@ -93,4 +93,6 @@ def test_create_rejects_bad_eos_and_counts(msf):
 def test_null_context_calls(msf):
     assert msf.msf_step(None, 1, 1.0, 1) == msf.MSF_EINVAL
     assert msf.msf_destroy(None) == msf.MSF_OK
-    assert msf.msf_adjoint_step(None, None, None, None) == msf.MSF_EINVAL
+    assert msf.msf_adjoint_step(None, None, None, None, None, None) == msf.MSF_EINVAL
+    assert msf.msf_step_taped(None, None, 0.0) == msf.MSF_EINVAL
+    assert msf.msf_replay_step(None, None) == msf.MSF_EINVAL
