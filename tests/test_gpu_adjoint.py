@@ -14,6 +14,13 @@ the C ABI on the GPU.
 * Pins independent of both implementations: with reflective walls total mass
   and total energy are invariants of the replay map, so their adjoint is
   exactly the seed (ones on the density / energy of every material).
+
+The Lax-Friedrichs coefficient of a face is a maximum over its stencil; on
+piecewise-constant data many stencils hold exact ties, where the step is not
+differentiable (a central difference then averages one-sided slopes while
+the adjoint returns one of them). The Q-direction checks therefore start from
+the case's state with 1% relative noise (no exact ties), and take central
+differences with steps far below the noise.
 """
 import dataclasses
 
@@ -26,6 +33,9 @@ from oracle import oracle as orc
 pytestmark = pytest.mark.gpu
 
 GRAD_RTOL = 1e-5
+EOS_RTOL = 1e-4
+NOISE = 1e-2
+EPS = 1e-7
 
 
 @pytest.fixture(scope="module")
@@ -39,8 +49,15 @@ def env():
     return m, torch
 
 
-def record(msf, case, steps, precision=0):
+def noisy_state(torch, case, Q0, seed=1):
+    g = np.random.default_rng(seed)
+    return Q0 * torch.tensor(1.0 + NOISE * g.uniform(-1, 1, Q0.shape), device=Q0.device)
+
+
+def record(msf, case, steps, precision=0, Q0=None):
     s = msf.Solver(case, precision=precision)
+    if Q0 is not None:
+        s.set_conserved(Q0)
     tapes = []
     for _ in range(steps):
         tp = s.new_tape()
@@ -122,16 +139,17 @@ def test_replay_matches_oracle_replay(env, name):
 def test_adjoint_dot_product_against_central_differences(env, name):
     msf, torch = env
     case, steps = CASES[name][0](), CASES[name][1]
-    s, tapes = record(msf, case, steps)
     ref = msf.Solver(case)
     Q0 = torch.empty((case.nmat, case.nv, case.cells), dtype=torch.float64, device="cuda")
     ref.get_state_device(Q0)
+    Q0 = noisy_state(torch, case, Q0)
+    s, tapes = record(msf, case, steps, Q0=Q0)
     rng = np.random.default_rng(11)
     lamK = torch.tensor(rng.uniform(-1, 1, Q0.shape), device="cuda")
     dQ = Q0 * torch.tensor(rng.uniform(-1, 1, Q0.shape), device="cuda")
     lam0, _, _ = adjoint_chain(s, tapes, lamK)
     adj = float((lam0 * dQ).sum())
-    eps = 1e-6
+    eps = EPS
     Jp = float((lamK * replay_state(msf, torch, case, tapes, Q0 + eps * dQ)).sum())
     Jm = float((lamK * replay_state(msf, torch, case, tapes, Q0 - eps * dQ)).sum())
     fd = (Jp - Jm) / (2 * eps)
@@ -147,10 +165,11 @@ def _with(case, **kw):
 def test_adjoint_eos_and_inflow_partials(env, name):
     msf, torch = env
     case, steps = CASES[name][0](), CASES[name][1]
-    s, tapes = record(msf, case, steps)
     ref = msf.Solver(case)
     Q0 = torch.empty((case.nmat, case.nv, case.cells), dtype=torch.float64, device="cuda")
     ref.get_state_device(Q0)
+    Q0 = noisy_state(torch, case, Q0, seed=2)
+    s, tapes = record(msf, case, steps, Q0=Q0)
     rng = np.random.default_rng(7)
     lamK = torch.tensor(rng.uniform(-1, 1, Q0.shape), device="cuda")
     _, d_eos, d_inf = adjoint_chain(s, tapes, lamK)
@@ -161,13 +180,13 @@ def test_adjoint_eos_and_inflow_partials(env, name):
     checks = []
     for m in range(case.nmat):
         g = list(case.gamma)
-        h = 1e-6 * g[m]
+        h = 1e-7 * g[m]
         gp, gm = list(g), list(g)
         gp[m] += h
         gm[m] -= h
         checks.append(("gamma", m, d_eos[m, 0], (J(_with(case, gamma=gp)) - J(_with(case, gamma=gm))) / (2 * h)))
         pinf = list(case.pinf)
-        h = 1e-6 * max(pinf[m], 1.0)
+        h = 1e-7 * max(pinf[m], 1.0)
         pp, pm = list(pinf), list(pinf)
         pp[m] += h
         pm[m] = max(pm[m] - h, 0.0)
@@ -176,14 +195,14 @@ def test_adjoint_eos_and_inflow_partials(env, name):
     if case.inflow_prim is not None and any(b == cs.INFLOW for bb in case.bc for b in bb):
         for v in range(case.nv):
             ip = np.array(case.inflow_prim)
-            h = 1e-6 * max(abs(ip[0, 0, v]), 1.0)
+            h = 1e-7 * max(abs(ip[0, 0, v]), 1.0)
             a, b = ip.copy(), ip.copy()
             a[0, 0, v] += h
             b[0, 0, v] -= h
             checks.append(("inflow", v, d_inf[0, 0, v],
                            (J(_with(case, inflow_prim=a)) - J(_with(case, inflow_prim=b))) / (2 * h)))
     for kind, k, adj, fd in checks:
-        tol = GRAD_RTOL * max(abs(fd), abs(adj)) + 1e-9 * float(lamK.abs().sum())
+        tol = EOS_RTOL * max(abs(fd), abs(adj)) + 1e-9 * float(lamK.abs().sum())
         assert abs(adj - fd) <= tol, (kind, k, adj, fd)
 
 
@@ -207,10 +226,12 @@ def test_adjoint_against_oracle_differences(env):
     """The GPU adjoint against central differences of the oracle's replay."""
     msf, torch = env
     case, steps = cs.triple_point(56, 24), 4
-    s, tapes = record(msf, case, steps)
-    o = orc.Oracle(case)
-    otapes = [o.step_taped(case.t_end) for _ in range(steps)]
     Q0 = orc.Oracle(case).state()["Q"]
+    Q0 = noisy_state(torch, case, torch.tensor(Q0), seed=4).numpy()
+    s, tapes = record(msf, case, steps, Q0=torch.tensor(Q0, device="cuda"))
+    o = orc.Oracle(case)
+    o.set_conserved(Q0)
+    otapes = [o.step_taped(case.t_end) for _ in range(steps)]
     rng = np.random.default_rng(19)
     lamK = rng.uniform(-1, 1, Q0.shape)
     dQ = Q0 * rng.uniform(-1, 1, Q0.shape)
@@ -224,6 +245,113 @@ def test_adjoint_against_oracle_differences(env):
             L.replay_step(tp)
         return float((lamK * L.state()["Q"]).sum())
 
-    eps = 1e-6
+    eps = EPS
     fd = (J(Q0 + eps * dQ) - J(Q0 - eps * dQ)) / (2 * eps)
     assert abs(adj - fd) <= GRAD_RTOL * max(abs(fd), abs(adj)), (adj, fd)
+
+
+def _objectives(prob, adj, torch, Qs, dts, alphas, eos, x, wall, farea):
+    """J1: bubble mass-centroid x displacement; J2: y = 0 wall pressure impulse."""
+    J1 = adj.mass_centroid_x(Qs[-1], 1, x) - adj.mass_centroid_x(Qs[0], 1, x)
+    J2 = sum(dt * adj.wall_pressure(Q, eos, a, wall, farea) for Q, dt, a in zip(Qs[1:], dts, alphas))
+    return J1, J2
+
+
+def test_shock_bubble_gradients_autograd_fd_and_oracle(env):
+    """3D shock on a heavy sphere (32 x 16 x 16, the workload's small
+    counterpart): d(J1, J2)/d(rho_bubble, gamma_bubble, Mach) through the
+    torch.autograd.Function (adjoint steps) against central differences of
+    the GPU replay and of the oracle's replay, within 1e-4 relative at
+    h = 1e-6 (relative). The step is piecewise smooth (maxima and minima in
+    the Lax-Friedrichs and HLLC wave speeds), so a difference with
+    h = 1e-3 is a secant across kinks; it is computed too and must agree
+    within 1e-2."""
+    msf, torch = env
+    from paper_1704_00519_gb300 import adjoint as adj
+    K = 10
+    prob = adj.ShockBubble((32, 16, 16))
+    th0 = prob.theta0()
+    case0 = prob.case(th0)
+    solver = msf.Solver(case0)
+    st0 = solver.state()
+    alpha0 = torch.tensor(st0["alpha"], device="cuda")
+    xs = torch.tensor(cs.centres(prob.n, case0.lo, case0.hi)[0].ravel(), device="cuda")
+    wall = torch.tensor(np.nonzero(cs.centres(prob.n, case0.lo, case0.hi)[1].ravel() < 1.0 / prob.n[1])[0],
+                        device="cuda")
+    h = [(case0.hi[d] - case0.lo[d]) / prob.n[d] for d in range(3)]
+    farea = h[0] * h[2]
+
+    theta = th0.clone().cuda().requires_grad_(True)
+    eos = prob.eos(theta)
+    inflow = prob.inflow(theta)
+    Q = prob.conserved(prob.prim(theta, "cuda"), eos, alpha0)
+    tapes, Qs, dts, alphas = [], [Q], [], []
+    for _ in range(K):
+        Q = adj.MsfStep.apply(Q, eos, inflow, solver, case0.t_end, tapes)
+        Qs.append(Q)
+        dts.append(adj.tape_dt(tapes[-1]))
+        alphas.append(torch.tensor(solver.state()["alpha"], device="cuda"))
+    J1, J2 = _objectives(prob, adj, torch, Qs, dts, alphas, eos, xs, wall, farea)
+    g1 = torch.autograd.grad(J1, theta, retain_graph=True)[0].cpu().numpy()
+    g2 = torch.autograd.grad(J2, theta)[0].cpu().numpy()
+
+    def replay_objectives(th, oracle=False):
+        th = torch.tensor(th, dtype=torch.float64)
+        c = prob.case(th)
+        thd = th.cuda()
+        e = prob.eos(thd)
+        Q0 = prob.conserved(prob.prim(thd, "cuda"), e, alpha0)
+        out = [Q0]
+        if oracle:
+            L = orc.Oracle(c)
+            L.set_conserved(Q0.cpu().numpy())
+            for tp in otapes:
+                L.replay_step(tp)
+                out.append(torch.tensor(L.state()["Q"], device="cuda"))
+        else:
+            s = msf.Solver(c)
+            s.set_conserved(Q0)
+            for tp in tapes:
+                s.replay_step(tp)
+                Qn = torch.empty_like(Q0)
+                s.get_state_device(Qn)
+                out.append(Qn)
+        j1, j2 = _objectives(prob, adj, torch, out, dts, alphas, e, xs, wall, farea)
+        return float(j1), float(j2)
+
+    o = orc.Oracle(case0)
+    otapes = [o.step_taped(case0.t_end) for _ in range(K)]
+    for oracle, hrel, tol in ((False, 1e-6, 1e-4), (True, 1e-6, 1e-4), (False, 1e-3, 1e-2)):
+        fd1, fd2 = np.zeros(3), np.zeros(3)
+        for i in range(3):
+            hh = hrel * float(th0[i])
+            tp_, tm_ = th0.numpy().copy(), th0.numpy().copy()
+            tp_[i] += hh
+            tm_[i] -= hh
+            a1, a2 = replay_objectives(tp_, oracle)
+            b1, b2 = replay_objectives(tm_, oracle)
+            fd1[i], fd2[i] = (a1 - b1) / (2 * hh), (a2 - b2) / (2 * hh)
+        for g, fd in ((g1, fd1), (g2, fd2)):
+            scale = np.abs(fd).max()
+            print("shock-bubble gradient", "oracle" if oracle else "gpu", hrel, g, fd)
+            assert np.abs(g - fd).max() <= tol * scale, (oracle, hrel, g, fd)
+
+
+def test_fp32_form_adjoint_close_to_fp64(env):
+    """The FP32-bulk context's adjoint (stencil states in float, adjoint
+    accumulated in double) of the same tapes against the FP64 adjoint."""
+    msf, torch = env
+    case, steps = CASES["shock_bubbles_inflow"][0](), 4
+    ref = msf.Solver(case)
+    Q0 = torch.empty((case.nmat, case.nv, case.cells), dtype=torch.float64, device="cuda")
+    ref.get_state_device(Q0)
+    Q0 = noisy_state(torch, case, Q0, seed=5)
+    s64, tapes = record(msf, case, steps, Q0=Q0)
+    s32 = msf.Solver(case, precision=msf.MSF_FP32_BULK)
+    rng = np.random.default_rng(23)
+    lamK = torch.tensor(rng.uniform(-1, 1, Q0.shape), device="cuda")
+    l64, e64, _ = adjoint_chain(s64, tapes, lamK)
+    l32, e32, _ = adjoint_chain(s32, tapes, lamK)
+    rel = float((l32 - l64).abs().sum() / l64.abs().sum())
+    assert rel <= 1e-4, rel
+    assert np.abs(e32 - e64).max() <= 1e-4 * np.abs(e64).max()
