@@ -214,6 +214,75 @@ def batched_rates(msf, torch, stream, K_persistent, K_sequence):
             "speedup_vs_per_instance": v1 / v2, "instances_with_device_error": max(bad1, bad2)}
 
 
+def workload_rates(msf, torch, stream, K):
+    """Forward throughput of the two-bubble (2D, 2048 x 512) and sphere (3D,
+    256 x 128 x 128) shock workloads, FP32-bulk and FP64, device-timed, with
+    the L1 density difference of the two after the same steps."""
+    import paper_1704_00519_gb300.cases as cs
+    out = {}
+    for name, maker in (("shock_bubbles_2048x512", lambda: cs.shock_bubbles(2048, 512)),
+                        ("shock_sphere_256x128x128", lambda: cs.shock_sphere((256, 128, 128)))):
+        case = maker()
+        r = {"cells": case.cells, "steps": K}
+        rho = {}
+        for key, prec in (("fp32", msf.MSF_FP32_BULK), ("fp64", msf.MSF_FP64)):
+            s = msf.Solver(case, precision=prec, stream=stream)
+            s.step(2, case.t_end)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            s.step(K, case.t_end, sync=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / K
+            r[key] = {"value": case.cells * 3 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms}
+            rho[key] = s.state()["Q"][:, 0].sum(0)
+            s.close()
+        r["fp32_over_fp64"] = r["fp32"]["value"] / r["fp64"]["value"]
+        r["l1_rho_fp32_vs_fp64"] = float(np.abs(rho["fp32"] - rho["fp64"]).sum() / np.abs(rho["fp64"]).sum())
+        out[name] = r
+    return out
+
+
+def adjoint_rates(msf, torch, stream, K):
+    """Adjoint form on the 3D shock-sphere workload (256 x 128 x 128), FP32-bulk
+    context: K taped steps (forward with stage checkpoints), then K adjoint
+    steps of a unit seed, each timed on the context stream; cell-stage/s of
+    the reverse sweep."""
+    import paper_1704_00519_gb300.cases as cs
+    case = cs.shock_sphere((256, 128, 128))
+    s = msf.Solver(case, precision=msf.MSF_FP32_BULK, stream=stream)
+    s.step(2, case.t_end)
+    tapes = [s.new_tape() for _ in range(K)]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record()
+    for tp in tapes:
+        s.step_taped(tp, case.t_end)
+    e[1].record()
+    lam = torch.ones((case.nmat, case.nv, case.cells), dtype=torch.float64, device="cuda")
+    lam1, _, _ = s.adjoint_step(tapes[-1], lam)   # allocates the adjoint workspace
+    torch.cuda.synchronize()
+    e[1].synchronize()
+    fwd_ms = e[0].elapsed_time(e[1]) / K
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record()
+    d_eos = np.zeros((case.nmat, 2))
+    for tp in reversed(tapes):
+        lam, de, _ = s.adjoint_step(tp, lam)
+        d_eos += de
+    b1.record()
+    torch.cuda.synchronize()
+    bwd_ms = b0.elapsed_time(b1) / K
+    finite = bool(torch.isfinite(lam).all()) and bool(np.all(np.isfinite(d_eos)))
+    tb = s.tape_bytes()
+    s.close()
+    return {"workload": "shock_sphere_256x128x128", "cells": case.cells, "steps": K, "precision": "fp32_bulk",
+            "value": case.cells * 3 / (bwd_ms / 1e3), "unit": UNIT, "adjoint_ms_per_step": bwd_ms,
+            "taped_forward_ms_per_step": fwd_ms, "tape_bytes_per_step": tb, "finite": finite,
+            "how": "msf_adjoint_step per step (recomputes the stages from the tape); events on the context stream"}
+
+
 def pairs_per_cell(s):
     """(cell, material) pairs the flux update processes: popcount of the step mask."""
     vals, counts = np.unique(s.debug(5).astype(np.int64), return_counts=True)
@@ -322,6 +391,12 @@ def run_gpu(args):
 
     launches = s32.launches_per_step() * K
     batched = batched_rates(msf, torch, sptr, max(K, 10), 3)
+    s32.close()
+    s64.close()
+    se.close()
+    workloads = workload_rates(msf, torch, sptr, 10)
+    adjoint = adjoint_rates(msf, torch, sptr, 4)
+    adjoint["vs_fp64_forward"] = adjoint["value"] / workloads["shock_sphere_256x128x128"]["fp64"]["value"]
     if rank != 0:
         return 0
 
@@ -354,6 +429,8 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "batched_1d": batched,
+        "workloads": workloads,
+        "adjoint": adjoint,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -373,3 +373,41 @@ def test_scale_separation_keeps_resolved_shapes():
         o = orc.Oracle(case)
         assert o.step(3, 10.0) == 0
         assert o.counters()["oddball"] == 0
+
+
+def test_replay_of_own_tapes_is_the_forward_step():
+    """A replay of recorded tapes from the recorded initial state reproduces
+    the forward trajectory bit for bit (the interface evolution it freezes is
+    exactly the one recorded)."""
+    case = cs.triple_point(28, 12)
+    a = orc.Oracle(case)
+    Q0 = a.state()["Q"]
+    tapes = [a.step_taped(case.t_end) for _ in range(4)]
+    b = orc.Oracle(case)
+    b.set_conserved(Q0)
+    for tp in tapes:
+        assert b.replay_step(tp) == 0
+    assert np.array_equal(a.state()["Q"], b.state()["Q"])
+    assert b.state()["t"] == pytest.approx(a.state()["t"], rel=1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_replay_map_conserves_total_mass_and_energy(seed):
+    """In a reflective box the replayed step from any nearby state conserves
+    total mass and total energy exactly (fluxes telescope, walls carry no
+    mass or energy flux, the exchange X^R = -sum X^m, mixing is conservative):
+    the invariants whose adjoint is the seed."""
+    case = cs.triple_point(28, 12)
+    a = orc.Oracle(case)
+    Q0 = a.state()["Q"]
+    tapes = [a.step_taped(case.t_end) for _ in range(3)]
+    rng = np.random.default_rng(seed)
+    Qp = Q0 * (1.0 + 1e-2 * rng.uniform(-1, 1, Q0.shape))
+    b = orc.Oracle(case)
+    b.set_conserved(Qp)
+    for tp in tapes:
+        assert b.replay_step(tp) == 0
+    Q = b.state()["Q"]
+    for v in (0, case.nv - 1):
+        s0, s1 = Qp[:, v].sum(), Q[:, v].sum()
+        assert abs(s1 - s0) <= 1e-13 * abs(s0), (v, s0, s1)
