@@ -18,6 +18,7 @@
 #include "msf_types.cuh"
 #include "msf_ops.h"
 #include "msf_adjoint.h"
+#include "msf_tiled.h"
 
 using namespace msf;
 
@@ -42,6 +43,7 @@ struct msf_ctx {
   std::vector<Inst> inst;
   std::vector<void*> allocs;
   const Ops* ops = nullptr;
+  const TiledOps* tops = nullptr;
   Ctl* h_ctl = nullptr;  // pinned readback of one control block
   unsigned* d_flag = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -164,6 +166,7 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
   c->opt = *opt;
   c->stream = (cudaStream_t)opt->stream;
   c->ops = opt->precision == MSF_FP32_BULK ? ops_f32() : ops_f64();
+  c->tops = opt->precision == MSF_FP32_BULK ? tiled_ops_f32() : nullptr;
   const size_t ts = c->ops->tsize;
   cudaError_t ce = cudaSuccess;
 #define ALLOC(ptr, type, count)                                        \
@@ -377,12 +380,19 @@ extern "C" msf_status msf_destroy(msf_ctx* c) {
 }
 
 // ---------------------------------------------------------------- stepping
+// the FP32-bulk form runs the ghost-state sweeps of two-dimensional grids
+// tiled (one launch for K sweeps)
+static bool tiled_ext(const msf_ctx* c, const Grid& g) {
+  return c->tops && g.D == 2 && g.ext_sweeps >= 1 && g.ext_sweeps <= TILED_MAX_SWEEPS;
+}
+
 // kernels one step enqueues (keep in step with enqueue_step)
 static long long count_launches(const msf_ctx* c) {
   long long n = 0;
   for (const Inst& in : c->inst) {
     const Grid& g = in.g;
-    const long long ext = g.ext_sweeps, vel = g.vel_sweeps, re = 2LL * g.reinit_iters;
+    const long long ext = tiled_ext(c, g) ? 1 : g.ext_sweeps;
+    const long long vel = g.vel_sweeps, re = 2LL * g.reinit_iters;
     const long long per_stage = 1 + ext + 1 + 1 + 1 + vel + 1 + 1 + 1 + 1 + 1 + 2 + 3;
     n += 1 + 1 + (2 + g.D) + 2 + 1 + 3 * per_stage + 2 + 1;
     if (g.scale_sep) n += 2 + 1;
@@ -450,9 +460,15 @@ static msf_status enqueue_step(msf_ctx* c, char* tape = nullptr) {
       void* W[2] = {b.W0, b.W1};
       uint8_t* F[2] = {b.f0, b.f1};
       int cur = 0;
-      for (int k = 0; k < g.ext_sweeps; k++) {
-        c->ops->extend(g, b, W[cur], W[cur ^ 1], F[cur], F[cur ^ 1], nb, s);
-        cur ^= 1;
+      if (tiled_ext(c, g)) {
+        cudaError_t te = c->tops->extend(g, b, W[0], W[1], F[0], F[1], g.ext_sweeps, s);
+        if (te != cudaSuccess) return fail(c, MSF_ECUDA, std::string("tiled extension: ") + cudaGetErrorString(te));
+        cur = 1;
+      } else {
+        for (int k = 0; k < g.ext_sweeps; k++) {
+          c->ops->extend(g, b, W[cur], W[cur ^ 1], F[cur], F[cur ^ 1], nb, s);
+          cur ^= 1;
+        }
       }
       c->ops->cons(g, b, Qs, W[cur], F[cur], nb, s);
       c->ops->bc_uhat(g, b, Qs, s);

@@ -5,6 +5,7 @@
 #include "msf_ops.h"
 #include "msf_prec.inc"
 #include "msf_adjoint.cuh"
+#include "msf_tiled.cuh"
 
 namespace msf {
 const Ops* ops_f32() {
@@ -13,6 +14,10 @@ const Ops* ops_f32() {
 }
 const AdjOps* adj_ops_f32() {
   static const AdjOps ops = make_adj_ops<float>();
+  return &ops;
+}
+const TiledOps* tiled_ops_f32() {
+  static const TiledOps ops = make_tiled_ops<float>();
   return &ops;
 }
 }  // namespace msf

@@ -97,19 +97,22 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("name", ["triple_point", "shock_sphere_3d"])
-def test_taped_step_and_replay_are_the_forward_step(env, name):
+@pytest.mark.parametrize("name,precision", [("triple_point", 0), ("shock_sphere_3d", 0), ("triple_point", 1)])
+def test_taped_step_and_replay_are_the_forward_step(env, name, precision):
+    """FP32-bulk form included: its two-dimensional forward step runs the
+    ghost-state sweeps tiled (all sweeps in one launch), the replay one sweep
+    per launch; the two give the same bits."""
     msf, torch = env
     case, steps = CASES[name][0](), CASES[name][1]
-    s_plain = msf.Solver(case)
+    s_plain = msf.Solver(case, precision=precision)
     Q0 = torch.empty((case.nmat, case.nv, case.cells), dtype=torch.float64, device="cuda")
     s_plain.get_state_device(Q0)
     s_plain.step(steps, case.t_end)
-    s_tape, tapes = record(msf, case, steps)
+    s_tape, tapes = record(msf, case, steps, precision=precision)
     a, b = s_plain.state(), s_tape.state()
     assert np.array_equal(a["Q"], b["Q"])
     assert np.array_equal(a["phi"], b["phi"]) and np.array_equal(a["chi"], b["chi"])
-    Qr = replay_state(msf, torch, case, tapes, Q0)
+    Qr = replay_state(msf, torch, case, tapes, Q0, precision=precision)
     assert np.array_equal(Qr.cpu().numpy(), a["Q"])
 
 
