@@ -354,7 +354,10 @@ __global__ void k_prim(const __grid_constant__ Grid g, const __grid_constant__ B
 }
 
 // one Jacobi sweep: targets take the upwind-weighted mean of filled face
-// neighbours (weights max(0, n . e)), else the plain mean of filled neighbours
+// neighbours (weights max(0, n . e)), else the plain mean of filled neighbours.
+// Every neighbour value is loaded up front, unconditionally (face neighbours of
+// an interior cell lie inside the padded arrays), so that a sweep costs one
+// round of memory latency instead of one per neighbour.
 template <typename T>
 __device__ __forceinline__ void extend_items(const Grid& g, const Bufs& b, const void* Win, void* Wout,
                                              const uint8_t* fin, uint8_t* fout, int first, int stride) {
@@ -365,33 +368,47 @@ __device__ __forceinline__ void extend_items(const Grid& g, const Bufs& b, const
   for (int it = first; it < total; it += stride) {
     const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
-    if (!((b.smask[c] >> m) & 1u)) continue;
-    if (b.isreal[midx(g, m, c)]) {
-      fout[midx(g, m, c)] = 1;
-      continue;
-    }
+    const uint8_t smc = b.smask[c], realc = b.isreal[midx(g, m, c)], finc = fin[midx(g, m, c)];
     int q[3];
     coords(g, c, q);
     double n[3];
     stored_normal(g, b, c, m, n);
+    long long jn[6];
+    bool use[6];
+    T x[6][5];
+    for (int d = 0; d < D; d++)
+      for (int s = 0; s < 2; s++) {
+        const int i = 2 * d + s;
+        const long long j = s ? c + g.st[d] : c - g.st[d];
+        jn[i] = j;
+        const int bij = b.bandidx[j];
+        const unsigned smj = b.smask[j];
+        const uint8_t fj = fin[midx(g, m, j)];
+        use[i] = nb_interior(g, q, d, s) & (bij >= 0) & (((smj >> m) & 1u) != 0) & (fj != 0);
+        for (int v = 0; v < NV; v++) x[i][v] = Wi[qidx(g, m, v, j)];
+      }
+    if (!((smc >> m) & 1u)) continue;
+    if (realc) {
+      fout[midx(g, m, c)] = 1;
+      continue;
+    }
     T acc[5] = {T(0), T(0), T(0), T(0), T(0)}, acc2[5] = {T(0), T(0), T(0), T(0), T(0)};
     T sw = T(0);
     int cnt = 0;
     for (int d = 0; d < D; d++)
       for (int s = 0; s < 2; s++) {
-        if (!nb_interior(g, q, d, s)) continue;
-        const long long j = s ? c + g.st[d] : c - g.st[d];
-        if (b.bandidx[j] < 0 || !((b.smask[j] >> m) & 1u) || !fin[midx(g, m, j)]) continue;
+        const int i = 2 * d + s;
+        if (!use[i]) continue;
         T w = (T)(s ? n[d] : -n[d]);
         w = w > T(0) ? w : T(0);
         for (int v = 0; v < NV; v++) {
-          const T x = Wi[qidx(g, m, v, j)];
-          acc[v] += w * x;
-          acc2[v] += x;
+          acc[v] += w * x[i][v];
+          acc2[v] += x[i][v];
         }
         sw += w;
         cnt++;
       }
+    (void)jn;
     if (sw > T(0)) {
       for (int v = 0; v < NV; v++) Wo[qidx(g, m, v, c)] = acc[v] / sw;
       fout[midx(g, m, c)] = 1;
@@ -400,7 +417,7 @@ __device__ __forceinline__ void extend_items(const Grid& g, const Bufs& b, const
       fout[midx(g, m, c)] = 1;
     } else {
       for (int v = 0; v < NV; v++) Wo[qidx(g, m, v, c)] = Wi[qidx(g, m, v, c)];
-      fout[midx(g, m, c)] = fin[midx(g, m, c)];
+      fout[midx(g, m, c)] = finc;
     }
   }
 }
@@ -669,36 +686,52 @@ __device__ __forceinline__ void extend_vel_items(const Grid& g, const Bufs& b, c
   const int nb = b.ctl->nband, D = g.D;
   for (int k = first; k < nb; k += stride) {
     const long long c = b.band[k];
-    if (b.gflag[c] & GF_CUT) {
-      for (int e = 0; e < 3; e++) vout[e * g.ncell + c] = vin[e * g.ncell + c];
+    // every value the sweep may use, loaded up front (one round of latency)
+    const uint8_t gf = b.gflag[c], finc = fin[c];
+    const double phc = b.phi[c];
+    double vc[3];
+    for (int e = 0; e < 3; e++) vc[e] = vin[e * g.ncell + c];
+    int q[3];
+    coords(g, c, q);
+    bool use[6];
+    double phj[6], vj[6][3];
+    for (int d = 0; d < D; d++)
+      for (int s = 0; s < 2; s++) {
+        const int i = 2 * d + s;
+        const long long j = s ? c + g.st[d] : c - g.st[d];
+        const int bij = b.bandidx[j];
+        const uint8_t fj = fin[j];
+        use[i] = nb_interior(g, q, d, s) & (bij >= 0) & (fj != 0);
+        phj[i] = b.phi[j];
+        for (int e = 0; e < D; e++) vj[i][e] = vin[e * g.ncell + j];
+      }
+    if (gf & GF_CUT) {
+      for (int e = 0; e < 3; e++) vout[e * g.ncell + c] = vc[e];
       fout[c] = 1;
       continue;
     }
     double acc[3] = {0, 0, 0}, acc2[3] = {0, 0, 0};
     int cnt = 0, cnt2 = 0;
-    int q[3];
-    coords(g, c, q);
     for (int d = 0; d < D; d++)
       for (int s = 0; s < 2; s++) {
-        if (!nb_interior(g, q, d, s)) continue;
-        const long long j = s ? c + g.st[d] : c - g.st[d];
-        if (b.bandidx[j] < 0 || !fin[j]) continue;
-        for (int e = 0; e < D; e++) acc2[e] += vin[e * g.ncell + j];
+        const int i = 2 * d + s;
+        if (!use[i]) continue;
+        for (int e = 0; e < D; e++) acc2[e] += vj[i][e];
         cnt2++;
-        if (b.phi[j] < b.phi[c]) {
-          for (int e = 0; e < D; e++) acc[e] += vin[e * g.ncell + j];
+        if (phj[i] < phc) {
+          for (int e = 0; e < D; e++) acc[e] += vj[i][e];
           cnt++;
         }
       }
     uint8_t filled = 0;
-    for (int e = 0; e < 3; e++) vout[e * g.ncell + c] = vin[e * g.ncell + c];
+    for (int e = 0; e < 3; e++) vout[e * g.ncell + c] = vc[e];
     if (cnt > 0) {
       for (int e = 0; e < D; e++) vout[e * g.ncell + c] = acc[e] / (double)cnt;
       filled = 1;
     } else if (cnt2 > 0) {
       for (int e = 0; e < D; e++) vout[e * g.ncell + c] = acc2[e] / (double)cnt2;
       filled = 1;
-    } else if (fin[c]) {
+    } else if (finc) {
       filled = 1;
     }
     fout[c] = filled;
@@ -1060,26 +1093,32 @@ __device__ __forceinline__ void phase_levelset(const Grid& g, const Bufs& b, con
     const int r = it / nb, k = it - r * nb;
     const long long c = b.band[k];
     if (!((b.xsS[c] >> r) & 1u)) continue;
+    // the 7-point line of every axis, loaded up front (one round of latency)
+    double pl[3][7], vdir[3];
+    for (int d = 0; d < D; d++) {
+      vdir[d] = vel[d * g.ncell + c];
+      for (int i = 0; i < 7; i++) pl[d][i] = phir_stage(b, c + (long long)(i - 3) * g.st[d], r);
+    }
     double adv = 0.0;
     for (int d = 0; d < D; d++) {
-      const double vd = vel[d * g.ncell + c];
+      const double vd = vdir[d];
       if (vd == 0.0) continue;
-      const long long st = g.st[d];
       const double rh = g.rh[d];
+      const double* p = pl[d] + 3;  // p[i] = phi^r at c + i e_d
       double gd;
       if (vd > 0.0) {
-        double v1 = (phir_stage(b, c - 2 * st, r) - phir_stage(b, c - 3 * st, r)) * rh;
-        double v2 = (phir_stage(b, c - st, r) - phir_stage(b, c - 2 * st, r)) * rh;
-        double v3 = (phir_stage(b, c, r) - phir_stage(b, c - st, r)) * rh;
-        double v4 = (phir_stage(b, c + st, r) - phir_stage(b, c, r)) * rh;
-        double v5 = (phir_stage(b, c + 2 * st, r) - phir_stage(b, c + st, r)) * rh;
+        double v1 = (p[-2] - p[-3]) * rh;
+        double v2 = (p[-1] - p[-2]) * rh;
+        double v3 = (p[0] - p[-1]) * rh;
+        double v4 = (p[1] - p[0]) * rh;
+        double v5 = (p[2] - p[1]) * rh;
         gd = weno5<double>(v1, v2, v3, v4, v5, eps);
       } else {
-        double v1 = (phir_stage(b, c + 3 * st, r) - phir_stage(b, c + 2 * st, r)) * rh;
-        double v2 = (phir_stage(b, c + 2 * st, r) - phir_stage(b, c + st, r)) * rh;
-        double v3 = (phir_stage(b, c + st, r) - phir_stage(b, c, r)) * rh;
-        double v4 = (phir_stage(b, c, r) - phir_stage(b, c - st, r)) * rh;
-        double v5 = (phir_stage(b, c - st, r) - phir_stage(b, c - 2 * st, r)) * rh;
+        double v1 = (p[3] - p[2]) * rh;
+        double v2 = (p[2] - p[1]) * rh;
+        double v3 = (p[1] - p[0]) * rh;
+        double v4 = (p[0] - p[-1]) * rh;
+        double v5 = (p[-1] - p[-2]) * rh;
         gd = weno5<double>(v1, v2, v3, v4, v5, eps);
       }
       adv = adv + vd * gd;
