@@ -92,7 +92,10 @@ typedef struct {
  *                per msf_step call, one CTA per instance (largest first, CTA
  *                size autotuned on the first steps); 1 = the per-instance
  *                kernel sequence of a single instance, instance after instance
- *   stream       cudaStream_t for all work of this context */
+ *   stream       cudaStream_t for all work of this context
+ *   rk_stages    3: three-stage TVD Runge-Kutta (default); 2: the two-stage
+ *                TVD Runge-Kutta the paper uses (Sec. 3), beta_s = (0, 1/2)
+ *                in the form of Eq. local-advection */
 typedef struct {
   int32_t precision;
   double cfl, weno_eps, mix_alpha;
@@ -101,6 +104,7 @@ typedef struct {
   double scale_eps_h, phi_cap_h;
   int32_t use_graph, profile, batch_mode;
   void* stream;
+  int32_t rk_stages;
 } msf_options;
 
 /* Fill opt with the defaults above for a grid of dimension dim. */

@@ -47,6 +47,7 @@
 struct orc {
   orc_params p;
   int D, N, NV;
+  int S; /* Runge-Kutta stages */
   int n[3], pn[3], off[3];
   long st[3], ncell;
   double h[3], rh[3], rh2[3], ih2[3], farea[3], V, rV, hmin, eps_ss, cap;
@@ -786,8 +787,16 @@ static void extend_velocity(orc* o) {
 /* ------------------------------------------------------------------ */
 /* fluxes and the RK stage update (a8, Eq. discretized_equ)            */
 /* ------------------------------------------------------------------ */
-static const double BETA[3] = {0.0, 0.75, 1.0 / 3.0};
-static const double LEDGER_W[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+/* Shu-Osher TVD Runge-Kutta in the beta form of Eq. local-advection:
+ * Q^(s+1) = beta_s Q^n + (1 - beta_s) (Q^(s) + dt L(Q^(s))). The ledger weight
+ * of stage s is the coefficient of dt L(Q^(s)) in Q^{n+1}. Three stages
+ * (beta = 0, 3/4, 1/3) or the paper's two (beta = 0, 1/2). */
+static const double BETA3[3] = {0.0, 0.75, 1.0 / 3.0};
+static const double LEDGER_W3[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+static const double BETA2[2] = {0.0, 0.5};
+static const double LEDGER_W2[2] = {0.5, 0.5};
+static double rk_beta(const orc* o, int s) { return o->S == 2 ? BETA2[s] : BETA3[s]; }
+static double rk_ledger_w(const orc* o, int s) { return o->S == 2 ? LEDGER_W2[s] : LEDGER_W3[s]; }
 
 static void face_flux(orc* o, long cL, int d, int m, double* Fh) {
   int NV = o->NV, D = o->D;
@@ -853,7 +862,7 @@ static void flux_update(orc* o, int s, const double* Qs, double* Qout) {
           for (int v = 0; v < NV; v++) Fb[m][v] -= A * Fh[v] * o->farea[d];
       }
     }
-  double beta = BETA[s], omb = 1.0 - BETA[s], dt = o->dt;
+  double beta = rk_beta(o, s), omb = 1.0 - rk_beta(o, s), dt = o->dt;
   for (long c = 0; c < o->ncell; c++) {
     if (!interior_c(o, c)) continue;
     for (int m = 0; m < N; m++) {
@@ -879,7 +888,7 @@ static void flux_update(orc* o, int s, const double* Qs, double* Qout) {
     }
   }
   for (int m = 0; m < N; m++)
-    for (int v = 0; v < NV; v++) o->ledger[m][v] += LEDGER_W[s] * dt * Fb[m][v];
+    for (int v = 0; v < NV; v++) o->ledger[m][v] += rk_ledger_w(o, s) * dt * Fb[m][v];
 }
 
 /* ------------------------------------------------------------------ */
@@ -890,7 +899,7 @@ static double phir_at(const orc* o, long c, int r) { return phim(o, c, r); }
 
 static void levelset_stage(orc* o, int s) {
   int N = o->N, D = o->D;
-  double beta = BETA[s], omb = 1.0 - BETA[s], dt = o->dt, eps = o->p.weno_eps;
+  double beta = rk_beta(o, s), omb = 1.0 - rk_beta(o, s), dt = o->dt, eps = o->p.weno_eps;
   for (long c = 0; c < o->ncell; c++) {
     o->phit[c] = o->phi[c];
     o->chit[c] = o->chi[c];
@@ -1252,9 +1261,9 @@ static int step_once(orc* o, double t_end, double* tphi, uint8_t* tchi, double* 
   memcpy(o->phin, o->phi, sizeof(double) * nc);
   memcpy(o->chin, o->chi, nc);
   int last = 0;
-  for (int s = 0; s < 3; s++) {
+  for (int s = 0; s < o->S; s++) {
     double* Qs = s == 0 ? o->Q : (s == 1 ? o->Q1 : o->Q2);
-    double* Qo = s == 0 ? o->Q1 : (s == 1 ? o->Q2 : o->Q);
+    double* Qo = s == o->S - 1 ? o->Q : (s == 0 ? o->Q1 : o->Q2);
     prim_extend(o, Qs);
     bc_uhat(o);
     if (s == 0) {
@@ -1321,8 +1330,10 @@ int orc_replay_step(orc* o, const double* tphi, const uint8_t* tchi, double dt) 
 
 orc* orc_create(const orc_params* p) {
   if (p->dim < 1 || p->dim > 3 || p->nmat < 1 || p->nmat > ORC_MAXM) return NULL;
+  if (p->rk_stages != 0 && p->rk_stages != 2 && p->rk_stages != 3) return NULL;
   orc* o = (orc*)calloc(1, sizeof(orc));
   o->p = *p;
+  o->S = p->rk_stages == 2 ? 2 : 3;
   o->D = p->dim;
   o->N = p->nmat;
   o->NV = p->dim + 2;

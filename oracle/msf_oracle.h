@@ -26,6 +26,7 @@ typedef struct {
   int32_t scale_sep, reinit;
   double scale_eps_h;        /* epsilon / h_min of the scale separation */
   double phi_cap_h;          /* level-set clamp, in units of h_min */
+  int32_t rk_stages;         /* 3: TVD-RK3 (0 means 3); 2: the TVD-RK2 of Sec. 3 */
 } orc_params;
 
 typedef struct orc orc;

@@ -37,7 +37,7 @@ class Params(C.Structure):
         ("cfl", C.c_double), ("weno_eps", C.c_double), ("mix_alpha", C.c_double),
         ("ext_sweeps", C.c_int32), ("vel_sweeps", C.c_int32), ("reinit_iters", C.c_int32),
         ("scale_sep", C.c_int32), ("reinit", C.c_int32),
-        ("scale_eps_h", C.c_double), ("phi_cap_h", C.c_double),
+        ("scale_eps_h", C.c_double), ("phi_cap_h", C.c_double), ("rk_stages", C.c_int32),
     ]
 
 
@@ -99,7 +99,7 @@ def make_params(p: dict) -> Params:
         s.pinf[m] = p["pinf"][m]
     for k in ("cfl", "weno_eps", "mix_alpha", "scale_eps_h", "phi_cap_h"):
         setattr(s, k, float(p[k]))
-    for k in ("ext_sweeps", "vel_sweeps", "reinit_iters", "scale_sep", "reinit"):
+    for k in ("ext_sweeps", "vel_sweeps", "reinit_iters", "scale_sep", "reinit", "rk_stages"):
         setattr(s, k, int(p[k]))
     return s
 

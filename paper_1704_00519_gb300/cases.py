@@ -75,7 +75,7 @@ class Case:
 
 def default_options(dim):
     return dict(cfl=0.6, weno_eps=1e-6, mix_alpha=0.5, ext_sweeps=dim + 3, vel_sweeps=6,
-                reinit_iters=6, scale_sep=1, reinit=1, scale_eps_h=0.0, phi_cap_h=8.0)
+                reinit_iters=6, scale_sep=1, reinit=1, scale_eps_h=0.0, phi_cap_h=8.0, rk_stages=3)
 
 
 def centres(n, lo, hi):
@@ -100,6 +100,19 @@ def shock_tube_3(n=400):
     states = [(1.0, 0.0, 1.0), (0.125, 0.0, 0.1), (0.5, 0.0, 0.1)]
     return Case("shock_tube_3", 1, (n,), (0.0,), (1.0,), [[TRANSMISSIVE, TRANSMISSIVE]],
                 [1.4, 1.667, 1.4], [0.0, 0.0, 0.0], phi, chi, _uniform_prim(3, 1, n, states), 0.2)
+
+
+def he_air_tube(n=200, gamma_right=1.667):
+    """The paper's Case I (Sec. 3.1): helium | air | helium between walls, the
+    air slab on [0.4, 0.6) as the text places it (its Table 1 prints 0.25 and
+    0.5); states of Table 1, u = 0. gamma_right = 1.249 gives the
+    helium-air-R22 variant of the table's footnote."""
+    (x,) = centres((n,), (0.0,), (1.0,))
+    chi = np.where(x < 0.4, 0, np.where(x < 0.6, 1, 2)).astype(np.int32)
+    phi = np.minimum(np.abs(x - 0.4), np.abs(x - 0.6))
+    states = [(0.125, 0.0, 0.1), (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)]
+    return Case("he_air_tube", 1, (n,), (0.0,), (1.0,), [[REFLECTIVE, REFLECTIVE]],
+                [1.667, 1.4, gamma_right], [0.0, 0.0, 0.0], phi, chi, _uniform_prim(3, 1, n, states), 0.1)
 
 
 def triple_point(nx=896, ny=384):

@@ -106,6 +106,7 @@ extern "C" msf_status msf_default_options(int32_t dim, msf_options* opt) {
   opt->profile = 0;
   opt->batch_mode = 0;
   opt->stream = nullptr;
+  opt->rk_stages = 3;
   return MSF_OK;
 }
 
@@ -130,7 +131,8 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
   if (opt->precision != MSF_FP64 && opt->precision != MSF_FP32_BULK) return fail(nullptr, MSF_EINVAL, "precision");
   if (!(opt->cfl > 0.0 && opt->cfl <= 1.0) || !(opt->weno_eps > 0.0) || !(opt->mix_alpha >= 0.0 && opt->mix_alpha < 1.0) ||
       opt->ext_sweeps < 1 || opt->ext_sweeps > 64 || opt->vel_sweeps < 0 || opt->vel_sweeps > 64 ||
-      opt->reinit_iters < 0 || opt->reinit_iters > 64 || !(opt->phi_cap_h >= 4.0) || !(opt->scale_eps_h >= 0.0))
+      opt->reinit_iters < 0 || opt->reinit_iters > 64 || !(opt->phi_cap_h >= 4.0) || !(opt->scale_eps_h >= 0.0) ||
+      (opt->rk_stages != 2 && opt->rk_stages != 3))
     return fail(nullptr, MSF_EINVAL, "option out of range");
   for (int i = 0; i < n_instances; i++) {
     const msf_grid& gr = grids[i];
@@ -242,6 +244,16 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
     g.reinit_iters = opt->reinit_iters;
     g.scale_sep = opt->scale_sep;
     g.reinit = opt->reinit;
+    // Shu-Osher TVD Runge-Kutta in the beta form; the ledger weight of stage s
+    // is the coefficient of dt L(Q^(s)) in Q^{n+1}
+    g.rk = opt->rk_stages;
+    if (g.rk == 2) {
+      g.rk_beta[0] = 0.0; g.rk_beta[1] = 0.5; g.rk_beta[2] = 0.0;
+      g.rk_lw[0] = 0.5; g.rk_lw[1] = 0.5; g.rk_lw[2] = 0.0;
+    } else {
+      g.rk_beta[0] = 0.0; g.rk_beta[1] = 0.75; g.rk_beta[2] = 1.0 / 3.0;
+      g.rk_lw[0] = 1.0 / 6.0; g.rk_lw[1] = 1.0 / 6.0; g.rk_lw[2] = 2.0 / 3.0;
+    }
     // boundary faces, numbered per (axis, side)
     long long nb = 0;
     for (int d = 0; d < dim; d++)
@@ -394,7 +406,7 @@ static long long count_launches(const msf_ctx* c) {
     const long long ext = tiled_ext(c, g) ? 1 : g.ext_sweeps;
     const long long vel = g.vel_sweeps, re = 2LL * g.reinit_iters;
     const long long per_stage = 1 + ext + 1 + 1 + 1 + vel + 1 + 1 + 1 + 1 + 1 + 2 + 3;
-    n += 1 + 1 + (2 + g.D) + 2 + 1 + 3 * per_stage + 2 + 1;
+    n += 1 + 1 + (2 + g.D) + 2 + 1 + g.rk * per_stage + 2 + 1;
     if (g.scale_sep) n += 2 + 1;
     if (g.reinit) n += re + 1;
   }
@@ -451,11 +463,10 @@ static msf_status enqueue_step(msf_ctx* c, char* tape = nullptr) {
     launch_masks(g, b, s);
     launch_geometry(g, b, b.Q[0], nullptr, nb, s);
     launch_band_save(g, b, nb, s);
-    const double BETA[3] = {0.0, 0.75, 1.0 / 3.0};
-    const double LW[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
-    for (int st = 0; st < 3; st++) {
+    for (int st = 0; st < g.rk; st++) {
+      const double beta = g.rk_beta[st];
       double* Qs = b.Q[st];
-      double* Qo = b.Q[(st + 1) % 3];
+      double* Qo = st == g.rk - 1 ? b.Q[0] : b.Q[st + 1];
       c->ops->prim(g, b, Qs, nb, s);
       void* W[2] = {b.W0, b.W1};
       uint8_t* F[2] = {b.f0, b.f1};
@@ -487,11 +498,11 @@ static msf_status enqueue_step(msf_ctx* c, char* tape = nullptr) {
       }
       const bool prof = c->ev[0] && &in == &c->inst[0];
       if (prof) cudaEventRecord(c->ev[2 * st], s);
-      cudaError_t fe = c->ops->flux(g, b, Qs, b.Q[0], Qo, BETA[st], 1.0 - BETA[st], in.bb, s);
+      cudaError_t fe = c->ops->flux(g, b, Qs, b.Q[0], Qo, beta, 1.0 - beta, in.bb, s);
       if (fe != cudaSuccess) return fail(c, MSF_ECUDA, std::string("flux launch: ") + cudaGetErrorString(fe));
       if (prof) cudaEventRecord(c->ev[2 * st + 1], s);
-      launch_ledger(g, b, in.nbnd, LW[st], s);
-      launch_levelset(g, b, V[vc], BETA[st], 1.0 - BETA[st], nb, s);
+      launch_ledger(g, b, in.nbnd, g.rk_lw[st], s);
+      launch_levelset(g, b, V[vc], beta, 1.0 - beta, nb, s);
       launch_bc_phichi(g, b, s);
       if (tape) tape_slot_save(in, tape, st + 1, s);
       launch_geometry(g, b, Qo, nullptr, nb, s);
@@ -854,15 +865,13 @@ extern "C" msf_status msf_profile_read(msf_ctx* c, double* flux_ms) {
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   for (int st = 0; st < 3; st++) {
     float ms = 0.0f;
-    CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev[2 * st], c->ev[2 * st + 1]));
+    if (st < c->inst[0].g.rk) CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev[2 * st], c->ev[2 * st + 1]));
     flux_ms[st] = ms;
   }
   return MSF_OK;
 }
 
 // ------------------------------------------------ tapes, replay, adjoint
-static const double RK_BETA[3] = {0.0, 0.75, 1.0 / 3.0};
-
 static msf_status check_single(msf_ctx* c) {
   if (!c) return MSF_EINVAL;
   if (c->ninst != 1 || c->batched) return fail(c, MSF_EUNSUPPORTED, "tapes and the adjoint need a single-instance context");
@@ -946,9 +955,9 @@ static void enqueue_replay(msf_ctx* c, const char* tape, bool rec) {
   launch_geometry(g, b, b.Q[0], nullptr, nb, s);
   launch_band_save(g, b, nb, s);
   if (rec) launch_adj_alpha(g, b, a.aband[0], 1, nb, s);
-  for (int st = 0; st < 3; st++) {
+  for (int st = 0; st < g.rk; st++) {
     double* Qs = b.Q[st];
-    double* Qo = b.Q[(st + 1) % 3];
+    double* Qo = st == g.rk - 1 ? b.Q[0] : b.Q[st + 1];
     c->ops->prim(g, b, Qs, nb, s);
     void* W[2] = {b.W0, b.W1};
     uint8_t* F[2] = {b.f0, b.f1};
@@ -960,8 +969,8 @@ static void enqueue_replay(msf_ctx* c, const char* tape, bool rec) {
     c->ops->cons(g, b, Qs, W[cur], F[cur], nb, s);
     c->ops->bc_uhat(g, b, Qs, s);
     c->ops->interface(g, b, Qs, nb, s);
-    c->ops->flux(g, b, Qs, b.Q[0], Qo, RK_BETA[st], 1.0 - RK_BETA[st], in.bb, s);
-    launch_ledger(g, b, in.nbnd, st == 2 ? 2.0 / 3.0 : 1.0 / 6.0, s);
+    c->ops->flux(g, b, Qs, b.Q[0], Qo, g.rk_beta[st], 1.0 - g.rk_beta[st], in.bb, s);
+    launch_ledger(g, b, in.nbnd, g.rk_lw[st], s);
     tape_slot_load(in, tape, st + 1, s);
     launch_geometry(g, b, Qo, nullptr, nb, s);
     if (rec) {
@@ -1038,10 +1047,10 @@ extern "C" msf_status msf_adjoint_step(msf_ctx* c, const void* tape_, const doub
   enqueue_replay(c, tape, true);
   void* W[2] = {b.W0, b.W1};
   uint8_t* F[2] = {b.f0, b.f1};
-  for (int sg = 2; sg >= 0; sg--) {
+  for (int sg = g.rk - 1; sg >= 0; sg--) {
     if (sg == 0) CUDA_TRY(c, cudaMemcpyAsync(b.Q[0], tape + L.q, qbytes, cudaMemcpyDeviceToDevice, s));
     const double* Qs = b.Q[sg];
-    const double beta = RK_BETA[sg], omb = 1.0 - RK_BETA[sg];
+    const double beta = g.rk_beta[sg], omb = 1.0 - g.rk_beta[sg];
     // stage-s geometry and states of the forward step
     tape_slot_load(in, tape, sg, s);
     launch_geometry(g, b, Qs, nullptr, nb, s);
@@ -1075,7 +1084,7 @@ extern "C" msf_status msf_adjoint_step(msf_ctx* c, const void* tape_, const doub
       lc ^= 1;
     }
     launch_adj_prim(g, b, a, Qs, LW[lc], nb, s);
-    launch_adj_combine(g, b, a, beta, omb, sg == 2 ? 1 : 0, s);
+    launch_adj_combine(g, b, a, beta, omb, sg == g.rk - 1 ? 1 : 0, s);
   }
   launch_adj_io(g, a, nullptr, lam_in, 1, s);
   // back to the state at the start of the tape's step

@@ -33,6 +33,8 @@ struct Grid {
   double gamma[MAXM], pinf[MAXM], gm1[MAXM], gpi[MAXM];
   double cfl, weno_eps, mix_alpha;
   int ext_sweeps, vel_sweeps, reinit_iters, scale_sep, reinit;
+  int rk;                       // Runge-Kutta stages (2 or 3)
+  double rk_beta[3], rk_lw[3];  // beta_s of Eq. local-advection; ledger weight of stage s
   int bc[3][2], inflow_mat[3][2];
   double inflow_prim[3][2][5];
   long long n_interior;

@@ -1628,8 +1628,6 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
   const int t = threadIdx.x, nt = BS;
   T* Ff = (T*)E.Fface;
   double* Af = E.Aface;
-  const double BETA[3] = {0.0, 0.75, 1.0 / 3.0};
-  const double LW[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
   for (int step = 0; step < n_steps; step++) {
     if (t == 0) {
       Ctl* c = b.ctl;
@@ -1653,9 +1651,10 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
     __syncthreads();
     phase_band_save(g, b, t, nt);
     __syncthreads();
-    for (int s = 0; s < 3; s++) {
+    for (int s = 0; s < g.rk; s++) {
       const double* Qs = b.Q[s];
-      double* Qo = b.Q[(s + 1) % 3];
+      double* Qo = s == g.rk - 1 ? b.Q[0] : b.Q[s + 1];
+      const double beta = g.rk_beta[s];
       phase_prim<T>(g, b, Qs, t, nt);
       __syncthreads();
       int cur = 0;
@@ -1699,16 +1698,16 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
       unsigned err = 0;
       flux1d_faces<T>(g, b, Qs, Ff, Af, E.bb, t, nt, err);
       __syncthreads();
-      flux1d_update<T>(g, b, Qs, b.Q[0], Qo, BETA[s], 1.0 - BETA[s], Ff, Af, t, nt, err);
+      flux1d_update<T>(g, b, Qs, b.Q[0], Qo, beta, 1.0 - beta, Ff, Af, t, nt, err);
       if (err) atomicOr(&b.ctl->err, err);
       __syncthreads();
       for (int mv = t; mv < g.N * g.NV; mv += nt) {
         double sum = 0.0;
         for (int f = 0; f < E.nbnd; f++) sum += b.bflux[(long long)f * g.N * g.NV + mv];
-        b.ctl->ledger[mv / g.NV][mv % g.NV] += LW[s] * b.ctl->dt * sum;
+        b.ctl->ledger[mv / g.NV][mv % g.NV] += g.rk_lw[s] * b.ctl->dt * sum;
       }
       __syncthreads();
-      phase_levelset(g, b, vc ? b.vel1 : b.vel0, BETA[s], 1.0 - BETA[s], t, nt);
+      phase_levelset(g, b, vc ? b.vel1 : b.vel0, beta, 1.0 - beta, t, nt);
       __syncthreads();
       phase_levelset_R(g, b, t, nt);
       __syncthreads();

@@ -54,8 +54,13 @@ def noisy_state(torch, case, Q0, seed=1):
     return Q0 * torch.tensor(1.0 + NOISE * g.uniform(-1, 1, Q0.shape), device=Q0.device)
 
 
+def _opts(case):
+    """Run options a case needs (the paper's Case I runs the two-stage scheme)."""
+    return {"rk_stages": 2} if case.name == "he_air_tube" else {}
+
+
 def record(msf, case, steps, precision=0, Q0=None):
-    s = msf.Solver(case, precision=precision)
+    s = msf.Solver(case, precision=precision, **_opts(case))
     if Q0 is not None:
         s.set_conserved(Q0)
     tapes = []
@@ -67,7 +72,7 @@ def record(msf, case, steps, precision=0, Q0=None):
 
 
 def replay_state(msf, torch, case, tapes, Q0, precision=0):
-    s = msf.Solver(case, precision=precision)
+    s = msf.Solver(case, precision=precision, **_opts(case))
     s.set_conserved(Q0)
     for tp in tapes:
         s.replay_step(tp)
@@ -89,6 +94,7 @@ def adjoint_chain(s, tapes, lam):
 
 CASES = {
     "shock_tube_3": (lambda: cs.shock_tube_3(120), 8),
+    "he_air_tube_rk2": (lambda: cs.he_air_tube(120), 8),
     "riemann_1d": (lambda: cs.riemann_1d(np.random.default_rng(5), 160, 3), 8),
     "triple_point": (lambda: cs.triple_point(56, 24), 6),
     "shock_bubbles_inflow": (lambda: cs.shock_bubbles(96, 32), 6),

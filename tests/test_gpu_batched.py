@@ -22,13 +22,13 @@ def msf():
     return m
 
 
-def _clean_batch(count, seed, lo=60, hi=420, steps=12):
+def _clean_batch(count, seed, lo=60, hi=420, steps=12, **opts):
     """Seeded Riemann problems that the oracle runs without a device error."""
     rng = np.random.default_rng(seed)
     out = []
     while len(out) < count:
         c = cs.riemann_1d(rng, ncell=int(rng.integers(lo, hi)))
-        o = orc.Oracle(c)
+        o = orc.Oracle(c, **opts)
         if o.step(steps, c.t_end) == 0:
             out.append((c, o))
     return out
@@ -88,3 +88,16 @@ def test_batched_conservation_and_end_time(msf):
         tot, led = batch.totals(i)
         scale = max(np.abs(tot0[i]).sum(), np.abs(tot).sum())
         assert np.abs((tot - tot0[i] - led).sum(0)).max() / scale < 1e-12
+
+
+def test_batched_rk2_matches_oracle(msf):
+    """The persistent batched kernel with the two-stage TVD Runge-Kutta of
+    Sec. 3: FP64 bit-identical to the oracle per instance."""
+    steps = 10
+    pairs = _clean_batch(8, 11, steps=steps, rk_stages=2)
+    batch = msf.Batch([c for c, _ in pairs], precision=0, rk_stages=2)
+    batch.step(steps, 0.1)
+    for i, (c, o) in enumerate(pairs):
+        a, b = batch.state(i), o.state()
+        assert np.array_equal(a["Q"][:c.nmat], b["Q"]), i
+        assert np.array_equal(a["phi"], b["phi"])

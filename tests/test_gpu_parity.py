@@ -206,6 +206,26 @@ def test_full_size_fp32_form_against_fp64(msf, maker, steps):
     assert l1_rho(states[1]["Q"], states[0]["Q"]) <= FP32_L1
 
 
+@pytest.mark.parametrize("gamma_right", [1.667, 1.249])
+def test_paper_case_one_rk2_fp64(msf, gamma_right):
+    """The paper's Case I (helium | air | helium between walls; the R22
+    variant) with its two-stage TVD Runge-Kutta, full run to t = 0.1: FP64
+    bit-identical to the oracle."""
+    case = cs.he_air_tube(200, gamma_right)
+    o, s, eo = run_pair(msf, case, 100000, rk_stages=2)
+    assert eo == 0
+    compare(o, s, FP64_L1, exact=True)
+
+
+def test_rk2_triple_point_fp64_and_fp32(msf):
+    case = cs.triple_point(112, 48)
+    o, s, eo = run_pair(msf, case, 40, rk_stages=2)
+    compare(o, s, FP64_L1, exact=True)
+    s32 = msf.Solver(case, precision=msf.MSF_FP32_BULK, rk_stages=2)
+    s32.step(40, case.t_end)
+    compare(o, s32, FP32_L1)
+
+
 def test_host_validation_rejects_bad_levelset(msf):
     case = cs.shock_tube_3(50)
     s = msf.Solver(case)
