@@ -62,10 +62,22 @@ typedef struct {
   int32_t inflow_mat[3][2];
 } msf_grid;
 
-/* Stiffened gas p = (gamma - 1) rho e - gamma pinf (Sec. 2.1; pinf = 0 is the
- * ideal gas of Sec. 2.1). Sound speed c^2 = gamma (p + pinf) / rho (Sec. 2.3.2). */
+/* Equation of state of one material (Sec. 2.1).
+ * kind MSF_EOS_STIFFENED (0): stiffened gas p = (gamma - 1) rho e - gamma pinf
+ *   (pinf = 0 is the ideal gas); sound speed c^2 = gamma (p + pinf) / rho.
+ * kind MSF_EOS_TAIT (1): Tait's equation p = B (rho/rho0)^gamma - B + p0 with
+ *   gamma, tait_B > 0, tait_rho0 > 0, tait_p0 (pinf is ignored). The pressure
+ *   does not depend on the internal energy; the energy of a state given by
+ *   (rho, u, p) and the sound speed are those of the stiffened gas with
+ *   pinf = B - p0, whose isentrope through (rho0, p0) is Tait's curve; in the
+ *   HLLC wave speeds (Sec. 2.3.2) Psi = c^2 and Upsilon = 0.
+ * The adjoint step and msf_cfl_dt_noalloc take stiffened gases only. */
+#define MSF_EOS_STIFFENED 0
+#define MSF_EOS_TAIT 1
 typedef struct {
   double gamma, pinf;
+  int32_t kind;
+  double tait_B, tait_rho0, tait_p0;
 } msf_eos;
 
 /* Run options. Zero-initialise and call msf_default_options() first.

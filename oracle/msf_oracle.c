@@ -11,7 +11,9 @@
  * method states its steps. Where the paper is silent the fixed readings
  * below are used (the CUDA path makes the same choices independently):
  *
- *   EOS        stiffened gas p = (g-1) rho e - g pinf, c^2 = g (p+pinf)/rho
+ *   EOS        stiffened gas p = (g-1) rho e - g pinf, c^2 = g (p+pinf)/rho;
+ *              or Tait's p = B (rho/rho0)^g - B + p0 with the energy and the
+ *              sound speed of the stiffened gas with pinf = B - p0 (Sec. 2.1)
  *              (Sec. 2.1; pinf = 0 gives the ideal gas of Sec. 2.1).
  *   geometry   per-material local field phi^m = C_m(phi, chi) (Sec. 2.2,
  *              construction operator); piecewise-linear interpolant on a
@@ -116,8 +118,16 @@ static int popc(unsigned x) {
 }
 
 /* ------------------------------------------------------------------ */
-/* EOS (Sec. 2.1, 2.3.2): stiffened gas                                 */
+/* EOS (Sec. 2.1, 2.3.2): stiffened gas, or Tait's equation             */
 /* ------------------------------------------------------------------ */
+/* Tait's equation (Sec. 2.1): p = B (rho / rho0)^gamma - B + p0. Its
+ * pressure does not depend on the internal energy; the energy carried with
+ * it is that of the stiffened gas with pinf = B - p0 (the gas whose isentrope
+ * through (rho0, p0) is Tait's curve), which is what prim_to_cons uses. */
+static double tait_pressure(const orc* o, int m, double rho) {
+  double B = o->p.tait_B[m];
+  return B * pow(rho / o->p.tait_rho0[m], o->p.gamma[m]) - B + o->p.tait_p0[m];
+}
 /* conservative (rho, rho u_d, rho E) -> primitive (rho, u_d, p) */
 static void cons_to_prim(const orc* o, int m, const double* u, double* w) {
   int D = o->D;
@@ -129,7 +139,7 @@ static void cons_to_prim(const orc* o, int m, const double* u, double* w) {
   double ke = 0.5 * rho * q;
   w[0] = rho;
   for (int d = 0; d < D; d++) w[1 + d] = vel[d];
-  w[D + 1] = o->gm1[m] * (u[D + 1] - ke) - o->gpi[m];
+  w[D + 1] = o->p.eos_kind[m] == 1 ? tait_pressure(o, m, rho) : o->gm1[m] * (u[D + 1] - ke) - o->gpi[m];
 }
 static void prim_to_cons(const orc* o, int m, const double* w, double* u) {
   int D = o->D;
@@ -182,7 +192,9 @@ double orc_weno5(double a, double b, double c, double d, double e, double eps) {
 
 /* ------------------------------------------------------------------ */
 /* HLLC interface state for two general-EOS states (Sec. 2.3.2)        */
-/* w = (rho, u_n, p), eos = (gamma, pinf)                              */
+/* w = (rho, u_n, p), eos = (gamma, pinf, kind); c^2 = Psi + Upsilon p/rho:
+ * stiffened gas Psi = (p + gamma pinf)/rho, Upsilon = gamma - 1; Tait
+ * (pinf = B - p0) Psi = gamma (p + pinf)/rho, Upsilon = 0                 */
 /* ------------------------------------------------------------------ */
 void orc_hllc(const double* wl, const double* wr, const double* eosl, const double* eosr,
               double* ustar, double* pstar) {
@@ -191,8 +203,10 @@ void orc_hllc(const double* wl, const double* wr, const double* eosl, const doub
   double c2l = (gl * (pl + pil)) / rl, c2r = (gr * (pr + pir)) / rr;
   double cl = sqrt(c2l > 0.0 ? c2l : 0.0), cr = sqrt(c2r > 0.0 ? c2r : 0.0);
   /* Psi = dp/drho|_e, Upsilon = (1/rho) dp/de|_rho */
-  double psil = (pl + gl * pil) / rl, psir = (pr + gr * pir) / rr;
-  double upsl = gl - 1.0, upsr = gr - 1.0;
+  int tl = eosl[2] == 1.0, tr = eosr[2] == 1.0;
+  double psil = tl ? (gl * (pl + pil)) / rl : (pl + gl * pil) / rl;
+  double psir = tr ? (gr * (pr + pir)) / rr : (pr + gr * pir) / rr;
+  double upsl = tl ? 0.0 : gl - 1.0, upsr = tr ? 0.0 : gr - 1.0;
   double sl = sqrt(rl), sr = sqrt(rr);
   double den = sl + sr;
   double psit = (sl * psil + sr * psir) / den;
@@ -724,7 +738,8 @@ static void interface_exchange(orc* o, const double* Qs) {
     double unl = 0.0, unr = 0.0;
     for (int d = 0; d < D; d++) { unl += wL[1 + d] * n[d]; unr += wR[1 + d] * n[d]; }
     double rl[3] = {wL[0], unl, wL[D + 1]}, rr[3] = {wR[0], unr, wR[D + 1]};
-    double el[2] = {o->p.gamma[L], o->p.pinf[L]}, er[2] = {o->p.gamma[R], o->p.pinf[R]};
+    double el[3] = {o->p.gamma[L], o->p.pinf[L], (double)o->p.eos_kind[L]};
+    double er[3] = {o->p.gamma[R], o->p.pinf[R], (double)o->p.eos_kind[R]};
     double us, ps;
     orc_hllc(rl, rr, el, er, &us, &ps);
     /* the pair's interface state acts on the boundary segment of every other
@@ -1331,8 +1346,13 @@ int orc_replay_step(orc* o, const double* tphi, const uint8_t* tchi, double dt) 
 orc* orc_create(const orc_params* p) {
   if (p->dim < 1 || p->dim > 3 || p->nmat < 1 || p->nmat > ORC_MAXM) return NULL;
   if (p->rk_stages != 0 && p->rk_stages != 2 && p->rk_stages != 3) return NULL;
+  for (int m = 0; m < p->nmat; m++)
+    if (p->eos_kind[m] == 1 && !(p->tait_B[m] > 0.0 && p->tait_rho0[m] > 0.0)) return NULL;
   orc* o = (orc*)calloc(1, sizeof(orc));
   o->p = *p;
+  /* Tait materials: the effective pinf of the sound speed and of the energy */
+  for (int m = 0; m < p->nmat; m++)
+    if (p->eos_kind[m] == 1) o->p.pinf[m] = p->tait_B[m] - p->tait_p0[m];
   o->S = p->rk_stages == 2 ? 2 : 3;
   o->D = p->dim;
   o->N = p->nmat;
@@ -1361,8 +1381,8 @@ orc* orc_create(const orc_params* p) {
   o->eps_ss = ce * o->hmin;
   o->cap = p->phi_cap_h * o->hmin;
   for (int m = 0; m < o->N; m++) {
-    o->gm1[m] = p->gamma[m] - 1.0;
-    o->gpi[m] = p->gamma[m] * p->pinf[m];
+    o->gm1[m] = o->p.gamma[m] - 1.0;
+    o->gpi[m] = o->p.gamma[m] * o->p.pinf[m];
   }
   long nc = o->ncell, N = o->N, NV = o->NV;
   o->Q = (double*)calloc((size_t)(N * NV * nc), 8);

@@ -27,6 +27,10 @@ typedef struct {
   double scale_eps_h;        /* epsilon / h_min of the scale separation */
   double phi_cap_h;          /* level-set clamp, in units of h_min */
   int32_t rk_stages;         /* 3: TVD-RK3 (0 means 3); 2: the TVD-RK2 of Sec. 3 */
+  /* equation of state per material: 0 stiffened gas (gamma, pinf); 1 Tait's
+   * equation p = B (rho/rho0)^gamma - B + p0 (Sec. 2.1; gamma, tait_*) */
+  int32_t eos_kind[ORC_MAXM];
+  double tait_B[ORC_MAXM], tait_rho0[ORC_MAXM], tait_p0[ORC_MAXM];
 } orc_params;
 
 typedef struct orc orc;
@@ -65,6 +69,7 @@ void orc_debug_field(const orc* o, int32_t which, double* out);
 
 /* building blocks, exported for pins */
 double orc_weno5(double a, double b, double c, double d, double e, double eps);
+/* eosl, eosr = (gamma, pinf, kind); kind 1 = Tait (pinf = B - p0) */
 void orc_hllc(const double* wl, const double* wr, const double* eosl, const double* eosr,
               double* ustar, double* pstar);
 double orc_seg_frac(double a, double b);

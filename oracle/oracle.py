@@ -38,6 +38,8 @@ class Params(C.Structure):
         ("ext_sweeps", C.c_int32), ("vel_sweeps", C.c_int32), ("reinit_iters", C.c_int32),
         ("scale_sep", C.c_int32), ("reinit", C.c_int32),
         ("scale_eps_h", C.c_double), ("phi_cap_h", C.c_double), ("rk_stages", C.c_int32),
+        ("eos_kind", C.c_int32 * MAXM), ("tait_B", C.c_double * MAXM),
+        ("tait_rho0", C.c_double * MAXM), ("tait_p0", C.c_double * MAXM),
     ]
 
 
@@ -97,6 +99,8 @@ def make_params(p: dict) -> Params:
     for m in range(p["nmat"]):
         s.gamma[m] = p["gamma"][m]
         s.pinf[m] = p["pinf"][m]
+        s.eos_kind[m] = int(p["eos_kind"][m])
+        s.tait_B[m], s.tait_rho0[m], s.tait_p0[m] = (float(x) for x in p["tait"][m])
     for k in ("cfl", "weno_eps", "mix_alpha", "scale_eps_h", "phi_cap_h"):
         setattr(s, k, float(p[k]))
     for k in ("ext_sweeps", "vel_sweeps", "reinit_iters", "scale_sep", "reinit", "rk_stages"):
@@ -205,7 +209,11 @@ def weno5(a, b, c, d, e, eps=1e-6):
 
 
 def hllc(wl, wr, eosl, eosr):
+    """Star velocity and pressure for w = (rho, u_n, p) and eos = (gamma,
+    pinf[, kind]); kind 1 marks Tait's equation with pinf = B - p0."""
     us, ps = np.zeros(1), np.zeros(1)
+    eosl = list(eosl) + [0.0] * (3 - len(eosl))
+    eosr = list(eosr) + [0.0] * (3 - len(eosr))
     arrs = [np.asarray(x, np.float64) for x in (wl, wr, eosl, eosr)]
     lib().orc_hllc(*[_dp(a) for a in arrs], _dp(us), _dp(ps))
     return float(us[0]), float(ps[0])

@@ -44,6 +44,8 @@ class Case:
     t_end: float
     inflow_prim: np.ndarray = None   # [3, 2, 5]
     inflow_mat: np.ndarray = None    # [3, 2]
+    eos_kind: list = None            # per material: 0 stiffened gas, 1 Tait
+    tait: list = None                # per material: (B, rho0, p0) of Tait's equation
 
     @property
     def nmat(self):
@@ -65,9 +67,11 @@ class Case:
         lo3 = list(self.lo) + [0.0] * (3 - self.dim)
         hi3 = list(self.hi) + [1.0] * (3 - self.dim)
         bc3 = [list(b) for b in self.bc] + [[0, 0]] * (3 - self.dim)
+        kind = list(self.eos_kind) if self.eos_kind is not None else [0] * self.nmat
+        tait = list(self.tait) if self.tait is not None else [(0.0, 0.0, 0.0)] * self.nmat
         p = dict(dim=self.dim, n=n3, lo=lo3, hi=hi3, bc=bc3, inflow_prim=np.asarray(ip, float),
                  inflow_mat=np.asarray(im, np.int32), nmat=self.nmat, gamma=list(self.gamma),
-                 pinf=list(self.pinf))
+                 pinf=list(self.pinf), eos_kind=kind, tait=tait)
         p.update(default_options(self.dim))
         p.update(opts)
         return p
@@ -161,6 +165,52 @@ def shock_bubbles(nx=2048, ny=512, mach=1.22, x_shock=0.5):
     imat = np.zeros((3, 2), np.int32)
     return Case("shock_bubbles", 2, (nx, ny), (0.0, 0.0), (3.0, 1.0), [[INFLOW, TRANSMISSIVE], [REFLECTIVE] * 2],
                 [1.4, 1.648, 1.249], [0.0, 0.0, 0.0], phi, chi.reshape(ny, nx), prim, 1.2, inflow, imat)
+
+
+# Tait's equation for water (Sec. 2.1) in the units of the air state rho = 1,
+# p = 1: B = 3.31e8 Pa / 1e5 Pa, rho0 = 1000, p0 = 1
+WATER_TAIT = (3310.0, 1000.0, 1.0)
+
+
+def shock_helium_water(nx=1024, ny=256, mach=6.0, x_shock=0.5):
+    """Mach-6 air shock on a helium bubble that then meets a water column
+    (Sec. 3.6, Table 2 states; water by Tait's equation, gamma 7.15). The
+    paper gives the geometry only in a figure: here the domain is [0,4]x[0,1]
+    (its 4 x 1 root blocks), the helium bubble (radius 0.3) at (1.0, 0.5),
+    the water column (radius 0.3) at (2.0, 0.5), the shock at x = 0.5; inflow
+    left, transmissive right, walls top and bottom."""
+    x, y = centres((nx, ny), (0.0, 0.0), (4.0, 1.0))
+    d1 = np.hypot(x - 1.0, y - 0.5) - 0.3
+    d2 = np.hypot(x - 2.0, y - 0.5) - 0.3
+    chi = np.where(d1 < 0, 1, np.where(d2 < 0, 2, 0)).astype(np.int32)
+    phi = np.minimum(np.abs(d1), np.abs(d2))
+    rho1, u1, p1, _ = normal_shock(1.4, 1.0, 1.0, mach)
+    cells = nx * ny
+    prim = np.zeros((3, 4, cells))
+    post = x.ravel() < x_shock
+    prim[0, 0] = np.where(post, rho1, 1.0)
+    prim[0, 1] = np.where(post, u1, 0.0)
+    prim[0, 3] = np.where(post, p1, 1.0)
+    prim[1] = np.array([0.138, 0.0, 0.0, 1.0])[:, None]
+    prim[2] = np.array([1000.0, 0.0, 0.0, 1.0])[:, None]
+    inflow = np.zeros((3, 2, 5))
+    inflow[0, 0, :4] = (rho1, u1, 0.0, p1)
+    return Case("shock_helium_water", 2, (nx, ny), (0.0, 0.0), (4.0, 1.0),
+                [[INFLOW, TRANSMISSIVE], [REFLECTIVE] * 2], [1.4, 1.667, 7.15], [0.0, 0.0, 0.0],
+                phi, chi.reshape(ny, nx), prim, 0.3, inflow, np.zeros((3, 2), np.int32),
+                eos_kind=[0, 0, 1], tait=[(0.0, 0.0, 0.0), (0.0, 0.0, 0.0), WATER_TAIT])
+
+
+def water_pulse(n=400, amp=1e-4):
+    """One-dimensional water at rest (Tait's equation) with a small Gaussian
+    density pulse and the matching Tait pressure: linear acoustics."""
+    (x,) = centres((n,), (0.0,), (1.0,))
+    B, rho0, p0 = WATER_TAIT
+    rho = rho0 * (1.0 + amp * np.exp(-((x - 0.5) / 0.03) ** 2))
+    p = B * (rho / rho0) ** 7.15 - B + p0
+    prim = np.stack([rho, np.zeros(n), p])[None]
+    return Case("water_pulse", 1, (n,), (0.0,), (1.0,), [[TRANSMISSIVE, TRANSMISSIVE]], [7.15], [0.0],
+                np.full(n, 10.0), np.zeros(n, np.int32), prim, 0.05, eos_kind=[1], tait=[WATER_TAIT])
 
 
 def shock_sphere(n=(256, 128, 128), mach=1.22, x_shock=0.25):

@@ -147,7 +147,9 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
           const int m = gr.inflow_mat[d][s];
           if (m < 0 || m >= n_mat) return fail(nullptr, MSF_EINVAL, "inflow material");
           const double rho = gr.inflow_prim[d][s][0], p = gr.inflow_prim[d][s][dim + 1];
-          if (!(rho > 0.0) || !(p + eos[i * n_mat + m].pinf > 0.0)) return fail(nullptr, MSF_EINVAL, "inflow state");
+          const msf_eos& em = eos[i * n_mat + m];
+          const double pinf_eff = em.kind == MSF_EOS_TAIT ? em.tait_B - em.tait_p0 : em.pinf;
+          if (!(rho > 0.0) || !(p + pinf_eff > 0.0)) return fail(nullptr, MSF_EINVAL, "inflow state");
         }
       }
     }
@@ -156,8 +158,13 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
     if (cells > (1LL << 31) - 1) return fail(nullptr, MSF_EINVAL, "grid too large");
     for (int m = 0; m < n_mat; m++) {
       const msf_eos& e = eos[i * n_mat + m];
-      if (!(e.gamma > 1.0) || !(e.pinf >= 0.0) || !std::isfinite(e.gamma) || !std::isfinite(e.pinf))
+      if (e.kind != MSF_EOS_STIFFENED && e.kind != MSF_EOS_TAIT) return fail(nullptr, MSF_EINVAL, "EOS kind");
+      if (!(e.gamma > 1.0) || !std::isfinite(e.gamma)) return fail(nullptr, MSF_EINVAL, "EOS parameters");
+      if (e.kind == MSF_EOS_STIFFENED && (!(e.pinf >= 0.0) || !std::isfinite(e.pinf)))
         return fail(nullptr, MSF_EINVAL, "EOS parameters");
+      if (e.kind == MSF_EOS_TAIT && (!(e.tait_B > 0.0) || !(e.tait_rho0 > 0.0) || !std::isfinite(e.tait_B) ||
+                                     !std::isfinite(e.tait_rho0) || !std::isfinite(e.tait_p0)))
+        return fail(nullptr, MSF_EINVAL, "Tait parameters");
     }
   }
 
@@ -231,8 +238,13 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
     g.eps_ss = ce_h * g.hmin;
     g.cap = opt->phi_cap_h * g.hmin;
     for (int m = 0; m < n_mat; m++) {
-      g.gamma[m] = eos[i * n_mat + m].gamma;
-      g.pinf[m] = eos[i * n_mat + m].pinf;
+      const msf_eos& e = eos[i * n_mat + m];
+      g.gamma[m] = e.gamma;
+      g.eos_kind[m] = e.kind;
+      g.tait_B[m] = e.kind == MSF_EOS_TAIT ? e.tait_B : 0.0;
+      g.tait_rho0[m] = e.kind == MSF_EOS_TAIT ? e.tait_rho0 : 0.0;
+      g.tait_p0[m] = e.kind == MSF_EOS_TAIT ? e.tait_p0 : 0.0;
+      g.pinf[m] = e.kind == MSF_EOS_TAIT ? e.tait_B - e.tait_p0 : e.pinf;
       g.gm1[m] = g.gamma[m] - 1.0;
       g.gpi[m] = g.gamma[m] * g.pinf[m];
     }
@@ -1025,6 +1037,9 @@ extern "C" msf_status msf_adjoint_step(msf_ctx* c, const void* tape_, const doub
   if (st != MSF_OK) return st;
   if (!tape_ || !tape_aligned(tape_)) return fail(c, MSF_EINVAL, "tape must be a 256-byte aligned device buffer");
   if (!lam_out || !lam_in) return fail(c, MSF_EINVAL, "NULL adjoint array");
+  for (int m = 0; m < c->N; m++)
+    if (c->inst[0].g.eos_kind[m] != MSF_EOS_STIFFENED)
+      return fail(c, MSF_EUNSUPPORTED, "the adjoint step takes stiffened-gas materials only");
   if ((st = ensure_adjoint(c)) != MSF_OK) return st;
   const char* tape = (const char*)tape_;
   const cudaStream_t s = c->stream;

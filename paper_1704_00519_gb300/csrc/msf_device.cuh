@@ -31,6 +31,10 @@ struct Grid {
   long long st[3], ncell;
   double lo[3], h[3], rh[3], rh2[3], ih2[3], farea[3], V, rV, hmin, eps_ss, cap;
   double gamma[MAXM], pinf[MAXM], gm1[MAXM], gpi[MAXM];
+  // Tait's equation per material (eos_kind 1): p = B (rho/rho0)^gamma - B + p0;
+  // pinf holds B - p0 (sound speed and energy of the equivalent stiffened gas)
+  int eos_kind[MAXM];
+  double tait_B[MAXM], tait_rho0[MAXM], tait_p0[MAXM];
   double cfl, weno_eps, mix_alpha;
   int ext_sweeps, vel_sweeps, reinit_iters, scale_sep, reinit;
   int rk;                       // Runge-Kutta stages (2 or 3)
@@ -98,6 +102,13 @@ __host__ __device__ inline long long aidx(const Grid& g, int d, int m, long long
 __device__ inline int popcount8(unsigned x) { return __popc(x & 0xffu); }
 
 // ---------------------------------------------------------------- EOS (Sec. 2.1)
+// Tait's equation (Sec. 2.1), evaluated in FP64: p = B (rho/rho0)^gamma - B + p0.
+// Its pressure does not depend on the internal energy; the energy carried with
+// it is that of the stiffened gas with pinf = B - p0 (prim_to_cons below).
+__device__ inline double tait_pressure(const Grid& g, int m, double rho) {
+  const double B = g.tait_B[m];
+  return B * pow(rho / g.tait_rho0[m], g.gamma[m]) - B + g.tait_p0[m];
+}
 // conservative (rho, rho u, rho E) -> primitive (rho, u, p), in T
 template <typename T>
 __device__ inline void cons_to_prim(const Grid& g, int m, int D, const T* u, T* w) {
@@ -109,7 +120,7 @@ __device__ inline void cons_to_prim(const Grid& g, int m, int D, const T* u, T* 
   T ke = T(0.5) * rho * q;
   w[0] = rho;
   for (int d = 0; d < D; d++) w[1 + d] = vel[d];
-  w[D + 1] = T(g.gm1[m]) * (u[D + 1] - ke) - T(g.gpi[m]);
+  w[D + 1] = g.eos_kind[m] == 1 ? (T)tait_pressure(g, m, (double)rho) : T(g.gm1[m]) * (u[D + 1] - ke) - T(g.gpi[m]);
 }
 template <typename T>
 __device__ inline void prim_to_cons(const Grid& g, int m, int D, const T* w, T* u) {
@@ -160,14 +171,18 @@ __device__ inline T weno5(T a, T b, T c, T d, T e, T eps) {
 
 // ---------------------------------------------------------------- HLLC (Sec. 2.3.2)
 // interface velocity and pressure of the two-state problem along n, for states
-// (rho, u_n, p) of two stiffened gases; wave speeds with Roe-averaged
-// Psi, Upsilon and p/rho
+// (rho, u_n, p) of two stiffened gases or Tait materials (tl, tr; pinf = B - p0);
+// wave speeds with Roe-averaged Psi, Upsilon and p/rho (c^2 = Psi + Upsilon p/rho:
+// stiffened gas Psi = (p + gamma pinf)/rho, Upsilon = gamma - 1; Tait
+// Psi = gamma (p + pinf)/rho, Upsilon = 0)
 template <typename T>
-__device__ inline void hllc_star(T rl, T ul, T pl, T gl, T pil, T rr, T ur, T pr, T gr, T pir, T* ustar, T* pstar) {
+__device__ inline void hllc_star(T rl, T ul, T pl, T gl, T pil, T rr, T ur, T pr, T gr, T pir, T* ustar, T* pstar,
+                                 bool tl = false, bool tr = false) {
   T c2l = (gl * (pl + pil)) / rl, c2r = (gr * (pr + pir)) / rr;
   T cl = sqrt(c2l > T(0) ? c2l : T(0)), cr = sqrt(c2r > T(0) ? c2r : T(0));
-  T psil = (pl + gl * pil) / rl, psir = (pr + gr * pir) / rr;
-  T upsl = gl - T(1), upsr = gr - T(1);
+  T psil = tl ? (gl * (pl + pil)) / rl : (pl + gl * pil) / rl;
+  T psir = tr ? (gr * (pr + pir)) / rr : (pr + gr * pir) / rr;
+  T upsl = tl ? T(0) : gl - T(1), upsr = tr ? T(0) : gr - T(1);
   T sl = sqrt(rl), sr = sqrt(rr);
   T den = sl + sr;
   T psit = (sl * psil + sr * psir) / den;

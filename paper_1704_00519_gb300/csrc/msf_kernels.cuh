@@ -653,7 +653,7 @@ __device__ __forceinline__ void phase_interface(const Grid& g, const Bufs& b, co
     }
     T us, ps;
     hllc_star<T>(wL[0], unl, wL[D + 1], (T)g.gamma[L], (T)g.pinf[L], wR[0], unr, wR[D + 1], (T)g.gamma[R],
-                 (T)g.pinf[R], &us, &ps);
+                 (T)g.pinf[R], &us, &ps, g.eos_kind[L] == 1, g.eos_kind[R] == 1);
     const double psd = (double)ps, usd = (double)us;
     double XR[5] = {0, 0, 0, 0, 0};
     for (int m = 0; m < N; m++) {
@@ -773,11 +773,26 @@ struct FluxSmem {
       sizeof(T) * ((size_t)NS * (NV + NP) + (size_t)NF * NV) + sizeof(double) * NF + (size_t)NS;
 };
 
+// Tait constants of a material (on = 0: stiffened gas)
+struct TaitK {
+  int on;
+  double B, rho0, p0, gamma;
+};
+__device__ inline TaitK tait_of(const Grid& g, int m) {
+  TaitK t;
+  t.on = g.eos_kind[m] == 1;
+  t.B = g.tait_B[m];
+  t.rho0 = g.tait_rho0[m];
+  t.p0 = g.tait_p0[m];
+  t.gamma = g.gamma[m];
+  return t;
+}
+
 // primitive velocity, pressure and sound speed of a stencil state (same
 // arithmetic as cons_to_prim and sound); isbad: rho <= 0 or c^2 <= 0
 template <int D, typename T>
-__device__ __forceinline__ void stencil_prim(const T* u, T gm1, T gpi, T gam, T pinf, T* vel, T& pres, T& cs,
-                                             bool& isbad) {
+__device__ __forceinline__ void stencil_prim(const T* u, T gm1, T gpi, T gam, T pinf, const TaitK& tk, T* vel,
+                                             T& pres, T& cs, bool& isbad) {
   const T rho = u[0];
   T qsum = T(0);
 #pragma unroll
@@ -785,7 +800,10 @@ __device__ __forceinline__ void stencil_prim(const T* u, T gm1, T gpi, T gam, T 
 #pragma unroll
   for (int e = 0; e < D; e++) qsum += vel[e] * vel[e];
   const T ke = T(0.5) * rho * qsum;
-  pres = gm1 * (u[D + 1] - ke) - gpi;
+  if (tk.on)
+    pres = (T)(tk.B * pow((double)rho / tk.rho0, tk.gamma) - tk.B + tk.p0);
+  else
+    pres = gm1 * (u[D + 1] - ke) - gpi;
   T c2 = (gam * (pres + pinf)) / rho;
   isbad = !(rho > T(0)) || !(c2 > T(0));
   if (isbad) c2 = c2 > T(0) ? c2 : T(0);
@@ -974,6 +992,7 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
   for (int m = 0; m < g.N; m++) {
     if (!((uni >> m) & 1u)) continue;
     const T mgm1 = T(g.gm1[m]), mgpi = T(g.gpi[m]), mgam = T(g.gamma[m]), mpinf = T(g.pinf[m]);
+    const TaitK mtk = tait_of(g, m);
     // stage the stencil state and its primitive quantities
 #pragma unroll 1
     for (int s = tid; s < NS; s += blockDim.x) {
@@ -1009,7 +1028,7 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
       if (!isnan(u[0])) {
         T vel[D], pres, cs;
         bool isbad;
-        stencil_prim<D, T>(u, mgm1, mgpi, mgam, mpinf, vel, pres, cs, isbad);
+        stencil_prim<D, T>(u, mgm1, mgpi, mgam, mpinf, mtk, vel, pres, cs, isbad);
 #pragma unroll
         for (int e = 0; e < D; e++) P[e * NS + s] = vel[e];
         P[D * NS + s] = pres;
@@ -1555,6 +1574,7 @@ __device__ __forceinline__ void flux1d_faces(const Grid& g, const Bufs& b, const
       if (Af_ > 0.0) {
         if ((lin && !((b.smask[cL] >> m) & 1u)) || (rin && !((b.smask[cR] >> m) & 1u))) err |= ERR_BAND;
         const T mgm1 = T(g.gm1[m]), mgpi = T(g.gpi[m]), mgam = T(g.gamma[m]), mpinf = T(g.pinf[m]);
+        const TaitK mtk = tait_of(g, m);
         T u[6][NV], un[6], pr[6], cs[6];
         bool avail = true, isbad = false;
         for (int q = 0; q < 6; q++) {
@@ -1572,7 +1592,7 @@ __device__ __forceinline__ void flux1d_faces(const Grid& g, const Bufs& b, const
           }
           T vel[1];
           bool bq;
-          stencil_prim<1, T>(u[q], mgm1, mgpi, mgam, mpinf, vel, pr[q], cs[q], bq);
+          stencil_prim<1, T>(u[q], mgm1, mgpi, mgam, mpinf, mtk, vel, pr[q], cs[q], bq);
           un[q] = vel[0];
           isbad = isbad || bq;
         }

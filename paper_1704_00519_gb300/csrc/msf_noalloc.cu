@@ -92,8 +92,8 @@ extern "C" msf_status msf_cfl_dt_noalloc(const double* U, int64_t cells, int32_t
                            "use msf_step / msf_last_dt for larger states");
     return MSF_EINVAL;
   }
-  if (!(eos->gamma > 1.0) || !(eos->pinf >= 0.0) || !(cfl > 0.0 && cfl <= 1.0)) {
-    msf_internal_set_error("msf_cfl_dt_noalloc: need gamma > 1, pinf >= 0, 0 < cfl <= 1");
+  if (eos->kind != MSF_EOS_STIFFENED || !(eos->gamma > 1.0) || !(eos->pinf >= 0.0) || !(cfl > 0.0 && cfl <= 1.0)) {
+    msf_internal_set_error("msf_cfl_dt_noalloc: need a stiffened gas with gamma > 1, pinf >= 0, 0 < cfl <= 1");
     return MSF_EINVAL;
   }
   CflArgs a;

@@ -36,7 +36,17 @@ class msf_grid(C.Structure):
 
 
 class msf_eos(C.Structure):
-    _fields_ = [("gamma", C.c_double), ("pinf", C.c_double)]
+    _fields_ = [("gamma", C.c_double), ("pinf", C.c_double), ("kind", C.c_int32), ("tait_B", C.c_double),
+                ("tait_rho0", C.c_double), ("tait_p0", C.c_double)]
+
+
+MSF_EOS_STIFFENED, MSF_EOS_TAIT = 0, 1
+
+
+def make_eos(p: dict, m: int) -> msf_eos:
+    """EOS of material m from a case parameter dictionary (cases.Case.params)."""
+    B, rho0, p0 = p["tait"][m]
+    return msf_eos(p["gamma"][m], p["pinf"][m], int(p["eos_kind"][m]), B, rho0, p0)
 
 
 class msf_options(C.Structure):
@@ -174,7 +184,7 @@ class Solver:
         self.p = case.params(**opts)
         self.N, self.NV, self.cells = case.nmat, case.nv, case.cells
         self._grid = make_grid(self.p)
-        eos = (msf_eos * self.N)(*[msf_eos(self.p["gamma"][m], self.p["pinf"][m]) for m in range(self.N)])
+        eos = (msf_eos * self.N)(*[make_eos(self.p, m) for m in range(self.N)])
         self._eos = eos
         self._opt = make_options(self.p, precision, stream, use_graph, profile)
         h = C.c_void_p()
@@ -304,6 +314,9 @@ def pad_materials(case, nmat):
         return c
     c.gamma = list(case.gamma) + [1.4] * extra
     c.pinf = list(case.pinf) + [0.0] * extra
+    if case.eos_kind is not None:
+        c.eos_kind = list(case.eos_kind) + [0] * extra
+        c.tait = list(case.tait) + [(0.0, 0.0, 0.0)] * extra
     pad = np.zeros((extra, case.nv, case.cells))
     pad[:, 0] = 1.0
     pad[:, -1] = 1.0
@@ -321,7 +334,7 @@ class Batch:
         self.n = len(cases)
         ps = [c.params(**opts) for c in self.cases]
         grids = (msf_grid * self.n)(*[make_grid(p) for p in ps])
-        eos = (msf_eos * (self.n * self.nmat))(*[msf_eos(p["gamma"][m], p["pinf"][m]) for p in ps
+        eos = (msf_eos * (self.n * self.nmat))(*[make_eos(p, m) for p in ps
                                                  for m in range(self.nmat)])
         self._keep = (grids, eos)
         self._opt = make_options(ps[0], precision, stream, 1, 0)

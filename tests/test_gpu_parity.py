@@ -226,6 +226,49 @@ def test_rk2_triple_point_fp64_and_fp32(msf):
     compare(o, s32, FP32_L1)
 
 
+def test_tait_water_pulse_fp64(msf):
+    """Tait's equation (Sec. 2.1), 1D water acoustics, full run: the GPU and
+    the oracle evaluate (rho/rho0)^gamma with two different math libraries
+    (pow may differ in the last bit), so the gate is the FP64 tolerance."""
+    case = cs.water_pulse(400)
+    o, s, eo = run_pair(msf, case, 100000)
+    assert eo == 0
+    compare(o, s, FP64_L1)
+
+
+def test_helium_water_case_fp64_fp32_and_conservation(msf):
+    """Mach-6 air shock, helium bubble and a Tait water column (Sec. 3.6
+    states) on a coarse grid: FP64 against the oracle within the FP64
+    tolerance; the FP32-bulk form within the FP32 tolerance; per-material
+    mass and summed momentum and energy through the ledger."""
+    case = cs.shock_helium_water(128, 32)
+    o, s, eo = run_pair(msf, case, 30)
+    assert eo == 0
+    compare(o, s, FP64_L1)
+    s32 = msf.Solver(case, precision=msf.MSF_FP32_BULK)
+    tot0, _ = s32.totals()
+    s32.step(30, case.t_end)
+    compare(o, s32, FP32_L1)
+    tot, led = s32.totals()
+    scale = max(np.abs(tot0).sum(), np.abs(tot).sum())
+    d = tot - tot0 - led
+    if s32.counters()["merge"] == 0:
+        assert np.abs(d[:, 0]).max() / scale < 1e-12
+    assert np.abs(d.sum(0)).max() / scale < 1e-12
+
+
+def test_adjoint_refuses_tait_materials(msf):
+    import torch
+    case = cs.water_pulse(64)
+    s = msf.Solver(case)
+    tp = s.new_tape()
+    s.step_taped(tp, case.t_end)
+    lam = torch.zeros((1, 3, 64), dtype=torch.float64, device="cuda")
+    with pytest.raises(msf.MsfError) as e:
+        s.adjoint_step(tp, lam)
+    assert e.value.status == msf.MSF_EUNSUPPORTED
+
+
 def test_host_validation_rejects_bad_levelset(msf):
     case = cs.shock_tube_3(50)
     s = msf.Solver(case)

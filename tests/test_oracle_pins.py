@@ -457,3 +457,47 @@ def test_paper_case_one_rk2_conserves_and_stays_bounded(gamma_right):
     assert np.all(rho > 0) and np.all(np.isfinite(st["Q"]))
     if gamma_right == 1.667:
         assert np.max(np.abs(rho - rho[::-1])) < 1e-10
+
+
+def test_tait_water_carries_sound_at_the_tait_speed():
+    """Tait's equation (Sec. 2.1): a small density pulse in water at rest
+    splits into two halves that move at the sound speed of the equation,
+    c^2 = dp/drho = gamma B / rho0 at rho0 (here by differencing the equation
+    itself); the right half's peak after t = 0.05 lies within two cells of
+    0.5 + c t."""
+    case = cs.water_pulse(400)
+    B, rho0, p0 = cs.WATER_TAIT
+    tait = lambda r: B * (r / rho0) ** 7.15 - B + p0
+    c = math.sqrt((tait(rho0 * (1 + 1e-7)) - tait(rho0 * (1 - 1e-7))) / (2e-7 * rho0))
+    o = orc.Oracle(case)
+    assert o.step(100000, 0.05) == 0
+    rho = o.state()["Q"][0, 0]
+    (x,) = cs.centres((400,), (0.0,), (1.0,))
+    i = 200 + int(np.argmax(rho[200:]))
+    assert abs(x[i] - (0.5 + c * 0.05)) < 2.0 / 400
+
+
+def test_tait_hllc_equal_states_and_mirror():
+    """HLLC with Tait materials (Psi = c^2, Upsilon = 0): equal states give
+    u* = u and p* = p; swapping the sides with u -> -u mirrors the result."""
+    B, rho0, p0 = cs.WATER_TAIT
+    e = (7.15, B - p0, 1)
+    w = (1000.3, 0.7, 2.5)
+    us, ps = orc.hllc(w, w, e, e)
+    assert us == pytest.approx(0.7, abs=1e-12) and ps == pytest.approx(2.5, rel=1e-12)
+    wl, wr, ea = (1000.0, 0.2, 1.0), (1.2, -0.5, 1.3), (1.4, 0.0, 0)
+    us, ps = orc.hllc(wl, wr, e, ea)
+    us2, ps2 = orc.hllc((wr[0], -wr[1], wr[2]), (wl[0], -wl[1], wl[2]), ea, e)
+    assert us2 == pytest.approx(-us, abs=1e-12) and ps2 == pytest.approx(ps, rel=1e-12)
+
+
+def test_tait_water_column_in_pressure_equilibrium_stays_at_rest():
+    """Air, helium and a Tait water column, all at rest at p = 1 (Tait's
+    pressure at rho0 is p0 = 1): the state stays at rest to round-off."""
+    case = cs.shock_helium_water(96, 24)
+    case.prim[0] = np.array([1.0, 0.0, 0.0, 1.0])[:, None]
+    case.inflow_prim[0, 0, :4] = (1.0, 0.0, 0.0, 1.0)
+    o = orc.Oracle(case, scale_sep=0, reinit=0)
+    assert o.step(40, 10.0) == 0
+    Q = o.state()["Q"]
+    assert np.abs(Q[:, 1:3]).max() < 1e-11
