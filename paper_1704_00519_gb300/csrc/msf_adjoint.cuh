@@ -94,45 +94,47 @@ template <int K>
 __device__ inline Dual<K> fmax(const Dual<K>& a, const Dual<K>& b) { return b.v > a.v ? b : a; }
 
 // ---------------------------------------------------- local derivatives
-// gradient of the WENO5-JS value (weno5) with respect to its five arguments
-__device__ inline double weno5_grad(double a, double b, double c, double d, double e, double eps, double* gr) {
-  const double q0 = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
-  const double q1 = (-b + 5.0 * c + 2.0 * d) / 6.0;
-  const double q2 = (2.0 * c + 5.0 * d - e) / 6.0;
-  const double t00 = a - 2.0 * b + c, t01 = a - 4.0 * b + 3.0 * c;
-  const double t10 = b - 2.0 * c + d, t11 = b - d;
-  const double t20 = c - 2.0 * d + e, t21 = 3.0 * c - 4.0 * d + e;
-  const double s0 = 13.0 / 12.0 * t00 * t00 + 0.25 * t01 * t01;
-  const double s1 = 13.0 / 12.0 * t10 * t10 + 0.25 * t11 * t11;
-  const double s2 = 13.0 / 12.0 * t20 * t20 + 0.25 * t21 * t21;
-  const double b0 = eps + s0, b1 = eps + s1, b2 = eps + s2;
-  const double a0 = 0.1 / (b0 * b0), a1 = 0.6 / (b1 * b1), a2 = 0.3 / (b2 * b2);
-  const double A = a0 + a1 + a2;
-  const double w0 = a0 / A, w1 = a1 / A, w2 = a2 / A;
-  const double out = w0 * q0 + w1 * q1 + w2 * q2;
+// gradient of the WENO5-JS value (weno5) with respect to its five arguments,
+// in the arithmetic type A
+template <typename A>
+__device__ inline A weno5_grad(A a, A b, A c, A d, A e, A eps, A* gr) {
+  const A r6 = A(1.0 / 6.0), k13 = A(13.0 / 12.0), k136 = A(13.0 / 6.0);
+  const A q0 = (A(2) * a - A(7) * b + A(11) * c) * r6;
+  const A q1 = (-b + A(5) * c + A(2) * d) * r6;
+  const A q2 = (A(2) * c + A(5) * d - e) * r6;
+  const A t00 = a - A(2) * b + c, t01 = a - A(4) * b + A(3) * c;
+  const A t10 = b - A(2) * c + d, t11 = b - d;
+  const A t20 = c - A(2) * d + e, t21 = A(3) * c - A(4) * d + e;
+  const A s0 = k13 * t00 * t00 + A(0.25) * t01 * t01;
+  const A s1 = k13 * t10 * t10 + A(0.25) * t11 * t11;
+  const A s2 = k13 * t20 * t20 + A(0.25) * t21 * t21;
+  const A b0 = eps + s0, b1 = eps + s1, b2 = eps + s2;
+  const A a0 = A(0.1) / (b0 * b0), a1 = A(0.6) / (b1 * b1), a2 = A(0.3) / (b2 * b2);
+  const A rA = A(1) / (a0 + a1 + a2);
+  const A w0 = a0 * rA, w1 = a1 * rA, w2 = a2 * rA;
+  const A out = w0 * q0 + w1 * q1 + w2 * q2;
   // d out / d s_k = (q_k - out) / A * d a_k / d s_k, d a_k / d s_k = -2 a_k / b_k
-  const double c0 = (q0 - out) / A * (-2.0 * a0 / b0);
-  const double c1 = (q1 - out) / A * (-2.0 * a1 / b1);
-  const double c2 = (q2 - out) / A * (-2.0 * a2 / b2);
-  const double r6 = 1.0 / 6.0;
+  const A c0 = (q0 - out) * rA * (A(-2) * a0 / b0);
+  const A c1 = (q1 - out) * rA * (A(-2) * a1 / b1);
+  const A c2 = (q2 - out) * rA * (A(-2) * a2 / b2);
   // linear parts
-  gr[0] = w0 * 2.0 * r6;
-  gr[1] = w0 * -7.0 * r6 + w1 * -1.0 * r6;
-  gr[2] = w0 * 11.0 * r6 + w1 * 5.0 * r6 + w2 * 2.0 * r6;
-  gr[3] = w1 * 2.0 * r6 + w2 * 5.0 * r6;
-  gr[4] = w2 * -1.0 * r6;
+  gr[0] = w0 * A(2) * r6;
+  gr[1] = w0 * A(-7) * r6 + w1 * A(-1) * r6;
+  gr[2] = w0 * A(11) * r6 + w1 * A(5) * r6 + w2 * A(2) * r6;
+  gr[3] = w1 * A(2) * r6 + w2 * A(5) * r6;
+  gr[4] = w2 * A(-1) * r6;
   // smoothness indicators
-  const double u00 = c0 * 13.0 / 6.0 * t00, u01 = c0 * 0.5 * t01;
+  const A u00 = c0 * k136 * t00, u01 = c0 * A(0.5) * t01;
   gr[0] += u00 + u01;
-  gr[1] += -2.0 * u00 - 4.0 * u01;
-  gr[2] += u00 + 3.0 * u01;
-  const double u10 = c1 * 13.0 / 6.0 * t10, u11 = c1 * 0.5 * t11;
+  gr[1] += A(-2) * u00 - A(4) * u01;
+  gr[2] += u00 + A(3) * u01;
+  const A u10 = c1 * k136 * t10, u11 = c1 * A(0.5) * t11;
   gr[1] += u10 + u11;
-  gr[2] += -2.0 * u10;
+  gr[2] += A(-2) * u10;
   gr[3] += u10 - u11;
-  const double u20 = c2 * 13.0 / 6.0 * t20, u21 = c2 * 0.5 * t21;
-  gr[2] += u20 + 3.0 * u21;
-  gr[3] += -2.0 * u20 - 4.0 * u21;
+  const A u20 = c2 * k136 * t20, u21 = c2 * A(0.5) * t21;
+  gr[2] += u20 + A(3) * u21;
+  gr[3] += A(-2) * u20 - A(4) * u21;
   gr[4] += u20 + u21;
   return out;
 }
@@ -203,7 +205,9 @@ __device__ inline bool updated(const Grid& g, const Bufs& b, long long c, int m)
 // +A rh and of its lower cell with -A rh; g = A rh (mu_R - mu_L) is pulled
 // back through WENO5 of the Lax-Friedrichs split fluxes to the six stencil
 // states and the EOS of the material (the same stencil states as the forward
-// flux: interior cells from interior_uhat, halo cells from Uh)
+// flux: interior cells from interior_uhat, halo cells from Uh). The
+// arithmetic is the stencil states' type T (the forward flux's), the
+// accumulation FP64.
 template <int D, typename T, int DIR>
 __global__ void __launch_bounds__(NTHREADS) k_adj_flux(const __grid_constant__ Grid g, const __grid_constant__ Bufs b,
                                                        const __grid_constant__ AdjBufs a, const double* Qs,
@@ -215,7 +219,7 @@ __global__ void __launch_bounds__(NTHREADS) k_adj_flux(const __grid_constant__ G
   for (int e = 0; e < D; e++)
     if (e != DIR) nf *= g.n[e];
   const long long total = nf * g.N;
-  const double eps = g.weno_eps;
+  const T eps = (T)g.weno_eps;
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
        it += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(it / nf);
@@ -229,90 +233,86 @@ __global__ void __launch_bounds__(NTHREADS) k_adj_flux(const __grid_constant__ G
     const long long cR = cell_at(g, q[0], q[1], q[2]), cL = cR - g.st[DIR];
     const double Af = face_aperture(g, b, cL, cR, DIR, m);
     if (!(Af > 0.0)) continue;
-    double gF[NV];
+    T gF[NV];
     const bool uL = updated(g, b, cL, m), uR = updated(g, b, cR, m);
     bool any = false;
     for (int v = 0; v < NV; v++) {
       const double muL = uL ? omb_dt * a.LA[qidx(g, m, v, cL)] : 0.0;
       const double muR = uR ? omb_dt * a.LA[qidx(g, m, v, cR)] : 0.0;
-      gF[v] = Af * g.rh[DIR] * (muR - muL);
-      any = any || gF[v] != 0.0;
+      gF[v] = (T)(Af * g.rh[DIR] * (muR - muL));
+      any = any || gF[v] != T(0);
     }
     if (!any) continue;
     // stencil states
-    double U[6][NV], un[6], pr[6], cs[6], vel[6][D];
+    T U[6][NV], un[6], pr[6], cs[6], vel[6][D];
     long long cq[6];
     bool ok = true;
-    const double gm1 = g.gm1[m], gpi = g.gpi[m], gam = g.gamma[m], pinf = g.pinf[m];
+    const T gm1 = (T)g.gm1[m], gpi = (T)g.gpi[m], gam = (T)g.gamma[m], pinf = (T)g.pinf[m];
     for (int k = 0; k < 6 && ok; k++) {
       const long long cc = cL + (long long)(k - 2) * g.st[DIR];
       cq[k] = cc;
-      T u[NV];
       if (interior_c(g, cc)) {
-        interior_uhat<T>(g, b, Qs, cc, m, u);
+        interior_uhat<T>(g, b, Qs, cc, m, U[k]);
       } else {
         const T* Uh = (const T*)b.Uh;
-        for (int v = 0; v < NV; v++) u[v] = Uh[qidx(g, m, v, cc)];
+        for (int v = 0; v < NV; v++) U[k][v] = Uh[qidx(g, m, v, cc)];
       }
-      for (int v = 0; v < NV; v++) U[k][v] = (double)u[v];
       if (isnan(U[k][0])) ok = false;
     }
     if (!ok) continue;
     for (int k = 0; k < 6; k++) {
-      const double rho = U[k][0];
-      double qs = 0.0;
+      const T rho = U[k][0];
+      T qs = T(0);
       for (int e = 0; e < D; e++) {
         vel[k][e] = U[k][1 + e] / rho;
         qs += vel[k][e] * vel[k][e];
       }
-      pr[k] = gm1 * (U[k][D + 1] - 0.5 * rho * qs) - gpi;
-      double c2 = gam * (pr[k] + pinf) / rho;
-      cs[k] = c2 > 0.0 ? ::sqrt(c2) : 0.0;
+      pr[k] = gm1 * (U[k][D + 1] - T(0.5) * rho * qs) - gpi;
+      const T c2 = gam * (pr[k] + pinf) / rho;
+      cs[k] = c2 > T(0) ? ::sqrt(c2) : T(0);
       un[k] = vel[k][DIR];
     }
-    double al = 0.0;
+    T al = T(0);
     int kst = -1;
     for (int k = 0; k < 6; k++) {
-      const double sp = fabs(un[k]) + cs[k];
+      const T sp = fabs(un[k]) + cs[k];
       if (sp > al) {
         al = sp;
         kst = k;
       }
     }
-    double gU[6][NV], gun[6], gpr[6], gcs[6];
+    T gU[6][NV], gun[6], gpr[6], gcs[6];
     for (int k = 0; k < 6; k++) {
-      gun[k] = gpr[k] = gcs[k] = 0.0;
-      for (int v = 0; v < NV; v++) gU[k][v] = 0.0;
+      gun[k] = gpr[k] = gcs[k] = T(0);
+      for (int v = 0; v < NV; v++) gU[k][v] = T(0);
     }
-    double gal = 0.0;
+    T gal = T(0);
     for (int v = 0; v < NV; v++) {
-      if (gF[v] == 0.0) continue;
-      double Fv[6], fp[6], fm[6];
+      if (gF[v] == T(0)) continue;
+      T fp[6], fm[6];
       for (int k = 0; k < 6; k++) {
-        const double uu = U[k][v];
-        double F;
+        const T uu = U[k][v];
+        T F;
         if (v == 0) F = U[k][1 + DIR];
         else if (v == NV - 1) F = un[k] * (uu + pr[k]);
         else F = (v - 1 == DIR) ? uu * un[k] + pr[k] : uu * un[k];
-        Fv[k] = F;
-        fp[k] = 0.5 * (F + al * uu);
-        fm[k] = 0.5 * (F - al * uu);
+        fp[k] = T(0.5) * (F + al * uu);
+        fm[k] = T(0.5) * (F - al * uu);
       }
-      double gp5[5], gm5[5];
-      weno5_grad(fp[0], fp[1], fp[2], fp[3], fp[4], eps, gp5);
-      weno5_grad(fm[5], fm[4], fm[3], fm[2], fm[1], eps, gm5);
-      double gfp[6] = {0, 0, 0, 0, 0, 0}, gfm[6] = {0, 0, 0, 0, 0, 0};
+      T gp5[5], gm5[5];
+      weno5_grad<T>(fp[0], fp[1], fp[2], fp[3], fp[4], eps, gp5);
+      weno5_grad<T>(fm[5], fm[4], fm[3], fm[2], fm[1], eps, gm5);
+      T gfp[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, gfm[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
       for (int k = 0; k < 5; k++) {
         gfp[k] = gF[v] * gp5[k];
         gfm[5 - k] = gF[v] * gm5[k];
       }
       for (int k = 0; k < 6; k++) {
-        const double gFk = 0.5 * (gfp[k] + gfm[k]);
-        const double dpm = gfp[k] - gfm[k];
-        gU[k][v] += 0.5 * al * dpm;
-        gal += 0.5 * U[k][v] * dpm;
-        if (gFk == 0.0) continue;
-        (void)Fv;
+        const T gFk = T(0.5) * (gfp[k] + gfm[k]);
+        const T dpm = gfp[k] - gfm[k];
+        gU[k][v] += T(0.5) * al * dpm;
+        gal += T(0.5) * U[k][v] * dpm;
+        if (gFk == T(0)) continue;
         if (v == 0) {
           gU[k][1 + DIR] += gFk;
         } else if (v == NV - 1) {
@@ -327,42 +327,42 @@ __global__ void __launch_bounds__(NTHREADS) k_adj_flux(const __grid_constant__ G
       }
     }
     if (kst >= 0) {
-      gun[kst] += gal * (un[kst] > 0.0 ? 1.0 : (un[kst] < 0.0 ? -1.0 : 0.0));
+      gun[kst] += gal * (un[kst] > T(0) ? T(1) : (un[kst] < T(0) ? T(-1) : T(0)));
       gcs[kst] += gal;
     }
-    double ge0 = 0.0, ge1 = 0.0;
+    T ge0 = T(0), ge1 = T(0);
     for (int k = 0; k < 6; k++) {
-      const double rho = U[k][0];
-      double gp = gpr[k], grho = 0.0;
-      double gvel[3] = {0, 0, 0};
+      const T rho = U[k][0];
+      T gp = gpr[k], grho = T(0);
+      T gvel[3] = {T(0), T(0), T(0)};
       gvel[DIR] += gun[k];
-      if (gcs[k] != 0.0 && cs[k] > 0.0) {
-        const double c2 = cs[k] * cs[k];
-        const double gc2 = gcs[k] * 0.5 / cs[k];
+      if (gcs[k] != T(0) && cs[k] > T(0)) {
+        const T c2 = cs[k] * cs[k];
+        const T gc2 = gcs[k] * T(0.5) / cs[k];
         gp += gc2 * gam / rho;
         grho -= gc2 * c2 / rho;
         ge0 += gc2 * (pr[k] + pinf) / rho;
         ge1 += gc2 * gam / rho;
       }
-      double qs = 0.0;
+      T qs = T(0);
       for (int e = 0; e < D; e++) qs += vel[k][e] * vel[k][e];
-      const double ke = 0.5 * rho * qs;
+      const T ke = T(0.5) * rho * qs;
       gU[k][D + 1] += gp * gm1;
-      const double gke = -gp * gm1;
+      const T gke = -gp * gm1;
       ge0 += gp * (U[k][D + 1] - ke - pinf);
       ge1 += -gp * gam;
-      grho += gke * 0.5 * qs;
+      grho += gke * T(0.5) * qs;
       for (int e = 0; e < D; e++) {
-        const double gv = gvel[e] + gke * rho * vel[k][e];
+        const T gv = gvel[e] + gke * rho * vel[k][e];
         gU[k][1 + e] += gv / rho;
         grho -= gv * vel[k][e] / rho;
       }
       gU[k][0] += grho;
       for (int v = 0; v < NV; v++)
-        if (gU[k][v] != 0.0) atomicAdd(&a.LU[qidx(g, m, v, cq[k])], gU[k][v]);
+        if (gU[k][v] != T(0)) atomicAdd(&a.LU[qidx(g, m, v, cq[k])], (double)gU[k][v]);
     }
-    if (ge0 != 0.0) atomicAdd(&s_de[2 * m], ge0);
-    if (ge1 != 0.0) atomicAdd(&s_de[2 * m + 1], ge1);
+    if (ge0 != T(0)) atomicAdd(&s_de[2 * m], (double)ge0);
+    if (ge1 != T(0)) atomicAdd(&s_de[2 * m + 1], (double)ge1);
   }
   eos_block_flush(s_de, a.deos, g.N);
 }

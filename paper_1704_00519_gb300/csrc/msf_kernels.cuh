@@ -773,6 +773,11 @@ struct FluxSmem {
       sizeof(T) * ((size_t)NS * (NV + NP) + (size_t)NF * NV) + sizeof(double) * NF + (size_t)NS;
 };
 
+// Tait's pressure of a stencil state, out of line: the stiffened-gas path of
+// the staging loop keeps its registers
+__device__ __noinline__ double tait_pressure_k(double rho, double B, double rho0, double p0, double gamma) {
+  return B * pow(rho / rho0, gamma) - B + p0;
+}
 // Tait constants of a material (on = 0: stiffened gas)
 struct TaitK {
   int on;
@@ -801,7 +806,7 @@ __device__ __forceinline__ void stencil_prim(const T* u, T gm1, T gpi, T gam, T 
   for (int e = 0; e < D; e++) qsum += vel[e] * vel[e];
   const T ke = T(0.5) * rho * qsum;
   if (tk.on)
-    pres = (T)(tk.B * pow((double)rho / tk.rho0, tk.gamma) - tk.B + tk.p0);
+    pres = (T)tait_pressure_k((double)rho, tk.B, tk.rho0, tk.p0, tk.gamma);
   else
     pres = gm1 * (u[D + 1] - ke) - gpi;
   T c2 = (gam * (pres + pinf)) / rho;
