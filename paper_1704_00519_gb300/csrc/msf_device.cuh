@@ -51,6 +51,7 @@ struct Ctl {
   int active, last;
   unsigned err;
   int nband, nbnd;
+  unsigned tile_ctr;  // next flux tile of the running flux-update launch
   unsigned long long cnt[NCOUNT];
   double ledger[MAXM][5];
 };

@@ -368,30 +368,28 @@ __device__ __forceinline__ void extend_items(const Grid& g, const Bufs& b, const
   for (int it = first; it < total; it += stride) {
     const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
-    const uint8_t smc = b.smask[c], realc = b.isreal[midx(g, m, c)], finc = fin[midx(g, m, c)];
+    if (!((b.smask[c] >> m) & 1u)) continue;
+    if (b.isreal[midx(g, m, c)]) {
+      fout[midx(g, m, c)] = 1;
+      continue;
+    }
+    const uint8_t finc = fin[midx(g, m, c)];
     int q[3];
     coords(g, c, q);
     double n[3];
     stored_normal(g, b, c, m, n);
-    long long jn[6];
     bool use[6];
     T x[6][5];
     for (int d = 0; d < D; d++)
       for (int s = 0; s < 2; s++) {
         const int i = 2 * d + s;
         const long long j = s ? c + g.st[d] : c - g.st[d];
-        jn[i] = j;
         const int bij = b.bandidx[j];
         const unsigned smj = b.smask[j];
         const uint8_t fj = fin[midx(g, m, j)];
         use[i] = nb_interior(g, q, d, s) & (bij >= 0) & (((smj >> m) & 1u) != 0) & (fj != 0);
         for (int v = 0; v < NV; v++) x[i][v] = Wi[qidx(g, m, v, j)];
       }
-    if (!((smc >> m) & 1u)) continue;
-    if (realc) {
-      fout[midx(g, m, c)] = 1;
-      continue;
-    }
     T acc[5] = {T(0), T(0), T(0), T(0), T(0)}, acc2[5] = {T(0), T(0), T(0), T(0), T(0)};
     T sw = T(0);
     int cnt = 0;
@@ -408,7 +406,6 @@ __device__ __forceinline__ void extend_items(const Grid& g, const Bufs& b, const
         sw += w;
         cnt++;
       }
-    (void)jn;
     if (sw > T(0)) {
       for (int v = 0; v < NV; v++) Wo[qidx(g, m, v, c)] = acc[v] / sw;
       fout[midx(g, m, c)] = 1;
@@ -688,9 +685,14 @@ __device__ __forceinline__ void extend_vel_items(const Grid& g, const Bufs& b, c
     const long long c = b.band[k];
     // every value the sweep may use, loaded up front (one round of latency)
     const uint8_t gf = b.gflag[c], finc = fin[c];
-    const double phc = b.phi[c];
     double vc[3];
     for (int e = 0; e < 3; e++) vc[e] = vin[e * g.ncell + c];
+    if (gf & GF_CUT) {
+      for (int e = 0; e < 3; e++) vout[e * g.ncell + c] = vc[e];
+      fout[c] = 1;
+      continue;
+    }
+    const double phc = b.phi[c];
     int q[3];
     coords(g, c, q);
     bool use[6];
@@ -705,11 +707,6 @@ __device__ __forceinline__ void extend_vel_items(const Grid& g, const Bufs& b, c
         phj[i] = b.phi[j];
         for (int e = 0; e < D; e++) vj[i][e] = vin[e * g.ncell + j];
       }
-    if (gf & GF_CUT) {
-      for (int e = 0; e < 3; e++) vout[e * g.ncell + c] = vc[e];
-      fout[c] = 1;
-      continue;
-    }
     double acc[3] = {0, 0, 0}, acc2[3] = {0, 0, 0};
     int cnt = 0, cnt2 = 0;
     for (int d = 0; d < D; d++)
@@ -936,13 +933,12 @@ __device__ inline void flux_face(const Grid& g, const Bufs& b, const T* U, const
   for (int v = 0; v < NV; v++) F[v * S::NF + f] = Fh[v];
 }
 
+// one tile of the flux update (tile index over the (x, y, z) tile grid)
 template <int D, typename T>
-__global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
-    k_flux_update(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs,
-                  const double* Qn, double* Qout, double beta, double omb, const __grid_constant__ BndBase bb) {
+__device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const double* Qs, const double* Qn,
+                                          double* Qout, double beta, double omb, const BndBase& bb, int tile) {
   using S = FluxSmem<D, T>;
   constexpr int NV = D + 2, TX = S::TX, TY = S::TY, TZ = S::TZ, SX = S::SX, SY = S::SY, NS = S::NS;
-  if (!ctl_active(b)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* A = (double*)smem_raw;       // [NF] apertures (8-byte aligned first)
   T* U = (T*)(A + S::NF);              // [NV][NS]
@@ -954,7 +950,7 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
 
   const int tid = threadIdx.x;
   const int nbx = (g.n[0] + TX - 1) / TX, nby = D >= 2 ? (g.n[1] + TY - 1) / TY : 1;
-  const int bx = blockIdx.x % nbx, by = (blockIdx.x / nbx) % nby, bz = blockIdx.x / (nbx * nby);
+  const int bx = tile % nbx, by = (tile / nbx) % nby, bz = tile / (nbx * nby);
   const int x0 = g.off[0] + bx * TX, y0 = (D >= 2 ? g.off[1] : 0) + by * TY, z0 = (D >= 3 ? g.off[2] : 0) + bz * TZ;
   const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
   const int cx = x0 + tx, cy = y0 + ty, cz = z0 + tz;
@@ -1087,6 +1083,28 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
   if (err) atomicOr(&s_err, err);
   __syncthreads();
   if (tid == 0 && s_err) atomicOr(&b.ctl->err, s_err);
+}
+
+// Persistent CTAs (as many as fit on the GPU at once) take tiles from a
+// counter in the control block, so that the tiles holding band cells (two or
+// three materials: two to three times the work) spread over every SM instead
+// of leaving a partial last wave; each tile's arithmetic does not depend on
+// which CTA runs it.
+template <int D, typename T>
+__global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
+    k_flux_update(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs,
+                  const double* Qn, double* Qout, double beta, double omb, const __grid_constant__ BndBase bb,
+                  int ntiles) {
+  if (!ctl_active(b)) return;
+  __shared__ int s_tile;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.ctl->tile_ctr, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    __syncthreads();
+    if (tile >= ntiles) break;
+    flux_tile<D, T>(g, b, Qs, Qn, Qout, beta, omb, bb, tile);
+  }
 }
 
 // sum the boundary-face fluxes of the stage (one block per material and
