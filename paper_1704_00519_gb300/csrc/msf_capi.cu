@@ -409,6 +409,9 @@ extern "C" msf_status msf_destroy(msf_ctx* c) {
 static bool tiled_ext(const msf_ctx* c, const Grid& g) {
   return c->tops && g.D == 2 && g.ext_sweeps >= 1 && g.ext_sweeps <= TILED_MAX_SWEEPS;
 }
+static bool tiled_vel(const msf_ctx* c, const Grid& g) {
+  return c->tops && g.D == 2 && g.vel_sweeps >= 1 && g.vel_sweeps <= TILED_MAX_SWEEPS;
+}
 
 // kernels one step enqueues (keep in step with enqueue_step)
 static long long count_launches(const msf_ctx* c) {
@@ -416,7 +419,7 @@ static long long count_launches(const msf_ctx* c) {
   for (const Inst& in : c->inst) {
     const Grid& g = in.g;
     const long long ext = tiled_ext(c, g) ? 1 : g.ext_sweeps;
-    const long long vel = g.vel_sweeps, re = 2LL * g.reinit_iters;
+    const long long vel = tiled_vel(c, g) ? 1 : g.vel_sweeps, re = 2LL * g.reinit_iters;
     const long long per_stage = 1 + ext + 1 + 1 + 1 + vel + 1 + 1 + 1 + 1 + 1 + 2 + 3;
     n += 1 + 1 + (2 + g.D) + 2 + 1 + g.rk * per_stage + 2 + 1;
     if (g.scale_sep) n += 2 + 1;
@@ -504,9 +507,15 @@ static msf_status enqueue_step(msf_ctx* c, char* tape = nullptr) {
       double* V[2] = {b.vel0, b.vel1};
       uint8_t* VF[2] = {b.vf0, b.vf1};
       int vc = 0;
-      for (int k = 0; k < g.vel_sweeps; k++) {
-        launch_extend_vel(g, b, V[vc], V[vc ^ 1], VF[vc], VF[vc ^ 1], nb, s);
-        vc ^= 1;
+      if (tiled_vel(c, g)) {
+        cudaError_t te = c->tops->extend_vel(g, b, V[0], V[1], VF[0], VF[1], g.vel_sweeps, s);
+        if (te != cudaSuccess) return fail(c, MSF_ECUDA, std::string("tiled velocity: ") + cudaGetErrorString(te));
+        vc = 1;
+      } else {
+        for (int k = 0; k < g.vel_sweeps; k++) {
+          launch_extend_vel(g, b, V[vc], V[vc ^ 1], VF[vc], VF[vc ^ 1], nb, s);
+          vc ^= 1;
+        }
       }
       const bool prof = c->ev[0] && &in == &c->inst[0];
       if (prof) cudaEventRecord(c->ev[2 * st], s);
