@@ -329,6 +329,7 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
       b.mixn = (uint8_t*)carve(nbmax * N);
       b.mixoff = (uint8_t*)carve(nbmax * N * MIX_MAXT);
       b.mixbeta = (double*)carve(8 * nbmax * N * MIX_MAXT);
+      b.mixin = (unsigned*)carve(4 * nbmax * N);
       b.phir = (double*)carve(8 * nbmax * N);
       b.bflux = (double*)carve(8 * std::max<long long>(1, in.nbnd) * N * NV);
       b.ctl = (Ctl*)carve(sizeof(Ctl));

@@ -1319,6 +1319,9 @@ __device__ __forceinline__ void phase_mix_mark(const Grid& g, const Bufs& b, con
     for (int t = 0; t < nt; t++) {
       b.mixoff[r * MIX_MAXT + t] = toff[t];
       b.mixbeta[r * MIX_MAXT + t] = tw[t] / sw;
+      // tell the target which neighbour (by this offset code) mixes into it
+      const long long tc = off_cell(g, c, toff[t]);
+      atomicOr(&b.mixin[(long long)b.bandidx[tc] * N + m], 1u << toff[t]);
     }
     b.mixn[r] = (uint8_t)nt;
   }
@@ -1359,11 +1362,15 @@ __device__ __forceinline__ void phase_mix_compute(const Grid& g, const Bufs& b, 
           acc[v] += beta * (as * Qc[qidx(g, m, v, tc)] - at * Qc[qidx(g, m, v, c)]) / (as + at);
       }
     }
+    // neighbours that mix into this cell (bits set by the marking pass)
+    const unsigned inbits = b.mixin[r];
     const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
-    for (int dz = -rz; dz <= rz; dz++)
+    for (int dz = -rz; dz <= rz && inbits; dz++)
       for (int dy = -ry; dy <= ry; dy++)
         for (int dx = -1; dx <= 1; dx++) {
           if (dx == 0 && dy == 0 && dz == 0) continue;
+          const uint8_t code = off_code(dx, dy, dz);
+          if (!((inbits >> code) & 1u)) continue;
           const int sx = q[0] - dx, sy = q[1] - dy, sz = q[2] - dz;
           if (!in_array(g, sx, sy, sz)) continue;
           const long long s = cell_at(g, sx, sy, sz);
@@ -1372,7 +1379,6 @@ __device__ __forceinline__ void phase_mix_compute(const Grid& g, const Bufs& b, 
           const long long rs = (long long)ks * N + m;
           const int ns = b.mixn[rs];
           if (ns == 0xff) continue;
-          const uint8_t code = off_code(dx, dy, dz);
           for (int t = 0; t < ns; t++) {
             if (b.mixoff[rs * MIX_MAXT + t] != code) continue;
             const double beta = b.mixbeta[rs * MIX_MAXT + t];
@@ -1410,8 +1416,10 @@ __device__ __forceinline__ void phase_mix_scatter(const Grid& g, const Bufs& b, 
       }
       b.mixmerge[k] = 0;
     }
-    for (int m = 0; m < N; m++)
+    for (int m = 0; m < N; m++) {
       for (int v = 0; v < NV; v++) Qc[qidx(g, m, v, c)] = in[m * NV + v];
+      b.mixin[(long long)k * N + m] = 0u;  // ready for the next marking pass
+    }
   }
   if (nmerge) atomicAdd(&b.ctl->cnt[C_MERGE], nmerge);
 }
