@@ -283,6 +283,30 @@ def adjoint_rates(msf, torch, stream, K):
             "how": "msf_adjoint_step per step (recomputes the stages from the tape); events on the context stream"}
 
 
+def later_window(msf, torch, stream, flush, K, t_start=0.6):
+    """Triple point advanced to t = t_start (waves fill most of the domain, so
+    few tiles are idle), then K device-timed steps per precision."""
+    case = make_case()
+    out = {"t_start": t_start, "steps": K}
+    for key, prec in (("fp32", msf.MSF_FP32_BULK), ("fp64", msf.MSF_FP64)):
+        s = msf.Solver(case, precision=prec, stream=stream)
+        s.step(100000, t_start)
+        ms = []
+        for k in range(K):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.step(1, case.t_end, sync=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = sum(ms) / K
+        out[key] = {"value": case.cells * 3 / (t / 1e3), "unit": UNIT, "ms_per_step": t}
+        s.close()
+    out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def pairs_per_cell(s):
     """(cell, material) pairs the flux update processes: popcount of the step mask."""
     vals, counts = np.unique(s.debug(5).astype(np.int64), return_counts=True)
@@ -395,6 +419,7 @@ def run_gpu(args):
     s64.close()
     se.close()
     workloads = workload_rates(msf, torch, sptr, 10)
+    later = later_window(msf, torch, sptr, flush, 10)
     adjoint = adjoint_rates(msf, torch, sptr, 4)
     adjoint["vs_fp64_forward"] = adjoint["value"] / workloads["shock_sphere_256x128x128"]["fp64"]["value"]
     if rank != 0:
@@ -429,6 +454,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "batched_1d": batched,
+        "triple_point_from_t_0.6": later,
         "workloads": workloads,
         "adjoint": adjoint,
     }
