@@ -283,14 +283,20 @@ def adjoint_rates(msf, torch, stream, K):
             "how": "msf_adjoint_step per step (recomputes the stages from the tape); events on the context stream"}
 
 
-def later_window(msf, torch, stream, flush, K, t_start=0.6):
-    """Triple point advanced to t = t_start (waves fill most of the domain, so
-    few tiles are idle), then K device-timed steps per precision."""
+def later_window(msf, torch, stream, flush, K, t_start=0.3):
+    """Triple point advanced to t = t_start (the waves have spread over much of
+    the domain, so fewer tiles are idle), then K device-timed steps per
+    precision. A device-detected error is reported, not raised."""
     case = make_case()
     out = {"t_start": t_start, "steps": K}
     for key, prec in (("fp32", msf.MSF_FP32_BULK), ("fp64", msf.MSF_FP64)):
         s = msf.Solver(case, precision=prec, stream=stream)
-        s.step(100000, t_start)
+        try:
+            s.step(100000, t_start)
+        except msf.MsfError as e:
+            out[key] = {"error": str(e)[:120]}
+            s.close()
+            continue
         ms = []
         for k in range(K):
             flush.fill_(float(k))
@@ -303,7 +309,8 @@ def later_window(msf, torch, stream, flush, K, t_start=0.6):
         t = sum(ms) / K
         out[key] = {"value": case.cells * 3 / (t / 1e3), "unit": UNIT, "ms_per_step": t}
         s.close()
-    out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    if "value" in out["fp32"] and "value" in out["fp64"]:
+        out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
     return out
 
 
@@ -454,7 +461,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "batched_1d": batched,
-        "triple_point_from_t_0.6": later,
+        "triple_point_from_t_0.3": later,
         "workloads": workloads,
         "adjoint": adjoint,
     }

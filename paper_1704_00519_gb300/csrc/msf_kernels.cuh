@@ -939,6 +939,26 @@ __device__ inline bool same_bits(double a, double b) {
   return __double_as_longlong(a) == __double_as_longlong(b) && a == a;
 }
 
+// does this thread's share of the staged stencil states (those the faces
+// read) equal, bit for bit, the state of the tile's first cell; out of line
+// so that the flux path keeps its registers
+template <int D, typename T>
+__device__ __noinline__ bool stencil_uniform(const T* U, const uint8_t* bad, int tid) {
+  using S = FluxSmem<D, T>;
+  constexpr int NV = D + 2, TX = S::TX, TY = S::TY, TZ = S::TZ, SX = S::SX, SY = S::SY, NS = S::NS;
+  const int sref = 3 + SX * (S::HY + SY * S::HZ);
+  bool same = !bad[sref];
+  for (int s = tid; s < NS && same; s += TX * TY * TZ) {
+    const int sx = s % SX, sy = (s / SX) % SY, sz = s / (SX * SY);
+    int outs = (sx < 3 || sx >= 3 + TX);
+    if (D >= 2) outs += (sy < S::HY || sy >= S::HY + TY);
+    if (D >= 3) outs += (sz < S::HZ || sz >= S::HZ + TZ);
+    if (outs > 1) continue;
+    for (int v = 0; v < NV; v++) same = same && same_bits(U[v * NS + s], U[v * NS + sref]);
+  }
+  return same;
+}
+
 // one tile of the flux update (tile index over the (x, y, z) tile grid)
 template <int D, typename T>
 __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const double* Qs, const double* Qn,
@@ -1054,29 +1074,17 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
     // exactly +0 and L = 0; the face evaluation is skipped and the update
     // below runs with L = 0, giving the same bits as the full evaluation.
     bool idle = false;
-    if (!anyband && interior_tile) {
-      const int sref = 3 + SX * (S::HY + SY * S::HZ);
-      bool same = !bad[sref];
-      for (int s = tid; s < NS && same; s += blockDim.x) {
-        const int sx = s % SX, sy = (s / SX) % SY, sz = s / (SX * SY);
-        int outs = (sx < 3 || sx >= 3 + TX);
-        if (D >= 2) outs += (sy < S::HY || sy >= S::HY + TY);
-        if (D >= 3) outs += (sz < S::HZ || sz >= S::HZ + TZ);
-        if (outs > 1) continue;
-#pragma unroll
-        for (int v = 0; v < NV; v++) same = same && same_bits(U[v * NS + s], U[v * NS + sref]);
-      }
-      idle = __syncthreads_and(same) != 0;
-    }
+    if (!anyband && interior_tile) idle = __syncthreads_and(stencil_uniform<D, T>(U, bad, tid)) != 0;
     // face apertures and fluxes: x faces, then y, then z
-    for (int f = tid; f < S::NF && !idle; f += blockDim.x) {
-      if (f < S::NFX)
-        flux_face<D, T, 0>(g, b, U, P, F, A, bad, bb, f, f, x0, y0, z0, m, anyband, eps, err);
-      else if (D >= 2 && f < S::NFX + S::NFY)
-        flux_face<D, T, 1>(g, b, U, P, F, A, bad, bb, f, f - S::NFX, x0, y0, z0, m, anyband, eps, err);
-      else if (D >= 3)
-        flux_face<D, T, 2>(g, b, U, P, F, A, bad, bb, f, f - S::NFX - S::NFY, x0, y0, z0, m, anyband, eps, err);
-    }
+    if (!idle)
+      for (int f = tid; f < S::NF; f += blockDim.x) {
+        if (f < S::NFX)
+          flux_face<D, T, 0>(g, b, U, P, F, A, bad, bb, f, f, x0, y0, z0, m, anyband, eps, err);
+        else if (D >= 2 && f < S::NFX + S::NFY)
+          flux_face<D, T, 1>(g, b, U, P, F, A, bad, bb, f, f - S::NFX, x0, y0, z0, m, anyband, eps, err);
+        else if (D >= 3)
+          flux_face<D, T, 2>(g, b, U, P, F, A, bad, bb, f, f - S::NFX - S::NFY, x0, y0, z0, m, anyband, eps, err);
+      }
     __syncthreads();
     // cell update
     if (inside && ((mymask >> m) & 1u)) {
@@ -1095,10 +1103,12 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
 #pragma unroll
       for (int v = 0; v < NV; v++) {
         double L = 0.0;
+        if (!idle) {
 #pragma unroll
-        for (int d = 0; d < D && !idle; d++) {
-          const double fl = (double)F[v * S::NF + flo[d]], fh = (double)F[v * S::NF + fhi[d]];
-          L = L + (A[flo[d]] * fl - A[fhi[d]] * fh) * g.rh[d];
+          for (int d = 0; d < D; d++) {
+            const double fl = (double)F[v * S::NF + flo[d]], fh = (double)F[v * S::NF + fhi[d]];
+            L = L + (A[flo[d]] * fl - A[fhi[d]] * fh) * g.rh[d];
+          }
         }
         if (cut) L = L + b.X[qidx(g, m, v, c)] * g.rV;
         const long long qi = qidx(g, m, v, c);
@@ -1121,7 +1131,7 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
 // of leaving a partial last wave; each tile's arithmetic does not depend on
 // which CTA runs it.
 template <int D, typename T>
-__global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z)
+__global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z, sizeof(T) == 4 ? 4 : 1)
     k_flux_update(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs,
                   const double* Qn, double* Qout, double beta, double omb, const __grid_constant__ BndBase bb,
                   int ntiles) {
