@@ -977,6 +977,7 @@ typedef struct {
   int small, ntarget;
   long tgt[MIX_MAXT];
   double M[MIX_MAXT][5];
+  double ws[MIX_MAXT], wt[MIX_MAXT]; /* weight of the partner in the small cell's / the target's mixed state */
 } mixrec;
 
 static int mix_axes(int D, int kidx) { return D <= 2 ? MIX_AX2[kidx] : MIX_AX3[kidx]; }
@@ -993,6 +994,13 @@ static void mix_source(const orc* o, const double* Qc, long c, int m, mixrec* r,
   if (as == 0.0)
     for (int v = 0; v < NV; v++)
       if (Qc[QI(o, m, v, c)] != 0.0) small = 1;
+  /* a non-physical state (rho <= 0 or p + pinf <= 0) mixes like a small cell */
+  if (as > 0.0 && !small) {
+    double u[5], w[5];
+    for (int v = 0; v < NV; v++) u[v] = Qc[QI(o, m, v, c)] / as;
+    cons_to_prim(o, m, u, w);
+    if (!(w[0] > 0.0) || !(w[NV - 1] + o->p.pinf[m] > 0.0)) small = 1;
+  }
   if (!small) return;
   r->small = 1;
   double n[3];
@@ -1064,7 +1072,17 @@ static void mix_source(const orc* o, const double* Qc, long c, int m, mixrec* r,
     r->tgt[q] = tlist[k];
     for (int v = 0; v < NV; v++)
       r->M[q][v] = beta * (as * Qc[QI(o, m, v, tlist[k])] - at * Qc[QI(o, m, v, c)]) / (as + at);
+    r->ws[q] = beta * at / (as + at);
+    r->wt[q] = beta * as / (as + at);
   }
+}
+
+/* scale of a pair exchange from the weight sums of its two cells */
+static double mix_limit(double Ts, double Tt) {
+  double f = 1.0;
+  if (Ts > 1.0) f = fmin(f, 1.0 / Ts);
+  if (Tt > 1.0) f = fmin(f, 1.0 / Tt);
+  return f;
 }
 
 static void mixing(orc* o, double* Qc) {
@@ -1081,6 +1099,42 @@ static void mixing(orc* o, double* Qc) {
       if (fail) o->cnt[ORC_C_MIXFAIL]++;
       if (merge && m != o->chi[c]) mergef[MI(o, m, c)] = 1;
     }
+  /* Weight limit (a reading of the mixing of Sec. 2.3.2): a pair exchange
+   * M = beta (a_s Q_t - a_t Q_s) / (a_s + a_t) moves the per-volume state of
+   * each side towards the other's with weight w (w_s = beta a_t / (a_s + a_t)
+   * for the small cell, w_t = beta a_s / (a_s + a_t) for the target). A cell
+   * in several pairs takes the sum T of its weights; when T > 1 its mixed state
+   * would extrapolate, so each pair's exchange is scaled by
+   * min(1, 1/T_s, 1/T_t): every mixed state is then a convex combination of
+   * the pre-mixing states around it, and the exchanges stay antisymmetric
+   * (conservative). T sums the cell's own pairs in target order, then the
+   * pairs of the neighbours that target it in (z, y, x) offset order. A small
+   * cell without volume (a_s = 0) has no per-volume state to keep convex and
+   * adds nothing to its target's T (w_t = 0): its exchanges stay whole, so
+   * its content always leaves. */
+  double* Tw = (double*)calloc((size_t)N * nc, sizeof(double));
+  for (long c = 0; c < nc; c++) {
+    if (!o->inB[c]) continue;
+    int ijk[3];
+    coords(o, c, ijk);
+    for (int m = 0; m < N; m++) {
+      if (!((o->smask[c] >> m) & 1u)) continue;
+      double T = 0.0;
+      const mixrec* own = &rec[MI(o, m, c)];
+      for (int q = 0; q < own->ntarget; q++) T += own->ws[q];
+      for (int dz = (D >= 3 ? -1 : 0); dz <= (D >= 3 ? 1 : 0); dz++)
+        for (int dy = (D >= 2 ? -1 : 0); dy <= (D >= 2 ? 1 : 0); dy++)
+          for (int dx = -1; dx <= 1; dx++) {
+            if (dx == 0 && dy == 0 && dz == 0) continue;
+            int sq[3] = {ijk[0] - dx, ijk[1] - dy, ijk[2] - dz};
+            if (!in_array(o, sq)) continue;
+            const mixrec* rs = &rec[MI(o, m, cell_at(o, sq))];
+            for (int q = 0; q < rs->ntarget; q++)
+              if (rs->tgt[q] == c) T += rs->wt[q];
+          }
+      Tw[MI(o, m, c)] = T;
+    }
+  }
   double* Qnew = (double*)malloc(sizeof(double) * (size_t)N * NV * nc);
   memcpy(Qnew, Qc, sizeof(double) * (size_t)N * NV * nc);
   for (long c = 0; c < nc; c++) {
@@ -1091,8 +1145,10 @@ static void mixing(orc* o, double* Qc) {
       if (!((o->smask[c] >> m) & 1u)) continue;
       double acc[5] = {0, 0, 0, 0, 0};
       const mixrec* own = &rec[MI(o, m, c)];
-      for (int q = 0; q < own->ntarget; q++)
-        for (int v = 0; v < NV; v++) acc[v] += own->M[q][v];
+      for (int q = 0; q < own->ntarget; q++) {
+        const double f = o->alpha[MI(o, m, c)] == 0.0 ? 1.0 : mix_limit(Tw[MI(o, m, c)], Tw[MI(o, m, own->tgt[q])]);
+        for (int v = 0; v < NV; v++) acc[v] += f * own->M[q][v];
+      }
       /* exchanges that neighbours send to this cell, neighbour offsets in
          lexicographic (z, y, x) order */
       for (int dz = (D >= 3 ? -1 : 0); dz <= (D >= 3 ? 1 : 0); dz++)
@@ -1104,8 +1160,10 @@ static void mixing(orc* o, double* Qc) {
             long sc = cell_at(o, sq);
             const mixrec* rs = &rec[MI(o, m, sc)];
             for (int q = 0; q < rs->ntarget; q++)
-              if (rs->tgt[q] == c)
-                for (int v = 0; v < NV; v++) acc[v] -= rs->M[q][v];
+              if (rs->tgt[q] == c) {
+                const double f = o->alpha[MI(o, m, sc)] == 0.0 ? 1.0 : mix_limit(Tw[MI(o, m, sc)], Tw[MI(o, m, c)]);
+                for (int v = 0; v < NV; v++) acc[v] -= f * rs->M[q][v];
+              }
           }
       for (int v = 0; v < NV; v++) Qnew[QI(o, m, v, c)] = Qc[QI(o, m, v, c)] + acc[v];
     }
@@ -1125,6 +1183,7 @@ static void mixing(orc* o, double* Qc) {
   free(Qnew);
   free(rec);
   free(mergef);
+  free(Tw);
 }
 
 /* ------------------------------------------------------------------ */

@@ -19,6 +19,7 @@ struct AdjBufs {
   uint8_t* mixn[3];  // mixing records of each stage (as Bufs::mixn / mixoff / mixbeta)
   uint8_t* mixoff[3];
   double* mixbeta[3];
+  double* mixT[3];
   double* aband[4];  // [nbmax][N] band volume fractions after each geometry: 0 step start, s+1 after stage s
   double* deos;      // [MAXM][2] d/d(gamma_m, pinf_m)
   double* dinf;      // [3][2][5] d/d(inflow primitive state)

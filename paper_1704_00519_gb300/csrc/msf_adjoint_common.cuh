@@ -140,13 +140,16 @@ __global__ void k_adj_mix_merge(const __grid_constant__ Grid g, const __grid_con
 }
 
 // mixing adjoint, part 2: transpose of the pairwise exchanges
-// M = beta (a_s Q_t - a_t Q_s) / (a_s + a_t), Q_s += M, Q_t -= M
+// M = f beta (a_s Q_t - a_t Q_s) / (a_s + a_t), Q_s += M, Q_t -= M, with the
+// pair scale f = mix_limit(a_s, T_s, T_t) of the recorded weight sums (f and
+// the volume fractions do not depend on Q at frozen interface evolution)
 __global__ void k_adj_mix_exchange(const __grid_constant__ Grid g, const __grid_constant__ Bufs b,
                                    const __grid_constant__ AdjBufs a, int st) {
   const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
   const uint8_t* mixn = a.mixn[st];
   const uint8_t* mixoff = a.mixoff[st];
   const double* mixbeta = a.mixbeta[st];
+  const double* mixT = a.mixT[st];
   const double* ab = a.aband[st + 1];
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < nb * N; it += gridDim.x * blockDim.x) {
     const int m = it / nb, kk = it - m * nb;
@@ -163,7 +166,7 @@ __global__ void k_adj_mix_exchange(const __grid_constant__ Grid g, const __grid_
           const long long tc = off_cell(g, c, mixoff[r * MIX_MAXT + t]);
           const long long rt = (long long)b.bandidx[tc] * N + m;
           const double at = ab[rt];
-          const double kap = mixbeta[r * MIX_MAXT + t] / (ax + at);
+          const double kap = mix_limit(ax, mixT[r], mixT[rt]) * mixbeta[r * MIX_MAXT + t] / (ax + at);
           for (int v = 0; v < NV; v++) out[v] += kap * at * (a.mixt[rt * NV + v] - lx[v]);
         }
       int q[3];
@@ -185,7 +188,7 @@ __global__ void k_adj_mix_exchange(const __grid_constant__ Grid g, const __grid_
             for (int t = 0; t < ns; t++) {
               if (mixoff[rs * MIX_MAXT + t] != code) continue;
               const double as = ab[rs];
-              const double kap = mixbeta[rs * MIX_MAXT + t] / (as + ax);
+              const double kap = mix_limit(as, mixT[rs], mixT[r]) * mixbeta[rs * MIX_MAXT + t] / (as + ax);
               for (int v = 0; v < NV; v++) out[v] += kap * as * (a.mixt[rs * NV + v] - lx[v]);
             }
           }

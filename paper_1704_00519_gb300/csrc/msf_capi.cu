@@ -48,6 +48,7 @@ struct msf_ctx {
   unsigned* d_flag = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool graph_tried = false;
+  long long graph_kernels = -1;  // kernel nodes of the captured step graph
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   long long launches = 0;  // kernel launches of the last enqueued step
   void* arena = nullptr;   // every device array of every instance
@@ -330,6 +331,7 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
       b.mixoff = (uint8_t*)carve(nbmax * N * MIX_MAXT);
       b.mixbeta = (double*)carve(8 * nbmax * N * MIX_MAXT);
       b.mixin = (unsigned*)carve(4 * nbmax * N);
+      b.mixT = (double*)carve(8 * nbmax * N);
       b.phir = (double*)carve(8 * nbmax * N);
       b.bflux = (double*)carve(8 * std::max<long long>(1, in.nbnd) * N * NV);
       b.ctl = (Ctl*)carve(sizeof(Ctl));
@@ -421,7 +423,7 @@ static long long count_launches(const msf_ctx* c) {
     const Grid& g = in.g;
     const long long ext = tiled_ext(c, g) ? 1 : g.ext_sweeps;
     const long long vel = tiled_vel(c, g) ? 1 : g.vel_sweeps, re = 2LL * g.reinit_iters;
-    const long long per_stage = 1 + ext + 1 + 1 + 1 + vel + 1 + 1 + 1 + 1 + 1 + 2 + 3;
+    const long long per_stage = 1 + ext + 1 + 1 + 1 + vel + 1 + 1 + 1 + 1 + 1 + 2 + 4;
     n += 1 + 1 + (2 + g.D) + 2 + 1 + g.rk * per_stage + 2 + 1;
     if (g.scale_sep) n += 2 + 1;
     if (g.reinit) n += re + 1;
@@ -605,6 +607,18 @@ extern "C" msf_status msf_step(msf_ctx* c, int32_t n_steps, double t_end, int32_
       msf_status st = enqueue_step(c);
       cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
       if (st == MSF_OK && e == cudaSuccess) {
+        size_t nn = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess) {
+          std::vector<cudaGraphNode_t> nodes(nn);
+          if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess) {
+            long long nk = 0;
+            for (size_t k = 0; k < nn; k++) {
+              cudaGraphNodeType ty;
+              if (cudaGraphNodeGetType(nodes[k], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) nk++;
+            }
+            c->graph_kernels = nk;
+          }
+        }
         if (cudaGraphInstantiate(&c->graph, graph, 0) != cudaSuccess) c->graph = nullptr;
         cudaGraphDestroy(graph);
       }
@@ -857,6 +871,9 @@ extern "C" msf_status msf_launches_per_step(msf_ctx* c, int64_t* n) {
   if (!c || !n) return MSF_EINVAL;
   // batched: one persistent launch (plus the end-time kernel) covers every step of a call
   *n = c->batched ? 1 : count_launches(c);
+  // the captured step graph holds the kernels one step actually enqueues
+  if (!c->batched && c->graph && c->graph_kernels >= 0 && c->graph_kernels != *n)
+    return fail(c, MSF_ESTATE, "kernel count of one step out of step with the captured graph");
   return MSF_OK;
 }
 
@@ -924,6 +941,7 @@ static msf_status ensure_adjoint(msf_ctx* c) {
     a.mixn[k] = (uint8_t*)take(nbmax * N);
     a.mixoff[k] = (uint8_t*)take(nbmax * N * MIX_MAXT);
     a.mixbeta[k] = (double*)take(8 * nbmax * N * MIX_MAXT);
+    a.mixT[k] = (double*)take(8 * nbmax * N);
   }
   for (int k = 0; k < 4; k++) a.aband[k] = (double*)take(8 * nbmax * N);
   a.deos = (double*)take(8 * MAXM * 2);
@@ -1001,6 +1019,7 @@ static void enqueue_replay(msf_ctx* c, const char* tape, bool rec) {
       br.mixn = a.mixn[st];
       br.mixoff = a.mixoff[st];
       br.mixbeta = a.mixbeta[st];
+      br.mixT = a.mixT[st];
       launch_mix(g, br, Qo, nb, s);
     } else {
       launch_mix(g, b, Qo, nb, s);

@@ -204,6 +204,7 @@ void launch_scatter_phichi(const Grid& g, const Bufs& b, int nblk, cudaStream_t 
 }
 void launch_mix(const Grid& g, const Bufs& b, double* Qc, int nblk, cudaStream_t s) {
   k_mix_mark<<<nblk, BAND_THREADS, 0, s>>>(g, b, Qc);
+  k_mix_weights<<<nblk, BAND_THREADS, 0, s>>>(g, b);
   k_mix_compute<<<nblk, BAND_THREADS, 0, s>>>(g, b, Qc);
   k_mix_scatter<<<nblk, BAND_THREADS, 0, s>>>(g, b, Qc);
 }

@@ -1334,6 +1334,12 @@ __device__ inline bool is_small(const Grid& g, const Bufs& b, const double* Qc, 
   if (as == 0.0)
     for (int v = 0; v < g.NV; v++)
       if (Qc[qidx(g, m, v, c)] != 0.0) return true;
+  if (as > 0.0) {  // a non-physical state (rho <= 0 or p + pinf <= 0) mixes like a small cell
+    double u[5], w[5];
+    for (int v = 0; v < g.NV; v++) u[v] = Qc[qidx(g, m, v, c)] / as;
+    cons_to_prim<double>(g, m, g.D, u, w);
+    if (!(w[0] > 0.0) || !(w[g.NV - 1] + g.pinf[m] > 0.0)) return true;
+  }
   return false;
 }
 
@@ -1373,8 +1379,79 @@ __global__ void k_mix_mark(const __grid_constant__ Grid g, const __grid_constant
   phase_mix_mark(g, b, Qc, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
+// Weight sum T of every (band cell, material). A pair exchange
+// M = beta (a_s Q_t - a_t Q_s) / (a_s + a_t) moves the small cell's
+// per-volume state towards the target's with weight beta a_t / (a_s + a_t)
+// and the target's towards the small cell's with weight beta a_s / (a_s + a_t).
+// T sums a cell's weights: its own pairs in target order, then the pairs of
+// the neighbours that mix into it in (z, y, x) offset order.
+__device__ __forceinline__ void phase_mix_weights(const Grid& g, const Bufs& b, int first_, int stride_) {
+  const int nb = b.ctl->nband, N = g.N, D = g.D;
+  const int total = nb * N;
+  for (int it = first_; it < total; it += stride_) {
+    const int m = it / nb, k = it - m * nb;
+    const long long c = b.band[k];
+    const long long r = (long long)k * N + m;
+    double T = 0.0;
+    if ((b.smask[c] >> m) & 1u) {
+      const double ac = b.alpha[midx(g, m, c)];
+      const int nown = b.mixn[r];
+      for (int t = 0; t < (nown == 0xff ? 0 : nown); t++) {
+        const long long tc = off_cell(g, c, b.mixoff[r * MIX_MAXT + t]);
+        const double at = b.alpha[midx(g, m, tc)];
+        T += b.mixbeta[r * MIX_MAXT + t] * at / (ac + at);
+      }
+      const unsigned inbits = b.mixin[r];
+      if (inbits) {
+        int q[3];
+        coords(g, c, q);
+        const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
+        for (int dz = -rz; dz <= rz; dz++)
+          for (int dy = -ry; dy <= ry; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+              if (dx == 0 && dy == 0 && dz == 0) continue;
+              const uint8_t code = off_code(dx, dy, dz);
+              if (!((inbits >> code) & 1u)) continue;
+              const int sx = q[0] - dx, sy = q[1] - dy, sz = q[2] - dz;
+              if (!in_array(g, sx, sy, sz)) continue;
+              const long long s = cell_at(g, sx, sy, sz);
+              const int ks = b.bandidx[s];
+              if (ks < 0) continue;
+              const long long rs = (long long)ks * N + m;
+              const int ns = b.mixn[rs];
+              if (ns == 0xff) continue;
+              for (int t = 0; t < ns; t++) {
+                if (b.mixoff[rs * MIX_MAXT + t] != code) continue;
+                const double as = b.alpha[midx(g, m, s)];
+                T += b.mixbeta[rs * MIX_MAXT + t] * as / (as + ac);
+              }
+            }
+      }
+    }
+    b.mixT[r] = T;
+  }
+}
+__global__ void k_mix_weights(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+  if (!ctl_active(b)) return;
+  phase_mix_weights(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// Scale of a pair exchange from the weight sums of its two cells: when a
+// cell's T exceeds one its mixed state would leave the range of the states it
+// mixes with, so the pair is scaled by min(1, 1/T_s, 1/T_t) (both sides by the
+// same factor, so the exchange stays conservative). A small cell without
+// volume has no per-volume state to bound: its pairs stay whole.
+__device__ inline double mix_limit(double as, double Ts, double Tt) {
+  if (as == 0.0) return 1.0;
+  double f = 1.0;
+  if (Ts > 1.0) f = fmin(f, 1.0 / Ts);
+  if (Tt > 1.0) f = fmin(f, 1.0 / Tt);
+  return f;
+}
+
 // new state of material m of every band cell: own exchanges minus the
-// exchanges its small neighbours send to it (lexicographic neighbour order)
+// exchanges its small neighbours send to it (lexicographic neighbour order),
+// each scaled by mix_limit
 __device__ __forceinline__ void phase_mix_compute(const Grid& g, const Bufs& b, const double* Qc, int first_, int stride_) {
     const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
   const int total = nb * N;
@@ -1394,12 +1471,14 @@ __device__ __forceinline__ void phase_mix_compute(const Grid& g, const Bufs& b, 
     if (nown != 0xff) {
       const double as = b.alpha[midx(g, m, c)];
       if (nown == 0 && as == 0.0 && m != b.chi[c]) atomicOr(&b.mixmerge[k], 1u << m);
+      const double Tc = b.mixT[r];
       for (int t = 0; t < (nown == 0xff ? 0 : nown); t++) {
         const long long tc = off_cell(g, c, b.mixoff[r * MIX_MAXT + t]);
         const double beta = b.mixbeta[r * MIX_MAXT + t];
         const double at = b.alpha[midx(g, m, tc)];
+        const double f = mix_limit(as, Tc, b.mixT[(long long)b.bandidx[tc] * N + m]);
         for (int v = 0; v < NV; v++)
-          acc[v] += beta * (as * Qc[qidx(g, m, v, tc)] - at * Qc[qidx(g, m, v, c)]) / (as + at);
+          acc[v] += f * (beta * (as * Qc[qidx(g, m, v, tc)] - at * Qc[qidx(g, m, v, c)]) / (as + at));
       }
     }
     // neighbours that mix into this cell (bits set by the marking pass)
@@ -1424,8 +1503,9 @@ __device__ __forceinline__ void phase_mix_compute(const Grid& g, const Bufs& b, 
             const double beta = b.mixbeta[rs * MIX_MAXT + t];
             const double as = b.alpha[midx(g, m, s)];
             const double at = b.alpha[midx(g, m, c)];
+            const double f = mix_limit(as, b.mixT[rs], b.mixT[r]);
             for (int v = 0; v < NV; v++)
-              acc[v] -= beta * (as * Qc[qidx(g, m, v, c)] - at * Qc[qidx(g, m, v, s)]) / (as + at);
+              acc[v] -= f * (beta * (as * Qc[qidx(g, m, v, c)] - at * Qc[qidx(g, m, v, s)]) / (as + at));
           }
         }
     for (int v = 0; v < NV; v++) out[v] = Qc[qidx(g, m, v, c)] + acc[v];
@@ -1809,6 +1889,8 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
       phase_geom_cell(g, b, (const double*)Qo, (const double*)nullptr, t, nt);
       __syncthreads();
       phase_mix_mark(g, b, (const double*)Qo, t, nt);
+      __syncthreads();
+      phase_mix_weights(g, b, t, nt);
       __syncthreads();
       phase_mix_compute(g, b, (const double*)Qo, t, nt);
       __syncthreads();

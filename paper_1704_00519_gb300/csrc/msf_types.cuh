@@ -34,6 +34,7 @@ struct Bufs {
   uint8_t* mixoff;          // [nbandmax][N][MIX_MAXT] target offset codes
   double* mixbeta;          // [nbandmax][N][MIX_MAXT] normalised mixing weights
   unsigned* mixin;          // [nbandmax][N] bit (offset code) of every neighbour that mixes into the cell
+  double* mixT;             // [nbandmax][N] weight sum of the mixing pairs of the cell
   double* phir;             // [nbandmax][N] new local level-set values
   double* bflux;            // [nbnd][N][NV] boundary-face fluxes of the stage
   Ctl* ctl;

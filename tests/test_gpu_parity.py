@@ -92,10 +92,12 @@ def test_random_2d_fp64(msf, n, nmat, seed):
 
 def test_device_errors_match_oracle(msf):
     """A violent random four-material start that drives a state non-physical:
-    the GPU path reports the same error as the oracle."""
+    the GPU path reports the same error as the oracle (the oracle may also
+    flag a non-finite state of the same step; a non-physical state takes
+    precedence in the status)."""
     case = cs.random_case(2, (75, 37), 4, 2)
     o = orc.Oracle(case)
-    assert o.step(15, case.t_end) == orc_ENEGATIVE
+    assert o.step(15, case.t_end) & orc_ENEGATIVE
     s = msf.Solver(case)
     with pytest.raises(msf.MsfError) as ei:
         s.step(15, case.t_end)
@@ -298,3 +300,19 @@ def test_device_inputs_and_set_state_roundtrip(msf):
     a, b = s.state(), s2.state()
     assert np.array_equal(a["Q"], b["Q"])
     assert a["t"] == b["t"]
+
+
+@pytest.mark.parametrize("maker,prec,opts", [
+    (lambda: cs.triple_point(56, 24), 0, {}),
+    (lambda: cs.triple_point(56, 24), 1, {}),
+    (lambda: cs.shock_tube_3(100), 0, dict(rk_stages=2)),
+    (lambda: cs.random_case(3, (10, 9, 8), 2, 2), 1, dict(scale_sep=0, reinit=0)),
+])
+def test_launch_count_matches_graph(msf, maker, prec, opts):
+    """The kernel count one step reports equals the kernel nodes of the step
+    graph the first call captures (the call raises when they differ)."""
+    case = maker()
+    s = msf.Solver(case, precision=prec, **opts)
+    s.step(2, case.t_end)
+    assert s.launches_per_step() > 0
+    s.close()
