@@ -52,7 +52,22 @@ typedef enum { MSF_FP64 = 0, MSF_FP32_BULK = 1 } msf_precision;
  *   lo, hi       domain box; h_d = (hi_d - lo_d) / n_d
  *   bc[d][side]  msf_bc for the low (0) and high (1) side of axis d
  *   inflow_prim  primitive (rho, u_0..u_{dim-1}, p) imposed on an inflow side
- *   inflow_mat   material of the inflow state */
+ *   inflow_mat   material of the inflow state
+ *   geom         MSF_GEOM_CARTESIAN (0), or MSF_GEOM_CYLINDRICAL (1): a grid of
+ *                one dimension whose x is the radius of an axisymmetric flow
+ *                (Sec. 3, Case II; lo[0] >= 0). Cell i has volume r_i h and
+ *                its faces areas r_f; the radial momentum gains p alpha / r_i;
+ *                totals weight each cell by its volume.
+ *   free_surface 0, or 1: material fs_mat is an ambient that is not solved
+ *                (Sec. 3, Case II). Its state is held at (fs_rho, 0, p(t)) and
+ *                the interfaces of the other materials with it carry the
+ *                pressure p(t) = fs_p0 for t <= fs_t0, falling linearly to
+ *                fs_p1 at fs_t1 and fs_p1 after; the interface velocity comes
+ *                from the two-shock wave curve of the solved side. Requires
+ *                fs_rho > 0 and fs_t1 > fs_t0. The batched form (n_instances > 1,
+ *                dim 1, batch_mode 0) and the tape and adjoint entry points
+ *                refuse a grid with geom != 0 or free_surface != 0
+ *                (MSF_EUNSUPPORTED); batch_mode 1 steps such instances. */
 typedef struct {
   int32_t dim;
   int32_t n[3];
@@ -60,7 +75,11 @@ typedef struct {
   int32_t bc[3][2];
   double inflow_prim[3][2][5];
   int32_t inflow_mat[3][2];
+  int32_t geom;
+  int32_t free_surface, fs_mat;
+  double fs_rho, fs_p0, fs_t0, fs_t1, fs_p1;
 } msf_grid;
+typedef enum { MSF_GEOM_CARTESIAN = 0, MSF_GEOM_CYLINDRICAL = 1 } msf_geom;
 
 /* Equation of state of one material (Sec. 2.1).
  * kind MSF_EOS_STIFFENED (0): stiffened gas p = (gamma - 1) rho e - gamma pinf

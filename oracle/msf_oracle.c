@@ -164,6 +164,51 @@ static double sound(orc* o, int m, double rho, double p) {
 }
 
 /* ------------------------------------------------------------------ */
+/* axisymmetric grid and free-surface ambient (Sec. 3, Case II)         */
+/* ------------------------------------------------------------------ */
+/* A cylindrical grid of one dimension takes x as the radius: the volume of
+ * cell i is r_i h and the area of a face r_f (per radian and unit length),
+ * so the update of a cell reads L = (A_lo F_lo r_lo - A_hi F_hi r_hi + X) /
+ * (r_i h) plus the source p alpha / r_i of the radial momentum (the pressure
+ * on the sides of the wedge). Volume fractions stay those of the segment. */
+static int cyl(const orc* o) { return o->p.geom == 1; }
+static double face_r(const orc* o, int i) { return o->p.lo[0] + (double)(i - o->off[0]) * o->h[0]; }
+static double cell_r(const orc* o, int i) { return o->p.lo[0] + ((double)(i - o->off[0]) + 0.5) * o->h[0]; }
+/* volume of cell c over the Cartesian cell volume (1 on Cartesian grids) */
+static double vfac(const orc* o, long c) { return cyl(o) ? cell_r(o, (int)(c % o->pn[0])) : 1.0; }
+
+/* pressure the ambient exerts at time t: p0 up to t0, linear to p1 at t1, p1 after */
+static double fs_pressure(const orc* o, double t) {
+  const orc_params* p = &o->p;
+  if (t <= p->fs_t0) return p->fs_p0;
+  if (t >= p->fs_t1) return p->fs_p1;
+  return p->fs_p0 - (p->fs_p0 - p->fs_p1) * (t - p->fs_t0) / (p->fs_t1 - p->fs_t0);
+}
+/* velocity jump across the wave of a material at (rho, pK) that takes its
+ * pressure to p, on the two-shock approximation of the Riemann problem
+ * (Toro, Riemann Solvers, Sec. 9.4.2): (p - pK) sqrt(A / (p + pinf + B)),
+ * A = 2 / ((g + 1) rho), B = (g - 1) / (g + 1) (pK + pinf) */
+static double fs_wave(const orc* o, int m, double rho, double pK, double p) {
+  double g = o->p.gamma[m], pi = o->p.pinf[m];
+  double A = 2.0 / ((g + 1.0) * rho), B = (g - 1.0) / (g + 1.0) * (pK + pi);
+  return (p - pK) * sqrt(A / (p + pi + B));
+}
+/* the ambient is not solved: its conserved state is alpha (fs_rho, 0, p(t)) */
+static void hold_ambient(orc* o, double* Qc, double t) {
+  int F = o->p.fs_mat;
+  if (F < 0) return;
+  double w[5] = {0, 0, 0, 0, 0}, u[5];
+  w[0] = o->p.fs_rho;
+  w[o->D + 1] = fs_pressure(o, t);
+  prim_to_cons(o, F, w, u);
+  for (long c = 0; c < o->ncell; c++) {
+    if (!interior_c(o, c)) continue;
+    double a = o->alpha[MI(o, F, c)];
+    for (int v = 0; v < o->NV; v++) Qc[QI(o, F, v, c)] = a * u[v];
+  }
+}
+
+/* ------------------------------------------------------------------ */
 /* WENO5-JS (Jiang & Shu), value at i+1/2 from cells i-2..i+2           */
 /* ------------------------------------------------------------------ */
 double orc_weno5(double a, double b, double c, double d, double e, double eps) {
@@ -688,7 +733,7 @@ static void compute_dt(orc* o, double t_end) {
   for (long c = 0; c < o->ncell; c++) {
     if (!interior_c(o, c)) continue;
     for (int m = 0; m < N; m++) {
-      if (!(o->alpha[MI(o, m, c)] > 0.0)) continue;
+      if (!(o->alpha[MI(o, m, c)] > 0.0) || m == o->p.fs_mat) continue;
       double u[5], w[5];
       for (int v = 0; v < o->NV; v++) u[v] = o->Uh[QI(o, m, v, c)];
       cons_to_prim(o, m, u, w);
@@ -706,7 +751,7 @@ static void compute_dt(orc* o, double t_end) {
 /* ------------------------------------------------------------------ */
 /* reduced interface interaction (a7, Sec. 2.3.2)                       */
 /* ------------------------------------------------------------------ */
-static void interface_exchange(orc* o, const double* Qs) {
+static void interface_exchange(orc* o, const double* Qs, double ts) {
   int N = o->N, NV = o->NV, D = o->D;
   for (long i = 0; i < (long)N * NV * o->ncell; i++) o->X[i] = 0.0;
   for (long c = 0; c < o->ncell; c++) {
@@ -741,7 +786,21 @@ static void interface_exchange(orc* o, const double* Qs) {
     double el[3] = {o->p.gamma[L], o->p.pinf[L], (double)o->p.eos_kind[L]};
     double er[3] = {o->p.gamma[R], o->p.pinf[R], (double)o->p.eos_kind[R]};
     double us, ps;
-    orc_hllc(rl, rr, el, er, &us, &ps);
+    const int F = o->p.fs_mat;
+    if (F >= 0 && (L == F || R == F)) {
+      /* free surface: the ambient imposes p* = p(t); the solved side's
+         two-shock wave curve gives u* */
+      ps = fs_pressure(o, ts);
+      if (R == F) {
+        (void)sound(o, L, wL[0], wL[D + 1]);
+        us = unl - fs_wave(o, L, wL[0], wL[D + 1], ps);
+      } else {
+        (void)sound(o, R, wR[0], wR[D + 1]);
+        us = unr + fs_wave(o, R, wR[0], wR[D + 1], ps);
+      }
+    } else {
+      orc_hllc(rl, rr, el, er, &us, &ps);
+    }
     /* the pair's interface state acts on the boundary segment of every other
        present material, S^m = sum_f A^m_f |f| n_f^out (pointing into m);
        material R takes minus their sum, so sum_m X^m = 0 exactly and with
@@ -750,7 +809,14 @@ static void interface_exchange(orc* o, const double* Qs) {
     for (int m = 0; m < N; m++) {
       if (m == R || !present(o, c, m)) continue;
       double S[3] = {0, 0, 0}, nS = 0.0;
-      for (int d = 0; d < D; d++) S[d] = (o->Ahi[AI(o, d, m, c)] - o->Alo[AI(o, d, m, c)]) * o->farea[d];
+      if (cyl(o)) {
+        /* interface area r_I n: the faces' r_f A_f less the wedge side alpha h */
+        int ic = (int)(c % o->pn[0]);
+        S[0] = o->Ahi[AI(o, 0, m, c)] * face_r(o, ic + 1) - o->Alo[AI(o, 0, m, c)] * face_r(o, ic) -
+               o->alpha[MI(o, m, c)] * o->h[0];
+      } else {
+        for (int d = 0; d < D; d++) S[d] = (o->Ahi[AI(o, d, m, c)] - o->Alo[AI(o, d, m, c)]) * o->farea[d];
+      }
       for (int d = 0; d < D; d++) nS += n[d] * S[d];
       for (int d = 0; d < D; d++) {
         o->X[QI(o, m, 1 + d, c)] = ps * S[d];
@@ -812,6 +878,10 @@ static const double BETA2[2] = {0.0, 0.5};
 static const double LEDGER_W2[2] = {0.5, 0.5};
 static double rk_beta(const orc* o, int s) { return o->S == 2 ? BETA2[s] : BETA3[s]; }
 static double rk_ledger_w(const orc* o, int s) { return o->S == 2 ? LEDGER_W2[s] : LEDGER_W3[s]; }
+/* time of stage s as a fraction of the step (s = S: the step's end) */
+static const double RKC3[4] = {0.0, 1.0, 0.5, 1.0};
+static const double RKC2[3] = {0.0, 1.0, 1.0};
+static double rk_c(const orc* o, int s) { return o->S == 2 ? RKC2[s] : RKC3[s]; }
 
 static void face_flux(orc* o, long cL, int d, int m, double* Fh) {
   int NV = o->NV, D = o->D;
@@ -865,16 +935,17 @@ static void flux_update(orc* o, int s, const double* Qs, double* Qout) {
       for (int m = 0; m < N; m++) {
         double Fh[5] = {0, 0, 0, 0, 0};
         double A = face_aperture(o, cL, c, d, m);
-        if (A > 0.0) {
+        if (A > 0.0 && m != o->p.fs_mat) {
           int lin = interior_c(o, cL), rin = interior_c(o, c);
           if ((lin && !((o->smask[cL] >> m) & 1u)) || (rin && !((o->smask[c] >> m) & 1u))) o->err |= ORC_EBAND;
           face_flux(o, cL, d, m, Fh);
         }
         for (int v = 0; v < NV; v++) o->F[((long)(d * N + m) * NV + v) * o->ncell + c] = Fh[v];
+        double fa = cyl(o) ? face_r(o, ijk[0]) : o->farea[d];
         if (r == 0)
-          for (int v = 0; v < NV; v++) Fb[m][v] += A * Fh[v] * o->farea[d];
+          for (int v = 0; v < NV; v++) Fb[m][v] += A * Fh[v] * fa;
         if (r == o->n[d])
-          for (int v = 0; v < NV; v++) Fb[m][v] -= A * Fh[v] * o->farea[d];
+          for (int v = 0; v < NV; v++) Fb[m][v] -= A * Fh[v] * fa;
       }
     }
   double beta = rk_beta(o, s), omb = 1.0 - rk_beta(o, s), dt = o->dt;
@@ -887,14 +958,36 @@ static void flux_update(orc* o, int s, const double* Qs, double* Qout) {
         Alo[d] = face_aperture(o, c - o->st[d], c, d, m);
         Ahi[d] = face_aperture(o, c, c + o->st[d], d, m);
       }
+      double rlo = 0.0, rhi = 0.0, rvc = 0.0, psrc = 0.0;
+      if (cyl(o)) {
+        int ic = (int)(c % o->pn[0]);
+        double rc = cell_r(o, ic), a = o->alpha[MI(o, m, c)];
+        rlo = face_r(o, ic);
+        rhi = face_r(o, ic + 1);
+        rvc = 1.0 / (rc * o->h[0]);
+        if (a > 0.0) {
+          double u[5], w[5];
+          for (int v = 0; v < NV; v++) u[v] = o->Uh[QI(o, m, v, c)];
+          cons_to_prim(o, m, u, w);
+          psrc = w[D + 1] * a / rc;
+        }
+      }
       for (int v = 0; v < NV; v++) {
         double L = 0.0;
-        for (int d = 0; d < D; d++) {
-          double flo = o->F[((long)(d * N + m) * NV + v) * o->ncell + c];
-          double fhi = o->F[((long)(d * N + m) * NV + v) * o->ncell + c + o->st[d]];
-          L = L + (Alo[d] * flo - Ahi[d] * fhi) * o->rh[d];
+        if (cyl(o)) {
+          double flo = o->F[((long)m * NV + v) * o->ncell + c];
+          double fhi = o->F[((long)m * NV + v) * o->ncell + c + 1];
+          L = (Alo[0] * flo * rlo - Ahi[0] * fhi * rhi) * rvc + o->X[QI(o, m, v, c)] * rvc;
+          if (v == 1) L = L + psrc;
+        } else {
+          for (int d = 0; d < D; d++) {
+            double flo = o->F[((long)(d * N + m) * NV + v) * o->ncell + c];
+            double fhi = o->F[((long)(d * N + m) * NV + v) * o->ncell + c + o->st[d]];
+            L = L + (Alo[d] * flo - Ahi[d] * fhi) * o->rh[d];
+          }
+          L = L + o->X[QI(o, m, v, c)] * o->rV;
         }
-        L = L + o->X[QI(o, m, v, c)] * o->rV;
+        if (m == o->p.fs_mat) L = 0.0;
         double qn = o->Q[QI(o, m, v, c)], qs = Qs[QI(o, m, v, c)];
         double q = beta * qn + omb * (qs + dt * L);
         if (!isfinite(q)) o->err |= ORC_ENONFINITE;
@@ -1065,15 +1158,19 @@ static void mix_source(const orc* o, const double* Qc, long c, int m, mixrec* r,
     if (as == 0.0) *merge = 1;
     return;
   }
+  /* with cell volumes V (r h on a cylindrical grid) the pair moves the content
+     C = beta V_s V_t (a_s Q_t - a_t Q_s) / (a_s V_s + a_t V_t): M below is
+     C / (V_s V_t); the small cell gains M V_t, the target loses M V_s */
+  const double vs = vfac(o, c);
   for (int k = 0; k < nt; k++) {
     double beta = wlist[k] / sw;
-    double at = o->alpha[MI(o, m, tlist[k])];
+    double at = o->alpha[MI(o, m, tlist[k])], vt = vfac(o, tlist[k]);
     int q = r->ntarget++;
     r->tgt[q] = tlist[k];
     for (int v = 0; v < NV; v++)
-      r->M[q][v] = beta * (as * Qc[QI(o, m, v, tlist[k])] - at * Qc[QI(o, m, v, c)]) / (as + at);
-    r->ws[q] = beta * at / (as + at);
-    r->wt[q] = beta * as / (as + at);
+      r->M[q][v] = beta * (as * Qc[QI(o, m, v, tlist[k])] - at * Qc[QI(o, m, v, c)]) / (as * vs + at * vt);
+    r->ws[q] = beta * (at * vt) / (as * vs + at * vt);
+    r->wt[q] = beta * (as * vs) / (as * vs + at * vt);
   }
 }
 
@@ -1147,7 +1244,8 @@ static void mixing(orc* o, double* Qc) {
       const mixrec* own = &rec[MI(o, m, c)];
       for (int q = 0; q < own->ntarget; q++) {
         const double f = o->alpha[MI(o, m, c)] == 0.0 ? 1.0 : mix_limit(Tw[MI(o, m, c)], Tw[MI(o, m, own->tgt[q])]);
-        for (int v = 0; v < NV; v++) acc[v] += f * own->M[q][v];
+        const double vt = vfac(o, own->tgt[q]);
+        for (int v = 0; v < NV; v++) acc[v] += f * (own->M[q][v] * vt);
       }
       /* exchanges that neighbours send to this cell, neighbour offsets in
          lexicographic (z, y, x) order */
@@ -1162,7 +1260,8 @@ static void mixing(orc* o, double* Qc) {
             for (int q = 0; q < rs->ntarget; q++)
               if (rs->tgt[q] == c) {
                 const double f = o->alpha[MI(o, m, sc)] == 0.0 ? 1.0 : mix_limit(Tw[MI(o, m, sc)], Tw[MI(o, m, c)]);
-                for (int v = 0; v < NV; v++) acc[v] -= f * rs->M[q][v];
+                const double vs = vfac(o, sc);
+                for (int v = 0; v < NV; v++) acc[v] -= f * (rs->M[q][v] * vs);
               }
           }
       for (int v = 0; v < NV; v++) Qnew[QI(o, m, v, c)] = Qc[QI(o, m, v, c)] + acc[v];
@@ -1332,6 +1431,7 @@ static int step_once(orc* o, double t_end, double* tphi, uint8_t* tchi, double* 
   }
   step_band(o);
   geometry(o, o->Q);
+  hold_ambient(o, o->Q, o->t);
   memcpy(o->phin, o->phi, sizeof(double) * nc);
   memcpy(o->chin, o->chi, nc);
   int last = 0;
@@ -1349,7 +1449,7 @@ static int step_once(orc* o, double t_end, double* tphi, uint8_t* tchi, double* 
         if (tdt) *tdt = o->dt;
       }
     }
-    interface_exchange(o, Qs);
+    interface_exchange(o, Qs, o->t + rk_c(o, s) * o->dt);
     if (!replay) extend_velocity(o);
     flux_update(o, s, Qs, Qo);
     if (replay) {
@@ -1364,6 +1464,7 @@ static int step_once(orc* o, double t_end, double* tphi, uint8_t* tchi, double* 
       }
     }
     geometry(o, Qo);
+    hold_ambient(o, Qo, o->t + rk_c(o, s + 1) * o->dt);
     mixing(o, Qo);
   }
   o->t = last ? t_end : o->t + o->dt;
@@ -1407,6 +1508,9 @@ orc* orc_create(const orc_params* p) {
   if (p->rk_stages != 0 && p->rk_stages != 2 && p->rk_stages != 3) return NULL;
   for (int m = 0; m < p->nmat; m++)
     if (p->eos_kind[m] == 1 && !(p->tait_B[m] > 0.0 && p->tait_rho0[m] > 0.0)) return NULL;
+  if (p->geom != 0 && !(p->geom == 1 && p->dim == 1 && p->lo[0] >= 0.0)) return NULL;
+  if (p->fs_mat < -1 || p->fs_mat >= p->nmat) return NULL;
+  if (p->fs_mat >= 0 && !(p->fs_rho > 0.0 && p->fs_t1 > p->fs_t0)) return NULL;
   orc* o = (orc*)calloc(1, sizeof(orc));
   o->p = *p;
   /* Tait materials: the effective pinf of the sound speed and of the energy */
@@ -1540,6 +1644,7 @@ int orc_set_levelset(orc* o, const double* phi, const int32_t* chi, const double
   o->t = 0.0;
   o->dt = 0.0;
   o->err = 0;
+  hold_ambient(o, o->Q, 0.0);
   memset(o->ledger, 0, sizeof(o->ledger));
   memset(o->cnt, 0, sizeof(o->cnt));
   return 0;
@@ -1606,7 +1711,7 @@ void orc_totals(const orc* o, double* totals, double* ledger) {
     for (int v = 0; v < NV; v++) {
       double s = 0.0;
       for (long c = 0; c < o->ncell; c++)
-        if (interior_c(o, c)) s += o->Q[QI(o, m, v, c)];
+        if (interior_c(o, c)) s += cyl(o) ? o->Q[QI(o, m, v, c)] * vfac(o, c) : o->Q[QI(o, m, v, c)];
       if (totals) totals[m * NV + v] = s * o->V;
       if (ledger) ledger[m * NV + v] = o->ledger[m][v];
     }

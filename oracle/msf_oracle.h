@@ -31,6 +31,15 @@ typedef struct {
    * equation p = B (rho/rho0)^gamma - B + p0 (Sec. 2.1; gamma, tait_*) */
   int32_t eos_kind[ORC_MAXM];
   double tait_B[ORC_MAXM], tait_rho0[ORC_MAXM], tait_p0[ORC_MAXM];
+  /* 0 Cartesian; 1 axisymmetric cylindrical grid of one dimension, x = radius
+   * (Sec. 3, Case II): cell volume r_i h, face areas r_f, momentum source p/r */
+  int32_t geom;
+  /* free-surface ambient (Sec. 3, Case II): material fs_mat (-1: none) is not
+   * solved; its state is held at (fs_rho, 0, p(t)) and the interfaces of the
+   * other materials with it carry the pressure p(t) = fs_p0 for t <= fs_t0,
+   * falling linearly to fs_p1 at fs_t1, fs_p1 after */
+  int32_t fs_mat;
+  double fs_rho, fs_p0, fs_t0, fs_t1, fs_p1;
 } orc_params;
 
 typedef struct orc orc;

@@ -40,6 +40,8 @@ class Params(C.Structure):
         ("scale_eps_h", C.c_double), ("phi_cap_h", C.c_double), ("rk_stages", C.c_int32),
         ("eos_kind", C.c_int32 * MAXM), ("tait_B", C.c_double * MAXM),
         ("tait_rho0", C.c_double * MAXM), ("tait_p0", C.c_double * MAXM),
+        ("geom", C.c_int32), ("fs_mat", C.c_int32), ("fs_rho", C.c_double), ("fs_p0", C.c_double),
+        ("fs_t0", C.c_double), ("fs_t1", C.c_double), ("fs_p1", C.c_double),
     ]
 
 
@@ -105,6 +107,10 @@ def make_params(p: dict) -> Params:
         setattr(s, k, float(p[k]))
     for k in ("ext_sweeps", "vel_sweeps", "reinit_iters", "scale_sep", "reinit", "rk_stages"):
         setattr(s, k, int(p[k]))
+    s.geom = int(p.get("geom", 0))
+    s.fs_mat = int(p.get("fs_mat", -1))
+    for k in ("fs_rho", "fs_p0", "fs_t0", "fs_t1", "fs_p1"):
+        setattr(s, k, float(p.get(k, 0.0)))
     return s
 
 

@@ -46,6 +46,8 @@ class Case:
     inflow_mat: np.ndarray = None    # [3, 2]
     eos_kind: list = None            # per material: 0 stiffened gas, 1 Tait
     tait: list = None                # per material: (B, rho0, p0) of Tait's equation
+    geom: int = 0                    # 0 Cartesian, 1 cylindrical (one dimension, x = radius)
+    free_surface: tuple = None       # (material, rho, p0, t0, t1, p1): held ambient with pressure p(t)
 
     @property
     def nmat(self):
@@ -71,7 +73,10 @@ class Case:
         tait = list(self.tait) if self.tait is not None else [(0.0, 0.0, 0.0)] * self.nmat
         p = dict(dim=self.dim, n=n3, lo=lo3, hi=hi3, bc=bc3, inflow_prim=np.asarray(ip, float),
                  inflow_mat=np.asarray(im, np.int32), nmat=self.nmat, gamma=list(self.gamma),
-                 pinf=list(self.pinf), eos_kind=kind, tait=tait)
+                 pinf=list(self.pinf), eos_kind=kind, tait=tait, geom=int(self.geom))
+        fs = self.free_surface if self.free_surface is not None else (-1, 0.0, 0.0, 0.0, 0.0, 0.0)
+        p.update(fs_mat=int(fs[0]), fs_rho=float(fs[1]), fs_p0=float(fs[2]), fs_t0=float(fs[3]),
+                 fs_t1=float(fs[4]), fs_p1=float(fs[5]))
         p.update(default_options(self.dim))
         p.update(opts)
         return p
@@ -199,6 +204,26 @@ def shock_helium_water(nx=1024, ny=256, mach=6.0, x_shock=0.5):
                 [[INFLOW, TRANSMISSIVE], [REFLECTIVE] * 2], [1.4, 1.667, 7.15], [0.0, 0.0, 0.0],
                 phi, chi.reshape(ny, nx), prim, 0.3, inflow, np.zeros((3, 2), np.int32),
                 eos_kind=[0, 0, 1], tait=[(0.0, 0.0, 0.0), (0.0, 0.0, 0.0), WATER_TAIT])
+
+
+ICF_DRIVE = (13.0, 0.04, 0.125, 0.5)   # p(t): 13 up to t = 0.04, linear to 0.5 at t = 0.125 (Sec. 3.2)
+
+
+def icf_implosion(n=320, r1=0.6, r2=0.9, gamma1=5.0 / 3.0, gamma_ratio=1.0, t_end=0.3):
+    """Case II (Sec. 3.2): one-dimensional cylindrical implosion on r in [0, 1].
+    A light core (r < r1) inside a dense shell (r1 < r < r2); the ambient
+    outside r2 is not solved and presses on the shell with the drive p(t).
+    The paper takes its states from another work and prints none: core
+    (0.05, 0, 0.1), shell (1, 0, 0.1), both gamma1 = 5/3 unless gamma_ratio
+    (gamma2 / gamma1) is given; the ambient is held at density 1."""
+    (x,) = centres((n,), (0.0,), (1.0,))
+    chi = np.where(x < r1, 0, np.where(x < r2, 1, 2)).astype(np.int32)
+    phi = np.minimum(np.abs(x - r1), np.abs(x - r2))
+    p0 = ICF_DRIVE[0]
+    states = [(0.05, 0.0, 0.1), (1.0, 0.0, 0.1), (1.0, 0.0, p0)]
+    return Case("icf_implosion", 1, (n,), (0.0,), (1.0,), [[REFLECTIVE, TRANSMISSIVE]],
+                [gamma1, gamma1 * gamma_ratio, gamma1], [0.0, 0.0, 0.0], phi, chi, _uniform_prim(3, 1, n, states),
+                t_end, geom=1, free_surface=(2, 1.0) + ICF_DRIVE)
 
 
 def water_pulse(n=400, amp=1e-4):

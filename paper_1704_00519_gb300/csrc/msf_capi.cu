@@ -154,6 +154,21 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
         }
       }
     }
+    if (gr.geom != MSF_GEOM_CARTESIAN &&
+        !(gr.geom == MSF_GEOM_CYLINDRICAL && dim == 1 && gr.lo[0] >= 0.0))
+      return fail(nullptr, MSF_EINVAL, "geom: cylindrical grids have one dimension and lo >= 0");
+    if (gr.free_surface != 0) {
+      if (gr.free_surface != 1 || gr.fs_mat < 0 || gr.fs_mat >= n_mat) return fail(nullptr, MSF_EINVAL, "fs_mat");
+      const msf_eos& ef = eos[i * n_mat + gr.fs_mat];
+      const double pinf_eff = ef.kind == MSF_EOS_TAIT ? ef.tait_B - ef.tait_p0 : ef.pinf;
+      if (!(gr.fs_rho > 0.0) || !std::isfinite(gr.fs_rho) || !(gr.fs_t1 > gr.fs_t0) || !std::isfinite(gr.fs_t0) ||
+          !std::isfinite(gr.fs_t1) || !(gr.fs_p0 + pinf_eff > 0.0) || !(gr.fs_p1 + pinf_eff > 0.0) ||
+          !std::isfinite(gr.fs_p0) || !std::isfinite(gr.fs_p1))
+        return fail(nullptr, MSF_EINVAL, "free-surface ambient state or drive");
+    }
+    if ((gr.geom != MSF_GEOM_CARTESIAN || gr.free_surface != 0) && n_instances > 1 && dim == 1 &&
+        opt->batch_mode == 0)
+      return fail(nullptr, MSF_EUNSUPPORTED, "the batched form takes Cartesian grids without a free surface");
     long long cells = 1;
     for (int d = 0; d < dim; d++) cells *= (long long)(gr.n[d] + 2 * G);
     if (cells > (1LL << 31) - 1) return fail(nullptr, MSF_EINVAL, "grid too large");
@@ -263,10 +278,20 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
     if (g.rk == 2) {
       g.rk_beta[0] = 0.0; g.rk_beta[1] = 0.5; g.rk_beta[2] = 0.0;
       g.rk_lw[0] = 0.5; g.rk_lw[1] = 0.5; g.rk_lw[2] = 0.0;
+      g.rk_c[0] = 0.0; g.rk_c[1] = 1.0; g.rk_c[2] = 1.0; g.rk_c[3] = 1.0;
     } else {
       g.rk_beta[0] = 0.0; g.rk_beta[1] = 0.75; g.rk_beta[2] = 1.0 / 3.0;
       g.rk_lw[0] = 1.0 / 6.0; g.rk_lw[1] = 1.0 / 6.0; g.rk_lw[2] = 2.0 / 3.0;
+      g.rk_c[0] = 0.0; g.rk_c[1] = 1.0; g.rk_c[2] = 0.5; g.rk_c[3] = 1.0;
     }
+    // axisymmetric grid and free-surface ambient (Case II)
+    g.geom = gr.geom;
+    g.fs_mat = gr.free_surface ? gr.fs_mat : -1;
+    g.fs_rho = gr.fs_rho;
+    g.fs_p0 = gr.fs_p0;
+    g.fs_t0 = gr.fs_t0;
+    g.fs_t1 = gr.fs_t1;
+    g.fs_p1 = gr.fs_p1;
     // boundary faces, numbered per (axis, side)
     long long nb = 0;
     for (int d = 0; d < dim; d++)
@@ -425,6 +450,7 @@ static long long count_launches(const msf_ctx* c) {
     const long long vel = tiled_vel(c, g) ? 1 : g.vel_sweeps, re = 2LL * g.reinit_iters;
     const long long per_stage = 1 + ext + 1 + 1 + 1 + vel + 1 + 1 + 1 + 1 + 1 + 2 + 4;
     n += 1 + 1 + (2 + g.D) + 2 + 1 + g.rk * per_stage + 2 + 1;
+    if (g.fs_mat >= 0) n += 1 + g.rk;
     if (g.scale_sep) n += 2 + 1;
     if (g.reinit) n += re + 1;
   }
@@ -480,6 +506,7 @@ static msf_status enqueue_step(msf_ctx* c, char* tape = nullptr) {
     }
     launch_masks(g, b, s);
     launch_geometry(g, b, b.Q[0], nullptr, nb, s);
+    if (g.fs_mat >= 0) launch_hold_ambient(g, b, b.Q[0], -1, s);
     launch_band_save(g, b, nb, s);
     for (int st = 0; st < g.rk; st++) {
       const double beta = g.rk_beta[st];
@@ -506,7 +533,7 @@ static msf_status enqueue_step(msf_ctx* c, char* tape = nullptr) {
         launch_dt_finalize(g, b, s);
         if (tape) cudaMemcpyAsync(tape + sizeof(double), &b.ctl->dt, sizeof(double), cudaMemcpyDeviceToDevice, s);
       }
-      c->ops->interface(g, b, Qs, nb, s);
+      c->ops->interface(g, b, Qs, st, nb, s);
       double* V[2] = {b.vel0, b.vel1};
       uint8_t* VF[2] = {b.vf0, b.vf1};
       int vc = 0;
@@ -530,6 +557,7 @@ static msf_status enqueue_step(msf_ctx* c, char* tape = nullptr) {
       launch_bc_phichi(g, b, s);
       if (tape) tape_slot_save(in, tape, st + 1, s);
       launch_geometry(g, b, Qo, nullptr, nb, s);
+      if (g.fs_mat >= 0) launch_hold_ambient(g, b, Qo, st + 1, s);
       launch_mix(g, b, Qo, nb, s);
     }
     launch_step_end(b, s);
@@ -729,6 +757,7 @@ extern "C" msf_status msf_set_levelset(msf_ctx* c, int32_t i, const double* phi,
   launch_geometry(g, b, nullptr, b.Q[1], in.nblk_band, s);
   cudaMemsetAsync(b.Q[1], 0, sizeof(double) * N * NV * g.ncell, s);
   launch_init_state(g, b, (const double*)dprim, s);
+  if (g.fs_mat >= 0) launch_hold_ambient(g, b, b.Q[0], -2, s);
   Ctl h{};
   h.t_end = INFINITY;
   CUDA_TRY(c, cudaMemcpyAsync(b.ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
@@ -914,6 +943,8 @@ extern "C" msf_status msf_profile_read(msf_ctx* c, double* flux_ms) {
 static msf_status check_single(msf_ctx* c) {
   if (!c) return MSF_EINVAL;
   if (c->ninst != 1 || c->batched) return fail(c, MSF_EUNSUPPORTED, "tapes and the adjoint need a single-instance context");
+  if (c->inst[0].g.geom != 0 || c->inst[0].g.fs_mat >= 0)
+    return fail(c, MSF_EUNSUPPORTED, "tapes and the adjoint take Cartesian grids without a free surface");
   if (c->sticky) return fail(c, MSF_ESTATE, "context holds a device-detected error; reset with msf_set_state");
   return MSF_OK;
 }
@@ -959,6 +990,7 @@ static bool tape_aligned(const void* p) { return ((uintptr_t)p & 255u) == 0; }
 extern "C" msf_status msf_tape_bytes(const msf_ctx* c, int64_t* bytes) {
   if (!c || !bytes) return MSF_EINVAL;
   if (c->ninst != 1 || c->batched) return MSF_EUNSUPPORTED;
+  if (c->inst[0].g.geom != 0 || c->inst[0].g.fs_mat >= 0) return MSF_EUNSUPPORTED;
   *bytes = (int64_t)tape_layout(c->inst[0].g).total;
   return MSF_OK;
 }
@@ -1008,7 +1040,7 @@ static void enqueue_replay(msf_ctx* c, const char* tape, bool rec) {
     }
     c->ops->cons(g, b, Qs, W[cur], F[cur], nb, s);
     c->ops->bc_uhat(g, b, Qs, s);
-    c->ops->interface(g, b, Qs, nb, s);
+    c->ops->interface(g, b, Qs, st, nb, s);
     c->ops->flux(g, b, Qs, b.Q[0], Qo, g.rk_beta[st], 1.0 - g.rk_beta[st], in.bb, s);
     launch_ledger(g, b, in.nbnd, g.rk_lw[st], s);
     tape_slot_load(in, tape, st + 1, s);
@@ -1109,7 +1141,7 @@ extern "C" msf_status msf_adjoint_step(msf_ctx* c, const void* tape_, const doub
     }
     c->ops->cons(g, b, Qs, W[cur], F[cur], nb, s);
     c->ops->bc_uhat(g, b, Qs, s);
-    c->ops->interface(g, b, Qs, nb, s);
+    c->ops->interface(g, b, Qs, sg, nb, s);
     // reverse: mixing, fluxes and exchange, boundary states, stencil states,
     // extension sweeps, primitive recovery, RK combination
     cudaMemsetAsync(a.LU, 0, qbytes, s);

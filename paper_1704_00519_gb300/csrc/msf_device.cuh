@@ -30,6 +30,10 @@ struct Grid {
   int n[3], pn[3], off[3];
   long long st[3], ncell;
   double lo[3], h[3], rh[3], rh2[3], ih2[3], farea[3], V, rV, hmin, eps_ss, cap;
+  int geom;    // 1: cylindrical grid of one dimension (x = radius)
+  int fs_mat;  // held free-surface ambient, -1: none
+  double fs_rho, fs_p0, fs_t0, fs_t1, fs_p1;
+  double rk_c[4];  // time of stage s as a fraction of the step (s = rk: the step's end)
   double gamma[MAXM], pinf[MAXM], gm1[MAXM], gpi[MAXM];
   // Tait's equation per material (eos_kind 1): p = B (rho/rho0)^gamma - B + p0;
   // pinf holds B - p0 (sound speed and energy of the equivalent stiffened gas)
@@ -141,6 +145,31 @@ __device__ inline T sound(const Grid& g, int m, T rho, T p, unsigned* err) {
     c2 = c2 > T(0) ? c2 : T(0);
   }
   return sqrt(c2);
+}
+
+// -------------------------- axisymmetric grid and free surface (Sec. 3, Case II)
+// A cylindrical grid of one dimension takes x as the radius: cell i has volume
+// r_i h and its faces the areas r_f (per radian and unit length).
+__device__ inline double face_r(const Grid& g, int i) { return g.lo[0] + (double)(i - g.off[0]) * g.h[0]; }
+__device__ inline double cell_r(const Grid& g, int i) { return g.lo[0] + ((double)(i - g.off[0]) + 0.5) * g.h[0]; }
+// volume of cell c over the Cartesian cell volume (1 on Cartesian grids)
+__device__ inline double vfac(const Grid& g, long long c) { return g.geom == 1 ? cell_r(g, (int)(c % g.pn[0])) : 1.0; }
+// pressure of the free-surface ambient at time t: fs_p0 up to fs_t0, linear to
+// fs_p1 at fs_t1, fs_p1 after
+__device__ inline double fs_pressure(const Grid& g, double t) {
+  if (t <= g.fs_t0) return g.fs_p0;
+  if (t >= g.fs_t1) return g.fs_p1;
+  return g.fs_p0 - (g.fs_p0 - g.fs_p1) * (t - g.fs_t0) / (g.fs_t1 - g.fs_t0);
+}
+// velocity jump across the wave of material m at (rho, pK) that takes its
+// pressure to p, on the two-shock approximation of the Riemann problem
+// (Toro, Riemann Solvers, Sec. 9.4.2): (p - pK) sqrt(A / (p + pinf + B)),
+// A = 2 / ((gamma + 1) rho), B = (gamma - 1) / (gamma + 1) (pK + pinf)
+template <typename T>
+__device__ inline T fs_wave(const Grid& g, int m, T rho, T pK, T p) {
+  const T ga = (T)g.gamma[m], pi = (T)g.pinf[m];
+  const T A = T(2) / ((ga + T(1)) * rho), B = (ga - T(1)) / (ga + T(1)) * (pK + pi);
+  return (p - pK) * sqrt(A / (p + pi + B));
 }
 
 // ---------------------------------------------------------------- WENO5-JS

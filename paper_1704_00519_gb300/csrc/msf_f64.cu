@@ -225,6 +225,9 @@ void launch_init_levelset(const Grid& g, const Bufs& b, const double* phi_in, co
 void launch_init_mass(const Grid& g, const Bufs& b, const double* prim_in, double* mass, cudaStream_t s) {
   k_init_mass<<<grid_blocks(g.n_interior), NTHREADS, 0, s>>>(g, b, prim_in, mass);
 }
+void launch_hold_ambient(const Grid& g, const Bufs& b, double* Qc, int k, cudaStream_t s) {
+  k_hold_ambient<<<grid_blocks(g.n_interior), NTHREADS, 0, s>>>(g, b, Qc, k);
+}
 void launch_init_state(const Grid& g, const Bufs& b, const double* prim_in, cudaStream_t s) {
   k_init_state<<<grid_blocks(g.n_interior), NTHREADS, 0, s>>>(g, b, prim_in);
 }

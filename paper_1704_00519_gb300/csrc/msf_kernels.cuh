@@ -545,7 +545,7 @@ __device__ __forceinline__ double dt_items(const Grid& g, const Bufs& b, const d
     const long long c = interior_cell(g, idx);
     const bool inb = b.bandidx[c] >= 0;
     for (int m = 0; m < N; m++) {
-      if (inb ? !(b.alpha[midx(g, m, c)] > 0.0) : b.chi[c] != m) continue;
+      if ((inb ? !(b.alpha[midx(g, m, c)] > 0.0) : b.chi[c] != m) || m == g.fs_mat) continue;
       T u[5], w[5];
       interior_uhat<T>(g, b, Qs, c, m, u);
       cons_to_prim<T>(g, m, D, u, w);
@@ -603,8 +603,10 @@ __global__ void k_step_end(const __grid_constant__ Bufs b) {
 
 // ----------------------------------------- reduced interface interaction (a7)
 template <typename T>
-__device__ __forceinline__ void phase_interface(const Grid& g, const Bufs& b, const double* Qs, int first_, int stride_) {
+__device__ __forceinline__ void phase_interface(const Grid& g, const Bufs& b, const double* Qs, int stage, int first_,
+                                                int stride_) {
     const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
+  const double ts = b.ctl->t + g.rk_c[stage] * b.ctl->dt;  // time of the stage
   const T* Uh = (const T*)b.Uh;
   unsigned err = 0;
   unsigned long long ncut = 0;
@@ -649,14 +651,35 @@ __device__ __forceinline__ void phase_interface(const Grid& g, const Bufs& b, co
       unr += wR[1 + d] * (T)n[d];
     }
     T us, ps;
-    hllc_star<T>(wL[0], unl, wL[D + 1], (T)g.gamma[L], (T)g.pinf[L], wR[0], unr, wR[D + 1], (T)g.gamma[R],
-                 (T)g.pinf[R], &us, &ps, g.eos_kind[L] == 1, g.eos_kind[R] == 1);
+    const int FS = g.fs_mat;
+    if (FS >= 0 && (L == FS || R == FS)) {
+      // free surface: the ambient imposes p* = p(t); the solved side's
+      // two-shock wave curve gives u*
+      ps = (T)fs_pressure(g, ts);
+      if (R == FS) {
+        (void)sound<T>(g, L, wL[0], wL[D + 1], &err);
+        us = unl - fs_wave<T>(g, L, wL[0], wL[D + 1], ps);
+      } else {
+        (void)sound<T>(g, R, wR[0], wR[D + 1], &err);
+        us = unr + fs_wave<T>(g, R, wR[0], wR[D + 1], ps);
+      }
+    } else {
+      hllc_star<T>(wL[0], unl, wL[D + 1], (T)g.gamma[L], (T)g.pinf[L], wR[0], unr, wR[D + 1], (T)g.gamma[R],
+                   (T)g.pinf[R], &us, &ps, g.eos_kind[L] == 1, g.eos_kind[R] == 1);
+    }
     const double psd = (double)ps, usd = (double)us;
     double XR[5] = {0, 0, 0, 0, 0};
     for (int m = 0; m < N; m++) {
       if (m == R || !present(g, b, c, m)) continue;
       double S[3] = {0, 0, 0}, nS = 0.0;
-      for (int d = 0; d < D; d++) S[d] = (b.Ahi[aidx(g, d, m, c)] - b.Alo[aidx(g, d, m, c)]) * g.farea[d];
+      if (g.geom == 1) {
+        // interface area r_I n: the faces' r_f A_f less the wedge side alpha h
+        const int ic = (int)(c % g.pn[0]);
+        S[0] = b.Ahi[aidx(g, 0, m, c)] * face_r(g, ic + 1) - b.Alo[aidx(g, 0, m, c)] * face_r(g, ic) -
+               b.alpha[midx(g, m, c)] * g.h[0];
+      } else {
+        for (int d = 0; d < D; d++) S[d] = (b.Ahi[aidx(g, d, m, c)] - b.Alo[aidx(g, d, m, c)]) * g.farea[d];
+      }
       for (int d = 0; d < D; d++) nS += n[d] * S[d];
       for (int d = 0; d < D; d++) {
         b.X[qidx(g, m, 1 + d, c)] = psd * S[d];
@@ -672,9 +695,9 @@ __device__ __forceinline__ void phase_interface(const Grid& g, const Bufs& b, co
   if (err) atomicOr(&b.ctl->err, err);
 }
 template <typename T>
-__global__ void k_interface(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
+__global__ void k_interface(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs, int stage) {
   if (!ctl_active(b)) return;
-  phase_interface<T>(g, b, Qs, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  phase_interface<T>(g, b, Qs, stage, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // one sweep of the interface-velocity extension into the band
@@ -889,7 +912,7 @@ __device__ inline void flux_face(const Grid& g, const Bufs& b, const T* U, const
   if (exists) {
     const long long cR = cell_at(g, gx, gy, gz), cL = cR - g.st[DIR];
     Af = anyband ? face_aperture(g, b, cL, cR, DIR, m) : 1.0;
-    if (Af > 0.0) {
+    if (Af > 0.0 && m != g.fs_mat) {
       if (anyband) {
         const bool lin = qd - 1 >= g.off[DIR], rin = qd < g.off[DIR] + g.n[DIR];
         if ((lin && !((b.smask[cL] >> m) & 1u)) || (rin && !((b.smask[cR] >> m) & 1u))) err |= ERR_BAND;
@@ -924,8 +947,9 @@ __device__ inline void flux_face(const Grid& g, const Bufs& b, const T* U, const
       }
       const long long fid = (rr == 0 ? bb.base[2 * DIR] : bb.base[2 * DIR + 1]) + lin_id;
       const double sgn = rr == 0 ? 1.0 : -1.0;
+      const double fa = (D == 1 && g.geom == 1) ? face_r(g, qd) : g.farea[DIR];
 #pragma unroll
-      for (int v = 0; v < NV; v++) b.bflux[((fid * g.N) + m) * NV + v] = sgn * (Af * (double)Fh[v] * g.farea[DIR]);
+      for (int v = 0; v < NV; v++) b.bflux[((fid * g.N) + m) * NV + v] = sgn * (Af * (double)Fh[v] * fa);
     }
   }
   A[f] = Af;
@@ -1074,7 +1098,7 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
     // exactly +0 and L = 0; the face evaluation is skipped and the update
     // below runs with L = 0, giving the same bits as the full evaluation.
     bool idle = false;
-    if (!anyband && interior_tile) idle = __syncthreads_and(stencil_uniform<D, T>(U, bad, tid)) != 0;
+    if (!anyband && interior_tile && g.geom == 0) idle = __syncthreads_and(stencil_uniform<D, T>(U, bad, tid)) != 0;
     // face apertures and fluxes: x faces, then y, then z
     if (!idle)
       for (int f = tid; f < S::NF; f += blockDim.x) {
@@ -1100,17 +1124,36 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
         flo[2] = S::NFX + S::NFY + tx + TX * (ty + TY * tz);
         fhi[2] = flo[2] + TX * TY;
       }
+      // cylindrical grid: faces weighted by their radii, volume r_i h, and the
+      // source p alpha / r_i of the radial momentum (the stage's stencil state)
+      const bool cyl = D == 1 && g.geom == 1;
+      double rlo = 0.0, rhi = 0.0, rvc = 0.0, psrc = 0.0;
+      if (cyl) {
+        const double rc = cell_r(g, cx), a = alpha_of(g, b, c, m);
+        rlo = face_r(g, cx);
+        rhi = face_r(g, cx + 1);
+        rvc = 1.0 / (rc * g.h[0]);
+        if (a > 0.0) psrc = (double)P[D * NS + (tx + 3) + SX * ((ty + S::HY) + SY * (tz + S::HZ))] * a / rc;
+      }
 #pragma unroll
       for (int v = 0; v < NV; v++) {
         double L = 0.0;
-        if (!idle) {
+        if (cyl) {
+          const double fl = (double)F[v * S::NF + flo[0]], fh = (double)F[v * S::NF + fhi[0]];
+          L = (A[flo[0]] * fl * rlo - A[fhi[0]] * fh * rhi) * rvc;
+          if (cut) L = L + b.X[qidx(g, m, v, c)] * rvc;
+          if (v == 1) L = L + psrc;
+        } else {
+          if (!idle) {
 #pragma unroll
-          for (int d = 0; d < D; d++) {
-            const double fl = (double)F[v * S::NF + flo[d]], fh = (double)F[v * S::NF + fhi[d]];
-            L = L + (A[flo[d]] * fl - A[fhi[d]] * fh) * g.rh[d];
+            for (int d = 0; d < D; d++) {
+              const double fl = (double)F[v * S::NF + flo[d]], fh = (double)F[v * S::NF + fhi[d]];
+              L = L + (A[flo[d]] * fl - A[fhi[d]] * fh) * g.rh[d];
+            }
           }
+          if (cut) L = L + b.X[qidx(g, m, v, c)] * g.rV;
         }
-        if (cut) L = L + b.X[qidx(g, m, v, c)] * g.rV;
+        if (m == g.fs_mat) L = 0.0;  // the ambient is not solved
         const long long qi = qidx(g, m, v, c);
         const double qn = Qn[qi], qs = Qs[qi];
         const double qv = beta * qn + omb * (qs + dt * L);
@@ -1379,10 +1422,12 @@ __global__ void k_mix_mark(const __grid_constant__ Grid g, const __grid_constant
   phase_mix_mark(g, b, Qc, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
-// Weight sum T of every (band cell, material). A pair exchange
-// M = beta (a_s Q_t - a_t Q_s) / (a_s + a_t) moves the small cell's
-// per-volume state towards the target's with weight beta a_t / (a_s + a_t)
-// and the target's towards the small cell's with weight beta a_s / (a_s + a_t).
+// Weight sum T of every (band cell, material). With cell volumes V (unit on
+// Cartesian grids, r on a cylindrical one) a pair moves the content
+// C = beta V_s V_t (a_s Q_t - a_t Q_s) / (a_s V_s + a_t V_t): the small cell's
+// per-volume state moves towards the target's with weight
+// beta a_t V_t / (a_s V_s + a_t V_t) and the target's towards the small
+// cell's with weight beta a_s V_s / (a_s V_s + a_t V_t).
 // T sums a cell's weights: its own pairs in target order, then the pairs of
 // the neighbours that mix into it in (z, y, x) offset order.
 __device__ __forceinline__ void phase_mix_weights(const Grid& g, const Bufs& b, int first_, int stride_) {
@@ -1394,12 +1439,12 @@ __device__ __forceinline__ void phase_mix_weights(const Grid& g, const Bufs& b, 
     const long long r = (long long)k * N + m;
     double T = 0.0;
     if ((b.smask[c] >> m) & 1u) {
-      const double ac = b.alpha[midx(g, m, c)];
+      const double ac = b.alpha[midx(g, m, c)], vc = vfac(g, c);
       const int nown = b.mixn[r];
       for (int t = 0; t < (nown == 0xff ? 0 : nown); t++) {
         const long long tc = off_cell(g, c, b.mixoff[r * MIX_MAXT + t]);
-        const double at = b.alpha[midx(g, m, tc)];
-        T += b.mixbeta[r * MIX_MAXT + t] * at / (ac + at);
+        const double at = b.alpha[midx(g, m, tc)], vt = vfac(g, tc);
+        T += b.mixbeta[r * MIX_MAXT + t] * (at * vt) / (ac * vc + at * vt);
       }
       const unsigned inbits = b.mixin[r];
       if (inbits) {
@@ -1422,8 +1467,8 @@ __device__ __forceinline__ void phase_mix_weights(const Grid& g, const Bufs& b, 
               if (ns == 0xff) continue;
               for (int t = 0; t < ns; t++) {
                 if (b.mixoff[rs * MIX_MAXT + t] != code) continue;
-                const double as = b.alpha[midx(g, m, s)];
-                T += b.mixbeta[rs * MIX_MAXT + t] * as / (as + ac);
+                const double as = b.alpha[midx(g, m, s)], vs = vfac(g, s);
+                T += b.mixbeta[rs * MIX_MAXT + t] * (as * vs) / (as * vs + ac * vc);
               }
             }
       }
@@ -1471,14 +1516,14 @@ __device__ __forceinline__ void phase_mix_compute(const Grid& g, const Bufs& b, 
     if (nown != 0xff) {
       const double as = b.alpha[midx(g, m, c)];
       if (nown == 0 && as == 0.0 && m != b.chi[c]) atomicOr(&b.mixmerge[k], 1u << m);
-      const double Tc = b.mixT[r];
+      const double Tc = b.mixT[r], vs = vfac(g, c);
       for (int t = 0; t < (nown == 0xff ? 0 : nown); t++) {
         const long long tc = off_cell(g, c, b.mixoff[r * MIX_MAXT + t]);
         const double beta = b.mixbeta[r * MIX_MAXT + t];
-        const double at = b.alpha[midx(g, m, tc)];
+        const double at = b.alpha[midx(g, m, tc)], vt = vfac(g, tc);
         const double f = mix_limit(as, Tc, b.mixT[(long long)b.bandidx[tc] * N + m]);
         for (int v = 0; v < NV; v++)
-          acc[v] += f * (beta * (as * Qc[qidx(g, m, v, tc)] - at * Qc[qidx(g, m, v, c)]) / (as + at));
+          acc[v] += f * ((beta * (as * Qc[qidx(g, m, v, tc)] - at * Qc[qidx(g, m, v, c)]) / (as * vs + at * vt)) * vt);
       }
     }
     // neighbours that mix into this cell (bits set by the marking pass)
@@ -1501,11 +1546,11 @@ __device__ __forceinline__ void phase_mix_compute(const Grid& g, const Bufs& b, 
           for (int t = 0; t < ns; t++) {
             if (b.mixoff[rs * MIX_MAXT + t] != code) continue;
             const double beta = b.mixbeta[rs * MIX_MAXT + t];
-            const double as = b.alpha[midx(g, m, s)];
-            const double at = b.alpha[midx(g, m, c)];
+            const double as = b.alpha[midx(g, m, s)], vs = vfac(g, s);
+            const double at = b.alpha[midx(g, m, c)], vt = vfac(g, c);
             const double f = mix_limit(as, b.mixT[rs], b.mixT[r]);
             for (int v = 0; v < NV; v++)
-              acc[v] -= f * (beta * (as * Qc[qidx(g, m, v, c)] - at * Qc[qidx(g, m, v, s)]) / (as + at));
+              acc[v] -= f * ((beta * (as * Qc[qidx(g, m, v, c)] - at * Qc[qidx(g, m, v, s)]) / (as * vs + at * vt)) * vs);
           }
         }
     for (int v = 0; v < NV; v++) out[v] = Qc[qidx(g, m, v, c)] + acc[v];
@@ -1687,7 +1732,8 @@ __global__ void k_totals(const __grid_constant__ Grid g, const double* Q, double
   const int m = mv / g.NV, v = mv % g.NV;
   double s = 0.0;
   for (long long idx = threadIdx.x; idx < g.n_interior; idx += blockDim.x) {
-    s += Q[qidx(g, m, v, interior_cell(g, idx))];
+    const long long c = interior_cell(g, idx);
+    s += g.geom == 1 ? Q[qidx(g, m, v, c)] * vfac(g, c) : Q[qidx(g, m, v, c)];
   }
   __shared__ double red[NTHREADS];
   red[threadIdx.x] = s;
@@ -1697,6 +1743,25 @@ __global__ void k_totals(const __grid_constant__ Grid g, const double* Q, double
     __syncthreads();
   }
   if (threadIdx.x == 0) out[mv] = red[0] * g.V;
+}
+
+// The free-surface ambient is not solved: its conserved state is
+// alpha (fs_rho, 0, p(t)) with t = 0 (k = -2), the step's start (k = -1) or
+// the time of stage k of the step.
+__global__ void k_hold_ambient(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, double* Qc, int k) {
+  if (k >= -1 && !ctl_active(b)) return;
+  const int F = g.fs_mat;
+  const double t = k == -2 ? 0.0 : (k == -1 ? b.ctl->t : b.ctl->t + g.rk_c[k] * b.ctl->dt);
+  double w[5] = {0, 0, 0, 0, 0}, u[5];
+  w[0] = g.fs_rho;
+  w[g.D + 1] = fs_pressure(g, t);
+  prim_to_cons<double>(g, F, g.D, w, u);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.n_interior;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long c = interior_cell(g, idx);
+    const double a = alpha_of(g, b, c, F);
+    for (int v = 0; v < g.NV; v++) Qc[qidx(g, F, v, c)] = a * u[v];
+  }
 }
 
 
@@ -1857,7 +1922,7 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
         }
         __syncthreads();
       }
-      phase_interface<T>(g, b, Qs, t, nt);
+      phase_interface<T>(g, b, Qs, s, t, nt);
       __syncthreads();
       int vc = 0;
       for (int k = 0; k < g.vel_sweeps; k++) {

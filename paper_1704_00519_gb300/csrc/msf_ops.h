@@ -17,7 +17,7 @@ struct Ops {
   void (*cons)(const Grid&, const Bufs&, const double* Qs, const void* W, const uint8_t* f, int nblk, cudaStream_t);
   void (*bc_uhat)(const Grid&, const Bufs&, const double* Qs, cudaStream_t);
   void (*dt)(const Grid&, const Bufs&, const double* Qs, cudaStream_t);
-  void (*interface)(const Grid&, const Bufs&, const double* Qs, int nblk, cudaStream_t);
+  void (*interface)(const Grid&, const Bufs&, const double* Qs, int stage, int nblk, cudaStream_t);
   cudaError_t (*flux)(const Grid&, const Bufs&, const double* Qs, const double* Qn, double* Qout, double beta,
                       double omb, const BndBase&, cudaStream_t);
   // n_steps steps of every 1D instance of a batch, one CTA of bs threads per instance
@@ -48,6 +48,9 @@ void launch_totals(const Grid&, const double* Q, double* out, cudaStream_t);
 void launch_init_levelset(const Grid&, const Bufs&, const double* phi_in, const int32_t* chi_in, cudaStream_t);
 void launch_init_mass(const Grid&, const Bufs&, const double* prim_in, double* mass, cudaStream_t);
 void launch_init_state(const Grid&, const Bufs&, const double* prim_in, cudaStream_t);
+// free-surface ambient held at alpha (fs_rho, 0, p(t)): k = -2 at t = 0, -1 at
+// the step's start, k >= 0 at the time of stage k
+void launch_hold_ambient(const Grid&, const Bufs&, double* Qc, int k, cudaStream_t);
 void launch_gather(const Grid&, const Bufs&, int which, double* out, int32_t* iout, cudaStream_t);
 void launch_scatter_state(const Grid&, const Bufs&, const double* Q, const double* phi, const int32_t* chi,
                           cudaStream_t);

@@ -32,7 +32,9 @@ COUNTERS = ["cut", "multi", "corrected", "small", "mixfail", "merge", "oddball",
 class msf_grid(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("bc", (C.c_int32 * 2) * 3), ("inflow_prim", ((C.c_double * 5) * 2) * 3),
-                ("inflow_mat", (C.c_int32 * 2) * 3)]
+                ("inflow_mat", (C.c_int32 * 2) * 3), ("geom", C.c_int32), ("free_surface", C.c_int32),
+                ("fs_mat", C.c_int32), ("fs_rho", C.c_double), ("fs_p0", C.c_double), ("fs_t0", C.c_double),
+                ("fs_t1", C.c_double), ("fs_p1", C.c_double)]
 
 
 class msf_eos(C.Structure):
@@ -149,6 +151,12 @@ def make_grid(p: dict) -> msf_grid:
             g.inflow_mat[d][s] = int(p["inflow_mat"][d][s])
             for v in range(5):
                 g.inflow_prim[d][s][v] = float(p["inflow_prim"][d][s][v])
+    g.geom = int(p.get("geom", 0))
+    fs = int(p.get("fs_mat", -1))
+    g.free_surface = 1 if fs >= 0 else 0
+    g.fs_mat = max(fs, 0)
+    for k in ("fs_rho", "fs_p0", "fs_t0", "fs_t1", "fs_p1"):
+        setattr(g, k, float(p.get(k, 0.0)))
     return g
 
 
