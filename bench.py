@@ -179,6 +179,34 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def icf_rates(msf, torch, stream, K):
+    """Case II's shell-thickness study (Sec. 3.2) as one batched launch: 256
+    cylindrical implosions of 1280 cells (r2 - r1 in [0.05, 0.3]) driven by the
+    free-surface pressure p(t), FP64 and FP32-bulk, device-timed over K steps
+    after 5 warm-up steps."""
+    import paper_1704_00519_gb300.cases as cs
+    cases = cs.icf_shell_study(1280, 256)
+    out = {"workload": "icf_shell_study_256x1280", "cells": int(sum(c.cells for c in cases)),
+           "instances": len(cases), "steps": K}
+    for key, prec in (("fp32", msf.MSF_FP32_BULK), ("fp64", msf.MSF_FP64)):
+        b = msf.Batch(cases, precision=prec, stream=stream)
+        b.step(5, 1.0, sync=False)
+        before = [b.info(i)[1] for i in range(len(cases))]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        b.step(K, 1.0, sync=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        info = [b.info(i) for i in range(len(cases))]
+        work = sum(c.cells * 3 * (info[i][1] - before[i]) for i, c in enumerate(cases))
+        out[key] = {"value": work / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K,
+                    "instances_with_device_error": sum(1 for x in info if x[2] != 0)}
+        b.close()
+    return out
+
+
 def batched_rates(msf, torch, stream, K_persistent, K_sequence):
     """256 seeded 1D multi-material Riemann problems (FP32-bulk): one
     persistent launch per call (one CTA per instance, autotuned CTA size)
@@ -422,6 +450,7 @@ def run_gpu(args):
 
     launches = s32.launches_per_step() * K
     batched = batched_rates(msf, torch, sptr, max(K, 10), 3)
+    icf = icf_rates(msf, torch, sptr, 50)
     s32.close()
     s64.close()
     se.close()
@@ -461,6 +490,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "batched_1d": batched,
+        "icf_shell_study": icf,
         "triple_point_from_t_0.3": later,
         "workloads": workloads,
         "adjoint": adjoint,

@@ -64,10 +64,9 @@ typedef enum { MSF_FP64 = 0, MSF_FP32_BULK = 1 } msf_precision;
  *                pressure p(t) = fs_p0 for t <= fs_t0, falling linearly to
  *                fs_p1 at fs_t1 and fs_p1 after; the interface velocity comes
  *                from the two-shock wave curve of the solved side. Requires
- *                fs_rho > 0 and fs_t1 > fs_t0. The batched form (n_instances > 1,
- *                dim 1, batch_mode 0) and the tape and adjoint entry points
+ *                fs_rho > 0 and fs_t1 > fs_t0. The tape and adjoint entry points
  *                refuse a grid with geom != 0 or free_surface != 0
- *                (MSF_EUNSUPPORTED); batch_mode 1 steps such instances. */
+ *                (MSF_EUNSUPPORTED). */
 typedef struct {
   int32_t dim;
   int32_t n[3];

@@ -743,6 +743,15 @@ static void compute_dt(orc* o, double t_end) {
       if (s > lam) lam = s;
     }
   }
+  /* a free surface moves at the u* of its wave curve, which the material
+     states do not bound: its cut cells enter the bound with |u*| */
+  if (o->p.fs_mat >= 0)
+    for (long c = 0; c < o->ncell; c++) {
+      if (!o->cut[c] || !(o->alpha[MI(o, o->p.fs_mat, c)] > 0.0)) continue;
+      double s = 0.0;
+      for (int d = 0; d < D; d++) s += fabs(o->vel[d * o->ncell + c]) * o->rh[d];
+      if (s > lam) lam = s;
+    }
   double dt = o->p.cfl / lam;
   if (o->t + dt >= t_end) dt = t_end - o->t;
   o->dt = dt;
@@ -1440,6 +1449,9 @@ static int step_once(orc* o, double t_end, double* tphi, uint8_t* tchi, double* 
     double* Qo = s == o->S - 1 ? o->Q : (s == 0 ? o->Q1 : o->Q2);
     prim_extend(o, Qs);
     bc_uhat(o);
+    /* the exchange of stage 0 comes first: the bound of the step reads the
+       free-surface velocities it sets */
+    interface_exchange(o, Qs, s == 0 ? o->t : o->t + rk_c(o, s) * o->dt);
     if (s == 0) {
       if (replay) {
         o->dt = *tdt;
@@ -1449,7 +1461,6 @@ static int step_once(orc* o, double t_end, double* tphi, uint8_t* tchi, double* 
         if (tdt) *tdt = o->dt;
       }
     }
-    interface_exchange(o, Qs, o->t + rk_c(o, s) * o->dt);
     if (!replay) extend_velocity(o);
     flux_update(o, s, Qs, Qo);
     if (replay) {

@@ -226,6 +226,28 @@ def icf_implosion(n=320, r1=0.6, r2=0.9, gamma1=5.0 / 3.0, gamma_ratio=1.0, t_en
                 t_end, geom=1, free_surface=(2, 1.0) + ICF_DRIVE)
 
 
+def icf_quarter_plane(n=64, r1=0.6, r2=0.9, t_end=0.1):
+    """Case II's states on a two-dimensional Cartesian quarter plane [0, 1]^2
+    (walls on the axes, transmissive outer sides): the same implosion without
+    the axisymmetric metric, for cross-checks."""
+    x, y = centres((n, n), (0.0, 0.0), (1.0, 1.0))
+    r = np.sqrt(x ** 2 + y ** 2)
+    chi = np.where(r < r1, 0, np.where(r < r2, 1, 2)).astype(np.int32)
+    phi = np.minimum(np.abs(r - r1), np.abs(r - r2))
+    states = [(0.05, 0.0, 0.0, 0.1), (1.0, 0.0, 0.0, 0.1), (1.0, 0.0, 0.0, ICF_DRIVE[0])]
+    g = 5.0 / 3.0
+    return Case("icf_quarter_plane", 2, (n, n), (0.0, 0.0), (1.0, 1.0),
+                [[REFLECTIVE, TRANSMISSIVE], [REFLECTIVE, TRANSMISSIVE]], [g, g, g], [0.0, 0.0, 0.0],
+                phi, chi, _uniform_prim(3, 2, n * n, states), t_end, free_surface=(2, 1.0) + ICF_DRIVE)
+
+
+def icf_shell_study(n=1280, count=256, t_end=0.3):
+    """Case II's study of the shell thickness (Sec. 3.2): instances with
+    r2 - r1 spread over [0.05, 0.3] (r1 = 0.6, gamma2 / gamma1 = 1)."""
+    return [icf_implosion(n, r1=0.6, r2=0.6 + 0.05 + 0.25 * k / max(count - 1, 1), t_end=t_end)
+            for k in range(count)]
+
+
 def water_pulse(n=400, amp=1e-4):
     """One-dimensional water at rest (Tait's equation) with a small Gaussian
     density pulse and the matching Tait pressure: linear acoustics."""

@@ -166,9 +166,6 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
           !std::isfinite(gr.fs_p0) || !std::isfinite(gr.fs_p1))
         return fail(nullptr, MSF_EINVAL, "free-surface ambient state or drive");
     }
-    if ((gr.geom != MSF_GEOM_CARTESIAN || gr.free_surface != 0) && n_instances > 1 && dim == 1 &&
-        opt->batch_mode == 0)
-      return fail(nullptr, MSF_EUNSUPPORTED, "the batched form takes Cartesian grids without a free surface");
     long long cells = 1;
     for (int d = 0; d < dim; d++) cells *= (long long)(gr.n[d] + 2 * G);
     if (cells > (1LL << 31) - 1) return fail(nullptr, MSF_EINVAL, "grid too large");
@@ -528,12 +525,14 @@ static msf_status enqueue_step(msf_ctx* c, char* tape = nullptr) {
       }
       c->ops->cons(g, b, Qs, W[cur], F[cur], nb, s);
       c->ops->bc_uhat(g, b, Qs, s);
+      // the exchange of stage 0 comes first: the bound of the step reads the
+      // free-surface velocities it sets
+      c->ops->interface(g, b, Qs, st, nb, s);
       if (st == 0) {
         c->ops->dt(g, b, Qs, s);
         launch_dt_finalize(g, b, s);
         if (tape) cudaMemcpyAsync(tape + sizeof(double), &b.ctl->dt, sizeof(double), cudaMemcpyDeviceToDevice, s);
       }
-      c->ops->interface(g, b, Qs, st, nb, s);
       double* V[2] = {b.vel0, b.vel1};
       uint8_t* VF[2] = {b.vf0, b.vf1};
       int vc = 0;

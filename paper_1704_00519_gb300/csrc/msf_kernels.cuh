@@ -554,6 +554,13 @@ __device__ __forceinline__ double dt_items(const Grid& g, const Bufs& b, const d
       for (int d = 0; d < D; d++) s += (fabs(w[1 + d]) + cs) * (T)g.rh[d];
       if ((double)s > lam) lam = (double)s;
     }
+    // a free surface moves at the u* of its wave curve, which the material
+    // states do not bound: its cut cells enter the bound with |u*|
+    if (g.fs_mat >= 0 && inb && (b.gflag[c] & GF_CUT) && b.alpha[midx(g, g.fs_mat, c)] > 0.0) {
+      double s = 0.0;
+      for (int d = 0; d < D; d++) s += fabs(b.vel0[d * g.ncell + c]) * g.rh[d];
+      if (s > lam) lam = s;
+    }
   }
   return lam;
 }
@@ -606,7 +613,7 @@ template <typename T>
 __device__ __forceinline__ void phase_interface(const Grid& g, const Bufs& b, const double* Qs, int stage, int first_,
                                                 int stride_) {
     const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
-  const double ts = b.ctl->t + g.rk_c[stage] * b.ctl->dt;  // time of the stage
+  const double ts = stage == 0 ? b.ctl->t : b.ctl->t + g.rk_c[stage] * b.ctl->dt;  // time of the stage
   const T* Uh = (const T*)b.Uh;
   unsigned err = 0;
   unsigned long long ncut = 0;
@@ -1748,20 +1755,24 @@ __global__ void k_totals(const __grid_constant__ Grid g, const double* Q, double
 // The free-surface ambient is not solved: its conserved state is
 // alpha (fs_rho, 0, p(t)) with t = 0 (k = -2), the step's start (k = -1) or
 // the time of stage k of the step.
-__global__ void k_hold_ambient(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, double* Qc, int k) {
-  if (k >= -1 && !ctl_active(b)) return;
+__device__ __forceinline__ void phase_hold(const Grid& g, const Bufs& b, double* Qc, int k, long long first,
+                                           long long stride) {
   const int F = g.fs_mat;
+  if (F < 0) return;
   const double t = k == -2 ? 0.0 : (k == -1 ? b.ctl->t : b.ctl->t + g.rk_c[k] * b.ctl->dt);
   double w[5] = {0, 0, 0, 0, 0}, u[5];
   w[0] = g.fs_rho;
   w[g.D + 1] = fs_pressure(g, t);
   prim_to_cons<double>(g, F, g.D, w, u);
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.n_interior;
-       idx += (long long)gridDim.x * blockDim.x) {
+  for (long long idx = first; idx < g.n_interior; idx += stride) {
     const long long c = interior_cell(g, idx);
     const double a = alpha_of(g, b, c, F);
     for (int v = 0; v < g.NV; v++) Qc[qidx(g, F, v, c)] = a * u[v];
   }
+}
+__global__ void k_hold_ambient(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, double* Qc, int k) {
+  if (k >= -1 && !ctl_active(b)) return;
+  phase_hold(g, b, Qc, k, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 
@@ -1787,7 +1798,7 @@ __device__ __forceinline__ void flux1d_faces(const Grid& g, const Bufs& b, const
     T Fh[NV] = {T(0), T(0), T(0)};
     if ((um >> m) & 1u) {
       Af_ = face_aperture(g, b, cL, cR, 0, m);
-      if (Af_ > 0.0) {
+      if (Af_ > 0.0 && m != g.fs_mat) {
         if ((lin && !((b.smask[cL] >> m) & 1u)) || (rin && !((b.smask[cR] >> m) & 1u))) err |= ERR_BAND;
         const T mgm1 = T(g.gm1[m]), mgpi = T(g.gpi[m]), mgam = T(g.gamma[m]), mpinf = T(g.pinf[m]);
         const TaitK mtk = tait_of(g, m);
@@ -1825,7 +1836,8 @@ __device__ __forceinline__ void flux1d_faces(const Grid& g, const Bufs& b, const
     if (f == 0 || f == n) {
       const long long fid = f == 0 ? bb.base[0] : bb.base[1];
       const double sgn = f == 0 ? 1.0 : -1.0;
-      for (int v = 0; v < NV; v++) b.bflux[((fid * g.N) + m) * NV + v] = sgn * (Af_ * (double)Fh[v] * g.farea[0]);
+      const double fa = g.geom == 1 ? face_r(g, off + f) : g.farea[0];
+      for (int v = 0; v < NV; v++) b.bflux[((fid * g.N) + m) * NV + v] = sgn * (Af_ * (double)Fh[v] * fa);
     }
   }
 }
@@ -1843,11 +1855,34 @@ __device__ __forceinline__ void flux1d_update(const Grid& g, const Bufs& b, cons
     const long long c = off + i;
     if (!((b.smask[c] >> m) & 1u)) continue;
     const bool cut = (b.gflag[c] & GF_CUT) != 0;
+    // cylindrical grid: faces weighted by their radii, volume r_i h, and the
+    // source p alpha / r_i of the radial momentum (the stage's stencil state)
+    const bool cyl = g.geom == 1;
+    double rlo = 0.0, rhi = 0.0, rvc = 0.0, psrc = 0.0;
+    if (cyl) {
+      const double rc = cell_r(g, (int)c), a = alpha_of(g, b, c, m);
+      rlo = face_r(g, (int)c);
+      rhi = face_r(g, (int)c + 1);
+      rvc = 1.0 / (rc * g.h[0]);
+      if (a > 0.0) {
+        T u[NV], w[NV];
+        interior_uhat<T>(g, b, Qs, c, m, u);
+        cons_to_prim<T>(g, m, 1, u, w);
+        psrc = (double)w[2] * a / rc;
+      }
+    }
     for (int v = 0; v < NV; v++) {
       double L = 0.0;
       const double fl = (double)Ff[((long long)m * NV + v) * nf + i], fh = (double)Ff[((long long)m * NV + v) * nf + i + 1];
-      L = L + (Af[(long long)m * nf + i] * fl - Af[(long long)m * nf + i + 1] * fh) * g.rh[0];
-      if (cut) L = L + b.X[qidx(g, m, v, c)] * g.rV;
+      if (cyl) {
+        L = (Af[(long long)m * nf + i] * fl * rlo - Af[(long long)m * nf + i + 1] * fh * rhi) * rvc;
+        if (cut) L = L + b.X[qidx(g, m, v, c)] * rvc;
+        if (v == 1) L = L + psrc;
+      } else {
+        L = L + (Af[(long long)m * nf + i] * fl - Af[(long long)m * nf + i + 1] * fh) * g.rh[0];
+        if (cut) L = L + b.X[qidx(g, m, v, c)] * g.rV;
+      }
+      if (m == g.fs_mat) L = 0.0;  // the ambient is not solved
       const long long qi = qidx(g, m, v, c);
       const double qv = beta * Qn[qi] + omb * (Qs[qi] + dt * L);
       if (!isfinite(qv)) err |= ERR_NONFINITE;
@@ -1885,6 +1920,10 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
     __syncthreads();
     phase_geom_cell(g, b, b.Q[0], (const double*)nullptr, t, nt);
     __syncthreads();
+    if (g.fs_mat >= 0) {
+      phase_hold(g, b, b.Q[0], -1, t, nt);
+      __syncthreads();
+    }
     phase_band_save(g, b, t, nt);
     __syncthreads();
     for (int s = 0; s < g.rk; s++) {
@@ -1904,6 +1943,10 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
       __syncthreads();
       phase_bc_uhat<T>(g, b, Qs, t, nt);
       __syncthreads();
+      // the exchange of stage 0 comes first: the bound of the step reads the
+      // free-surface velocities it sets
+      phase_interface<T>(g, b, Qs, s, t, nt);
+      __syncthreads();
       if (s == 0) {
         unsigned err = 0;
         const double lam = block_max(dt_items<T>(g, b, Qs, t, nt, err));
@@ -1922,8 +1965,6 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
         }
         __syncthreads();
       }
-      phase_interface<T>(g, b, Qs, s, t, nt);
-      __syncthreads();
       int vc = 0;
       for (int k = 0; k < g.vel_sweeps; k++) {
         if (vc) extend_vel_items(g, b, b.vel1, b.vel0, b.vf1, b.vf0, t, nt);
@@ -1953,6 +1994,10 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
       __syncthreads();
       phase_geom_cell(g, b, (const double*)Qo, (const double*)nullptr, t, nt);
       __syncthreads();
+      if (g.fs_mat >= 0) {
+        phase_hold(g, b, Qo, s + 1, t, nt);
+        __syncthreads();
+      }
       phase_mix_mark(g, b, (const double*)Qo, t, nt);
       __syncthreads();
       phase_mix_weights(g, b, t, nt);

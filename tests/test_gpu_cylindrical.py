@@ -90,21 +90,46 @@ def test_icf_full_run_fp64(msf):
         assert abs(tot[m, 0] - tot0[m, 0]) / tot0[m, 0] < 1e-12
 
 
+def test_icf_quarter_plane_fp64(msf):
+    """The free surface on a two-dimensional Cartesian grid (a circle)."""
+    o, s, eo = run_pair(msf, cs.icf_quarter_plane(64), 60)
+    assert eo == 0
+    compare(o, s, FP64_L1, exact=True)
+
+
 def test_icf_fp32(msf):
     o, s, eo = run_pair(msf, cs.icf_implosion(320), 200, precision=1)
     assert eo == 0
     compare(o, s, FP32_L1)
 
 
-def test_cylindrical_refusals(msf):
-    """The batched form and the tape / adjoint entry points take Cartesian
-    grids without a free surface only."""
-    with pytest.raises(msf.MsfError) as ei:
-        msf.Batch([cs.icf_implosion(160), cs.icf_implosion(200)])
-    assert ei.value.status == msf.MSF_EUNSUPPORTED
-    b = msf.Batch([cs.icf_implosion(160), cs.icf_implosion(200)], batch_mode=1)
-    b.step(5, 1.0)
-    b.close()
+@pytest.mark.parametrize("precision", [0, 1])
+def test_icf_batched_matches_oracle(msf, precision):
+    """The shell-thickness study as one batched launch (one CTA per instance):
+    every instance bit-identical to the oracle in FP64, within the FP32
+    tolerance in the FP32-bulk form."""
+    steps = 150
+    cases = cs.icf_shell_study(160, 5)
+    batch = msf.Batch(cases, precision=precision)
+    batch.step(steps, 1.0)
+    assert batch.launches_per_step() == 1
+    for i, c in enumerate(cases):
+        o = orc.Oracle(c)
+        assert o.step(steps, 1.0) == 0
+        a, b = batch.state(i), o.state()
+        if precision == 0:
+            assert a["t"] == b["t"]
+            assert np.array_equal(a["Q"], b["Q"]), (i, np.abs(a["Q"] - b["Q"]).max())
+            assert np.array_equal(a["chi"], b["chi"])
+        else:
+            assert a["t"] == pytest.approx(b["t"], rel=1e-5)
+            ra, rb = a["Q"][:, 0].sum(0), b["Q"][:, 0].sum(0)
+            assert np.abs(ra - rb).sum() / np.abs(rb).sum() <= FP32_L1
+
+
+def test_cylindrical_tape_refused(msf):
+    """The tape and adjoint entry points take Cartesian grids without a free
+    surface only."""
     s = msf.Solver(cs.icf_implosion(160))
     with pytest.raises(msf.MsfError) as ei:
         s.tape_bytes()

@@ -163,3 +163,24 @@ def test_free_surface_drives_the_exact_shock():
     # the density carries the start-up error of a shock born at a wall (an
     # entropy dip at the surface): within one percent
     assert np.abs(q[0, plateau] - rho_exact).max() < 1e-2 * rho_exact
+
+
+def test_icf_quarter_plane_matches_cylindrical_grid():
+    """Case II on a two-dimensional Cartesian quarter plane (no axisymmetric
+    metric; the free surface is a circle) against the one-dimensional
+    cylindrical grid: the radii of the shell's interfaces at t = 0.1 (from the
+    volumes of core and shell) agree to grid accuracy."""
+    n, t_end = 64, 0.1
+    o2 = orc.Oracle(cs.icf_quarter_plane(n, t_end=t_end))
+    assert o2.step(100000, t_end) == 0
+    a2 = o2.state()["alpha"]
+    core, shell = a2[0].sum() / n ** 2, a2[1].sum() / n ** 2
+    r_in2, r_out2 = np.sqrt(4 * core / np.pi), np.sqrt(4 * (core + shell) / np.pi)
+    o1 = orc.Oracle(cs.icf_implosion(n, t_end=t_end))
+    assert o1.step(100000, t_end) == 0
+    a1 = o1.state()["alpha"]
+    (x,) = cs.centres((n,), (0.0,), (1.0,))
+    v0, v1 = (a1[0] * x).sum() / n, (a1[1] * x).sum() / n
+    r_in1, r_out1 = np.sqrt(2 * v0), np.sqrt(2 * (v0 + v1))
+    assert r_in1 < 0.5 and r_out1 < 0.7          # both interfaces have moved in
+    assert abs(r_in2 - r_in1) < 2e-3 and abs(r_out2 - r_out1) < 2e-3
