@@ -229,9 +229,12 @@ double orc_weno5(double a, double b, double c, double d, double e, double eps) {
   t = 3.0 * c - 4.0 * d + e;
   s2 = s2 + 0.25 * t * t;
   double b0 = eps + s0, b1 = eps + s1, b2 = eps + s2;
-  double a0 = 0.1 / (b0 * b0);
-  double a1 = 0.6 / (b1 * b1);
-  double a2 = 0.3 / (b2 * b2);
+  /* the weights 0.1/b0^2, 0.6/b1^2, 0.3/b2^2, each multiplied by
+     b0^2 b1^2 b2^2: the normalised weights are unchanged */
+  double p0 = b0 * b0, p1 = b1 * b1, p2 = b2 * b2;
+  double a0 = 0.1 * (p1 * p2);
+  double a1 = 0.6 * (p0 * p2);
+  double a2 = 0.3 * (p0 * p1);
   return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
 }
 
