@@ -479,6 +479,35 @@ __device__ __forceinline__ void interior_uhat(const Grid& g, const Bufs& b, cons
     for (int v = 0; v < g.NV; v++) u[v] = nanv;
   }
 }
+// the same with the variable count known at compile time; the band index,
+// the indicator and the conserved state are loaded together (one round of
+// memory latency for a bulk cell)
+template <typename T, int NV>
+__device__ __forceinline__ void interior_uhat_n(const Grid& g, const Bufs& b, const double* Qs, long long c, int m,
+                                                T* u) {
+  const T nanv = (T)__longlong_as_double(0x7ff8000000000000LL);
+  const T* Uh = (const T*)b.Uh;
+  const int bi = b.bandidx[c];
+  const uint8_t ch = b.chi[c];
+  double q[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) q[v] = Qs[qidx(g, m, v, c)];
+  if (bi >= 0) {
+    if ((b.smask[c] >> m) & 1u) {
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = Uh[qidx(g, m, v, c)];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = nanv;
+    }
+  } else if (ch == m) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) u[v] = (T)q[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; v++) u[v] = nanv;
+  }
+}
 
 // halo cells of the stencil state (one axis out of range at a time)
 template <typename T>
@@ -1051,6 +1080,12 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
   const double dt = b.ctl->dt;
   unsigned err = 0;
 
+  // a tile that may be idle (see below); in FP64, whose divisions and square
+  // roots are costly, it stages the states first and derives the primitive
+  // quantities only when it is not idle
+  const bool cand = !anyband && interior_tile && g.geom == 0;
+  const bool defer = cand && sizeof(T) == 8;
+  const int sref = 3 + SX * (S::HY + SY * S::HZ);
   for (int m = 0; m < g.N; m++) {
     if (!((uni >> m) & 1u)) continue;
     const T mgm1 = T(g.gm1[m]), mgpi = T(g.gpi[m]), mgam = T(g.gamma[m]), mpinf = T(g.pinf[m]);
@@ -1074,7 +1109,7 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
         if (D >= 2) inner = inner && gy >= g.off[1] && gy < g.off[1] + g.n[1];
         if (D >= 3) inner = inner && gz >= g.off[2] && gz < g.off[2] + g.n[2];
         if (inner) {
-          interior_uhat<T>(g, b, Qs, gc, m, u);
+          interior_uhat_n<T, NV>(g, b, Qs, gc, m, u);
         } else {
           const T* Uh = (const T*)b.Uh;
 #pragma unroll
@@ -1087,7 +1122,7 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
 #pragma unroll
       for (int v = 0; v < NV; v++) U[v * NS + s] = u[v];
       bad[s] = 0;
-      if (!isnan(u[0])) {
+      if (!isnan(u[0]) && (!defer || s == sref)) {
         T vel[D], pres, cs;
         bool isbad;
         stencil_prim<D, T>(u, mgm1, mgpi, mgam, mpinf, mtk, vel, pres, cs, isbad);
@@ -1105,7 +1140,28 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
     // exactly +0 and L = 0; the face evaluation is skipped and the update
     // below runs with L = 0, giving the same bits as the full evaluation.
     bool idle = false;
-    if (!anyband && interior_tile && g.geom == 0) idle = __syncthreads_and(stencil_uniform<D, T>(U, bad, tid)) != 0;
+    if (cand) {
+      idle = __syncthreads_and(stencil_uniform<D, T>(U, bad, tid)) != 0;
+      if (defer && !idle) {
+        // not idle after all: the primitive quantities of the other staged states
+#pragma unroll 1
+        for (int s = tid; s < NS; s += blockDim.x) {
+          if (s == sref || isnan(U[s])) continue;
+          T u[NV];
+#pragma unroll
+          for (int v = 0; v < NV; v++) u[v] = U[v * NS + s];
+          T vel[D], pres, cs;
+          bool isbad;
+          stencil_prim<D, T>(u, mgm1, mgpi, mgam, mpinf, mtk, vel, pres, cs, isbad);
+#pragma unroll
+          for (int e = 0; e < D; e++) P[e * NS + s] = vel[e];
+          P[D * NS + s] = pres;
+          P[(D + 1) * NS + s] = cs;
+          bad[s] = isbad ? 1 : 0;
+        }
+        __syncthreads();
+      }
+    }
     // face apertures and fluxes: x faces, then y, then z
     if (!idle)
       for (int f = tid; f < S::NF; f += blockDim.x) {
