@@ -185,8 +185,9 @@ __device__ inline unsigned block_bits(const Grid& g, const uint8_t* chi, const i
 
 // per (band cell, material): unit normal of phi^m for the materials the cell
 // carries this step, volume fraction and raw face apertures
-__device__ __forceinline__ void phase_geom_mat(const Grid& g, const Bufs& b, int first_, int stride_) {
-    const int nb = b.ctl->nband, N = g.N, D = g.D;
+template <int DD>
+__device__ __forceinline__ void phase_geom_mat_d(const Grid& g, const Bufs& b, int first_, int stride_) {
+    const int nb = b.ctl->nband, N = g.N, D = DD;
   const int total = nb * N;
   for (int it = first_; it < total; it += stride_) {
     const int m = it / nb, k = it - m * nb;
@@ -214,6 +215,11 @@ __device__ __forceinline__ void phase_geom_mat(const Grid& g, const Bufs& b, int
       b.Ahi[aidx(g, d, m, c)] = ahi[d];
     }
   }
+}
+__device__ __forceinline__ void phase_geom_mat(const Grid& g, const Bufs& b, int first_, int stride_) {
+  if (g.D == 1) phase_geom_mat_d<1>(g, b, first_, stride_);
+  else if (g.D == 2) phase_geom_mat_d<2>(g, b, first_, stride_);
+  else phase_geom_mat_d<3>(g, b, first_, stride_);
 }
 __global__ void k_geom_mat(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
   if (!ctl_active(b)) return;
@@ -358,10 +364,10 @@ __global__ void k_prim(const __grid_constant__ Grid g, const __grid_constant__ B
 // Every neighbour value is loaded up front, unconditionally (face neighbours of
 // an interior cell lie inside the padded arrays), so that a sweep costs one
 // round of memory latency instead of one per neighbour.
-template <typename T>
-__device__ __forceinline__ void extend_items(const Grid& g, const Bufs& b, const void* Win, void* Wout,
+template <typename T, int DD>
+__device__ __forceinline__ void extend_items_d(const Grid& g, const Bufs& b, const void* Win, void* Wout,
                                              const uint8_t* fin, uint8_t* fout, int first, int stride) {
-  const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
+  const int nb = b.ctl->nband, N = g.N, NV = DD + 2, D = DD;
   const T* Wi = (const T*)Win;
   T* Wo = (T*)Wout;
   const int total = nb * N;
@@ -417,6 +423,13 @@ __device__ __forceinline__ void extend_items(const Grid& g, const Bufs& b, const
       fout[midx(g, m, c)] = finc;
     }
   }
+}
+template <typename T>
+__device__ __forceinline__ void extend_items(const Grid& g, const Bufs& b, const void* Win, void* Wout,
+                                             const uint8_t* fin, uint8_t* fout, int first, int stride) {
+  if (g.D == 1) extend_items_d<T, 1>(g, b, Win, Wout, fin, fout, first, stride);
+  else if (g.D == 2) extend_items_d<T, 2>(g, b, Win, Wout, fin, fout, first, stride);
+  else extend_items_d<T, 3>(g, b, Win, Wout, fin, fout, first, stride);
 }
 
 // one Jacobi sweep: targets take the upwind-weighted mean of filled face
@@ -510,9 +523,9 @@ __device__ __forceinline__ void interior_uhat_n(const Grid& g, const Bufs& b, co
 }
 
 // halo cells of the stencil state (one axis out of range at a time)
-template <typename T>
-__device__ __forceinline__ void phase_bc_uhat(const Grid& g, const Bufs& b, const double* Qs, int first_, int stride_) {
-    const int N = g.N, NV = g.NV, D = g.D;
+template <typename T, int DD>
+__device__ __forceinline__ void phase_bc_uhat_d(const Grid& g, const Bufs& b, const double* Qs, int first_, int stride_) {
+    const int N = g.N, NV = DD + 2, D = DD;
   long long per[3] = {0, 0, 0}, total = 0;
   for (int d = 0; d < D; d++) {
     per[d] = 2LL * G * (g.n_interior / g.n[d]);
@@ -558,6 +571,12 @@ __device__ __forceinline__ void phase_bc_uhat(const Grid& g, const Bufs& b, cons
   }
 }
 template <typename T>
+__device__ __forceinline__ void phase_bc_uhat(const Grid& g, const Bufs& b, const double* Qs, int first_, int stride_) {
+  if (g.D == 1) phase_bc_uhat_d<T, 1>(g, b, Qs, first_, stride_);
+  else if (g.D == 2) phase_bc_uhat_d<T, 2>(g, b, Qs, first_, stride_);
+  else phase_bc_uhat_d<T, 3>(g, b, Qs, first_, stride_);
+}
+template <typename T>
 __global__ void k_bc_uhat(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
   if (!ctl_active(b)) return;
   phase_bc_uhat<T>(g, b, Qs, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
@@ -565,10 +584,10 @@ __global__ void k_bc_uhat(const __grid_constant__ Grid g, const __grid_constant_
 
 // ----------------------------------------------------------- CFL step (a2)
 // largest sum_d (|u_d| + c) / h_d over the items [first, n_interior) with stride
-template <typename T>
-__device__ __forceinline__ double dt_items(const Grid& g, const Bufs& b, const double* Qs, long long first,
+template <typename T, int DD>
+__device__ __forceinline__ double dt_items_d(const Grid& g, const Bufs& b, const double* Qs, long long first,
                                            long long stride, unsigned& err) {
-  const int N = g.N, D = g.D;
+  const int N = g.N, D = DD;
   double lam = 0.0;
   for (long long idx = first; idx < g.n_interior; idx += stride) {
     const long long c = interior_cell(g, idx);
@@ -592,6 +611,13 @@ __device__ __forceinline__ double dt_items(const Grid& g, const Bufs& b, const d
     }
   }
   return lam;
+}
+template <typename T>
+__device__ __forceinline__ double dt_items(const Grid& g, const Bufs& b, const double* Qs, long long first,
+                                           long long stride, unsigned& err) {
+  if (g.D == 1) return dt_items_d<T, 1>(g, b, Qs, first, stride, err);
+  if (g.D == 2) return dt_items_d<T, 2>(g, b, Qs, first, stride, err);
+  return dt_items_d<T, 3>(g, b, Qs, first, stride, err);
 }
 // block maximum of per-thread values (blockDim.x a power of two <= 1024)
 __device__ __forceinline__ double block_max(double v) {
@@ -638,10 +664,10 @@ __global__ void k_step_end(const __grid_constant__ Bufs b) {
 }
 
 // ----------------------------------------- reduced interface interaction (a7)
-template <typename T>
-__device__ __forceinline__ void phase_interface(const Grid& g, const Bufs& b, const double* Qs, int stage, int first_,
+template <typename T, int DD>
+__device__ __forceinline__ void phase_interface_d(const Grid& g, const Bufs& b, const double* Qs, int stage, int first_,
                                                 int stride_) {
-    const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
+    const int nb = b.ctl->nband, N = g.N, NV = DD + 2, D = DD;
   const double ts = stage == 0 ? b.ctl->t : b.ctl->t + g.rk_c[stage] * b.ctl->dt;  // time of the stage
   const T* Uh = (const T*)b.Uh;
   unsigned err = 0;
@@ -731,15 +757,23 @@ __device__ __forceinline__ void phase_interface(const Grid& g, const Bufs& b, co
   if (err) atomicOr(&b.ctl->err, err);
 }
 template <typename T>
+__device__ __forceinline__ void phase_interface(const Grid& g, const Bufs& b, const double* Qs, int stage, int first_,
+                                                int stride_) {
+  if (g.D == 1) phase_interface_d<T, 1>(g, b, Qs, stage, first_, stride_);
+  else if (g.D == 2) phase_interface_d<T, 2>(g, b, Qs, stage, first_, stride_);
+  else phase_interface_d<T, 3>(g, b, Qs, stage, first_, stride_);
+}
+template <typename T>
 __global__ void k_interface(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs, int stage) {
   if (!ctl_active(b)) return;
   phase_interface<T>(g, b, Qs, stage, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // one sweep of the interface-velocity extension into the band
-__device__ __forceinline__ void extend_vel_items(const Grid& g, const Bufs& b, const double* vin, double* vout,
+template <int DD>
+__device__ __forceinline__ void extend_vel_items_d(const Grid& g, const Bufs& b, const double* vin, double* vout,
                                                  const uint8_t* fin, uint8_t* fout, int first, int stride) {
-  const int nb = b.ctl->nband, D = g.D;
+  const int nb = b.ctl->nband, D = DD;
   for (int k = first; k < nb; k += stride) {
     const long long c = b.band[k];
     // every value the sweep may use, loaded up front (one round of latency)
@@ -792,6 +826,12 @@ __device__ __forceinline__ void extend_vel_items(const Grid& g, const Bufs& b, c
     }
     fout[c] = filled;
   }
+}
+__device__ __forceinline__ void extend_vel_items(const Grid& g, const Bufs& b, const double* vin, double* vout,
+                                                 const uint8_t* fin, uint8_t* fout, int first, int stride) {
+  if (g.D == 1) extend_vel_items_d<1>(g, b, vin, vout, fin, fout, first, stride);
+  else if (g.D == 2) extend_vel_items_d<2>(g, b, vin, vout, fin, fout, first, stride);
+  else extend_vel_items_d<3>(g, b, vin, vout, fin, fout, first, stride);
 }
 __global__ void k_extend_vel(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* vin,
                              double* vout, const uint8_t* fin, uint8_t* fout) {
@@ -1273,8 +1313,9 @@ __global__ void k_ledger(const __grid_constant__ Grid g, const __grid_constant__
 // --------------------------------------------- level-set stage (a9) + R
 __device__ inline double phir_stage(const Bufs& b, long long c, int r) { return phi_m(b.phi, b.chi, c, r); }
 
-__device__ __forceinline__ void phase_levelset(const Grid& g, const Bufs& b, const double* vel, double beta, double omb, int first_, int stride_) {
-    const int nb = b.ctl->nband, N = g.N, D = g.D;
+template <int DD>
+__device__ __forceinline__ void phase_levelset_d(const Grid& g, const Bufs& b, const double* vel, double beta, double omb, int first_, int stride_) {
+    const int nb = b.ctl->nband, N = g.N, D = DD;
   const double dt = b.ctl->dt, eps = g.weno_eps;
   const int total = nb * N;
   for (int it = first_; it < total; it += stride_) {
@@ -1314,6 +1355,11 @@ __device__ __forceinline__ void phase_levelset(const Grid& g, const Bufs& b, con
     const double phn = b.chin[c] == r ? b.phin[c] : -b.phin[c];
     b.phir[(long long)k * N + r] = beta * phn + omb * (phir_stage(b, c, r) - dt * adv);
   }
+}
+__device__ __forceinline__ void phase_levelset(const Grid& g, const Bufs& b, const double* vel, double beta, double omb, int first_, int stride_) {
+  if (g.D == 1) phase_levelset_d<1>(g, b, vel, beta, omb, first_, stride_);
+  else if (g.D == 2) phase_levelset_d<2>(g, b, vel, beta, omb, first_, stride_);
+  else phase_levelset_d<3>(g, b, vel, beta, omb, first_, stride_);
 }
 __global__ void k_levelset(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* vel, double beta, double omb) {
   if (!ctl_active(b)) return;
@@ -1493,8 +1539,9 @@ __global__ void k_mix_mark(const __grid_constant__ Grid g, const __grid_constant
 // cell's with weight beta a_s V_s / (a_s V_s + a_t V_t).
 // T sums a cell's weights: its own pairs in target order, then the pairs of
 // the neighbours that mix into it in (z, y, x) offset order.
-__device__ __forceinline__ void phase_mix_weights(const Grid& g, const Bufs& b, int first_, int stride_) {
-  const int nb = b.ctl->nband, N = g.N, D = g.D;
+template <int DD>
+__device__ __forceinline__ void phase_mix_weights_d(const Grid& g, const Bufs& b, int first_, int stride_) {
+  const int nb = b.ctl->nband, N = g.N, D = DD;
   const int total = nb * N;
   for (int it = first_; it < total; it += stride_) {
     const int m = it / nb, k = it - m * nb;
@@ -1539,6 +1586,11 @@ __device__ __forceinline__ void phase_mix_weights(const Grid& g, const Bufs& b, 
     b.mixT[r] = T;
   }
 }
+__device__ __forceinline__ void phase_mix_weights(const Grid& g, const Bufs& b, int first_, int stride_) {
+  if (g.D == 1) phase_mix_weights_d<1>(g, b, first_, stride_);
+  else if (g.D == 2) phase_mix_weights_d<2>(g, b, first_, stride_);
+  else phase_mix_weights_d<3>(g, b, first_, stride_);
+}
 __global__ void k_mix_weights(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
   if (!ctl_active(b)) return;
   phase_mix_weights(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
@@ -1560,8 +1612,9 @@ __device__ inline double mix_limit(double as, double Ts, double Tt) {
 // new state of material m of every band cell: own exchanges minus the
 // exchanges its small neighbours send to it (lexicographic neighbour order),
 // each scaled by mix_limit
-__device__ __forceinline__ void phase_mix_compute(const Grid& g, const Bufs& b, const double* Qc, int first_, int stride_) {
-    const int nb = b.ctl->nband, N = g.N, NV = g.NV, D = g.D;
+template <int DD>
+__device__ __forceinline__ void phase_mix_compute_d(const Grid& g, const Bufs& b, const double* Qc, int first_, int stride_) {
+    const int nb = b.ctl->nband, N = g.N, NV = DD + 2, D = DD;
   const int total = nb * N;
   for (int it = first_; it < total; it += stride_) {
     const int m = it / nb, k = it - m * nb;
@@ -1618,6 +1671,11 @@ __device__ __forceinline__ void phase_mix_compute(const Grid& g, const Bufs& b, 
         }
     for (int v = 0; v < NV; v++) out[v] = Qc[qidx(g, m, v, c)] + acc[v];
   }
+}
+__device__ __forceinline__ void phase_mix_compute(const Grid& g, const Bufs& b, const double* Qc, int first_, int stride_) {
+  if (g.D == 1) phase_mix_compute_d<1>(g, b, Qc, first_, stride_);
+  else if (g.D == 2) phase_mix_compute_d<2>(g, b, Qc, first_, stride_);
+  else phase_mix_compute_d<3>(g, b, Qc, first_, stride_);
 }
 __global__ void k_mix_compute(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qc) {
   if (!ctl_active(b)) return;
@@ -1729,8 +1787,9 @@ __global__ void k_scale_sep(const __grid_constant__ Grid g, const __grid_constan
 }
 
 // --------------------------------------------- band distance maintenance
-__device__ __forceinline__ void reinit_items(const Grid& g, const Bufs& b, int first, int stride) {
-  const int nb = b.ctl->nband, D = g.D;
+template <int DD>
+__device__ __forceinline__ void reinit_items_d(const Grid& g, const Bufs& b, int first, int stride) {
+  const int nb = b.ctl->nband, D = DD;
   for (int k = first; k < nb; k += stride) {
     const long long c = b.band[k];
     b.phit[k] = b.phi[c];
@@ -1775,6 +1834,11 @@ __device__ __forceinline__ void reinit_items(const Grid& g, const Bufs& b, int f
     if (ph > g.cap) ph = g.cap;
     b.phit[k] = ph;
   }
+}
+__device__ __forceinline__ void reinit_items(const Grid& g, const Bufs& b, int first, int stride) {
+  if (g.D == 1) reinit_items_d<1>(g, b, first, stride);
+  else if (g.D == 2) reinit_items_d<2>(g, b, first, stride);
+  else reinit_items_d<3>(g, b, first, stride);
 }
 __device__ __forceinline__ void scatter_items(const Bufs& b, int first, int stride) {
   const int nb = b.ctl->nband;
@@ -1972,7 +2036,7 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
     __syncthreads();
     phase_band(g, b, b.mtmp, t, nt);
     __syncthreads();
-    phase_geom_mat(g, b, t, nt);
+    phase_geom_mat_d<1>(g, b, t, nt);
     __syncthreads();
     phase_geom_cell(g, b, b.Q[0], (const double*)nullptr, t, nt);
     __syncthreads();
@@ -1990,22 +2054,22 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
       __syncthreads();
       int cur = 0;
       for (int k = 0; k < g.ext_sweeps; k++) {
-        if (cur) extend_items<T>(g, b, b.W1, b.W0, b.f1, b.f0, t, nt);
-        else extend_items<T>(g, b, b.W0, b.W1, b.f0, b.f1, t, nt);
+        if (cur) extend_items_d<T, 1>(g, b, b.W1, b.W0, b.f1, b.f0, t, nt);
+        else extend_items_d<T, 1>(g, b, b.W0, b.W1, b.f0, b.f1, t, nt);
         cur ^= 1;
         __syncthreads();
       }
       phase_cons<T>(g, b, Qs, cur ? b.W1 : b.W0, cur ? b.f1 : b.f0, t, nt);
       __syncthreads();
-      phase_bc_uhat<T>(g, b, Qs, t, nt);
+      phase_bc_uhat_d<T, 1>(g, b, Qs, t, nt);
       __syncthreads();
       // the exchange of stage 0 comes first: the bound of the step reads the
       // free-surface velocities it sets
-      phase_interface<T>(g, b, Qs, s, t, nt);
+      phase_interface_d<T, 1>(g, b, Qs, s, t, nt);
       __syncthreads();
       if (s == 0) {
         unsigned err = 0;
-        const double lam = block_max(dt_items<T>(g, b, Qs, t, nt, err));
+        const double lam = block_max(dt_items_d<T, 1>(g, b, Qs, t, nt, err));
         if (err) atomicOr(&b.ctl->err, err);
         if (t == 0) {
           Ctl* c = b.ctl;
@@ -2023,8 +2087,8 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
       }
       int vc = 0;
       for (int k = 0; k < g.vel_sweeps; k++) {
-        if (vc) extend_vel_items(g, b, b.vel1, b.vel0, b.vf1, b.vf0, t, nt);
-        else extend_vel_items(g, b, b.vel0, b.vel1, b.vf0, b.vf1, t, nt);
+        if (vc) extend_vel_items_d<1>(g, b, b.vel1, b.vel0, b.vf1, b.vf0, t, nt);
+        else extend_vel_items_d<1>(g, b, b.vel0, b.vel1, b.vf0, b.vf1, t, nt);
         vc ^= 1;
         __syncthreads();
       }
@@ -2040,13 +2104,13 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
         b.ctl->ledger[mv / g.NV][mv % g.NV] += g.rk_lw[s] * b.ctl->dt * sum;
       }
       __syncthreads();
-      phase_levelset(g, b, vc ? b.vel1 : b.vel0, beta, 1.0 - beta, t, nt);
+      phase_levelset_d<1>(g, b, vc ? b.vel1 : b.vel0, beta, 1.0 - beta, t, nt);
       __syncthreads();
       phase_levelset_R(g, b, t, nt);
       __syncthreads();
       phase_bc_phichi(g, b, t, nt);
       __syncthreads();
-      phase_geom_mat(g, b, t, nt);
+      phase_geom_mat_d<1>(g, b, t, nt);
       __syncthreads();
       phase_geom_cell(g, b, (const double*)Qo, (const double*)nullptr, t, nt);
       __syncthreads();
@@ -2056,9 +2120,9 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
       }
       phase_mix_mark(g, b, (const double*)Qo, t, nt);
       __syncthreads();
-      phase_mix_weights(g, b, t, nt);
+      phase_mix_weights_d<1>(g, b, t, nt);
       __syncthreads();
-      phase_mix_compute(g, b, (const double*)Qo, t, nt);
+      phase_mix_compute_d<1>(g, b, (const double*)Qo, t, nt);
       __syncthreads();
       phase_mix_scatter(g, b, Qo, t, nt);
       __syncthreads();
@@ -2079,7 +2143,7 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
     }
     if (g.reinit) {
       for (int k = 0; k < g.reinit_iters; k++) {
-        reinit_items(g, b, t, nt);
+        reinit_items_d<1>(g, b, t, nt);
         __syncthreads();
         scatter_items(b, t, nt);
         __syncthreads();
