@@ -312,18 +312,19 @@ __device__ inline double facec_val(const Grid& g, const double* phi, const uint8
 }
 
 // volume fraction and raw face apertures of material m in cell c
+template <int D>
 __device__ inline void cell_geom(const Grid& g, const double* phi, const uint8_t* chi, long long c, int m,
                                  double* alpha, double* alo, double* ahi) {
   int q[3];
   coords(g, c, q);
   const int i = q[0], j = q[1], k = q[2];
   double vc = phi_m(phi, chi, c, m);
-  if (g.D == 1) {
+  if constexpr (D == 1) {
     double c0 = vertex_val(g, phi, chi, i, j, k, m), c1 = vertex_val(g, phi, chi, i + 1, j, k, m);
     *alpha = (frac_seg(c0, vc) + frac_seg(vc, c1)) * 0.5;
     alo[0] = c0 > 0.0 ? 1.0 : (c0 < 0.0 ? 0.0 : 0.5);
     ahi[0] = c1 > 0.0 ? 1.0 : (c1 < 0.0 ? 0.0 : 0.5);
-  } else if (g.D == 2) {
+  } else if constexpr (D == 2) {
     double c00 = vertex_val(g, phi, chi, i, j, k, m), c10 = vertex_val(g, phi, chi, i + 1, j, k, m);
     double c01 = vertex_val(g, phi, chi, i, j + 1, k, m), c11 = vertex_val(g, phi, chi, i + 1, j + 1, k, m);
     alo[0] = frac_seg(c00, c01);

@@ -207,7 +207,7 @@ __device__ __forceinline__ void phase_geom_mat_d(const Grid& g, const Bufs& b, i
         for (int d = 0; d < D; d++) alo[d] = ahi[d] = 1.0;
       }
     } else if ((bits >> m) & 1u) {
-      cell_geom(g, b.phi, b.chi, c, m, &a, alo, ahi);
+      cell_geom<DD>(g, b.phi, b.chi, c, m, &a, alo, ahi);
     }
     b.alpha[midx(g, m, c)] = a;
     for (int d = 0; d < D; d++) {
