@@ -358,6 +358,24 @@ def flux_bytes_per_step(case, npairs):
     return npairs * per_pair + case.cells * 2 * 3
 
 
+def max_over_ranks(vals, device=None):
+    """Largest value of each entry over all ranks (the slowest rank sets the
+    job's time); the values themselves on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in vals]
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: every rank processes the same units (weak scaling),
+    in the time of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -413,12 +431,9 @@ def run_gpu(args):
     s64, ms64, fl64, _ = timed(msf.MSF_FP64)
     total32 = sum(ms32) / 1e3
     total64 = sum(ms64) / 1e3
-    if world > 1:
-        t = torch.tensor([total32, total64], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total32, total64 = float(t[0]), float(t[1])
-    value = world * cells * stages * K / total32
-    value64 = world * cells * stages * K / total64
+    total32, total64 = max_over_ranks([total32, total64], dev)
+    value = job_rate(cells * stages * K, world, total32)
+    value64 = job_rate(cells * stages * K, world, total64)
     a, b = s32.state(), s64.state()
     ra, rb = a["Q"][:, 0].sum(0), b["Q"][:, 0].sum(0)
     l1 = float(np.abs(ra - rb).sum() / np.abs(rb).sum())
@@ -444,7 +459,8 @@ def run_gpu(args):
     se.step(K, case.t_end)
     st = se.state()
     t1 = time.perf_counter()
-    e2e_val = world * cells * stages * K / (t1 - t0)
+    (e2e_s,) = max_over_ranks([t1 - t0], dev)
+    e2e_val = job_rate(cells * stages * K, world, e2e_s)
     h2d = phi.nbytes + chi.nbytes + prim.nbytes
     d2h = st["Q"].nbytes + st["alpha"].nbytes + st["phi"].nbytes + st["chi"].nbytes
 
