@@ -1705,6 +1705,10 @@ void orc_set_state(orc* o, const double* Q, const double* phi, const int32_t* ch
 
 /* overwrite the conserved state of the interior cells (SoA [N][NV][cells]),
  * keeping the level set, the time and the counters */
+/* the mixing pass alone on the current state and geometry (a test hook: the
+   properties of reading 16 are pinned on it) */
+void orc_mix_only(orc* o) { mixing(o, o->Q); }
+
 void orc_set_conserved(orc* o, const double* Q) {
   int N = o->N, NV = o->NV;
   long ni = n_interior(o);

@@ -66,6 +66,8 @@ long orc_ncell(const orc* o);
 int orc_step_taped(orc* o, double t_end, double* tphi, uint8_t* tchi, double* tdt);
 int orc_replay_step(orc* o, const double* tphi, const uint8_t* tchi, double dt);
 void orc_set_conserved(orc* o, const double* Q);
+/* the mixing pass (Sec. 2.3.2) alone on the current state and geometry */
+void orc_mix_only(orc* o);
 void orc_get_state(const orc* o, double* Q, double* alpha, double* phi, int32_t* chi, double* t);
 void orc_set_state(orc* o, const double* Q, const double* phi, const int32_t* chi, double t);
 void orc_totals(const orc* o, double* totals, double* ledger);

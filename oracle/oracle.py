@@ -68,6 +68,7 @@ def lib():
         _lib.orc_step_taped.argtypes = [P, C.c_double, dp, u8p, dp]
         _lib.orc_replay_step.argtypes = [P, dp, u8p, C.c_double]
         _lib.orc_set_conserved.argtypes = [P, dp]
+        _lib.orc_mix_only.argtypes = [P]
         _lib.orc_totals.argtypes = [P, dp, dp]
         _lib.orc_counters.argtypes = [P, C.POINTER(C.c_int64)]
         _lib.orc_last_dt.restype = C.c_double
@@ -165,6 +166,10 @@ class Oracle:
         """Replace the conserved state of the interior cells ([N][NV][cells])."""
         Q = np.ascontiguousarray(Q, np.float64)
         lib().orc_set_conserved(self.h, _dp(Q))
+
+    def mix_only(self):
+        """The mixing pass alone on the current state and geometry."""
+        lib().orc_mix_only(self.h)
 
     def step_taped(self, t_end=np.inf):
         """One step that records its replay tape (the level set at the start of

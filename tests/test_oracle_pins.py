@@ -507,3 +507,115 @@ def test_tait_water_column_in_pressure_equilibrium_stays_at_rest():
     assert o.step(40, 10.0) == 0
     Q = o.state()["Q"]
     assert np.abs(Q[:, 1:3]).max() < 1e-11
+
+
+def _neighbourhood_bounds(U, on, shape, dim):
+    """Per-variable min / max of U over the 3^d block of every cell, counting
+    only cells where `on` holds (U: [NV][cells], on: [cells])."""
+    nv = U.shape[0]
+    Ug = U.reshape((nv,) + tuple(shape[::-1]))
+    og = on.reshape(tuple(shape[::-1]))
+    lo = np.full_like(Ug, np.inf)
+    hi = np.full_like(Ug, -np.inf)
+    import itertools
+    axes = list(range(1, dim + 1))
+    for off in itertools.product((-1, 0, 1), repeat=dim):
+        sh = np.roll(Ug, shift=off, axis=axes)
+        so = np.roll(og, shift=off, axis=[a - 1 for a in axes])
+        # no wrap-around: cells rolled in from the opposite side do not count
+        valid = so.copy()
+        for k, o in enumerate(off):
+            if o == 0:
+                continue
+            idx = [slice(None)] * dim
+            idx[k] = 0 if o == 1 else -1
+            valid[tuple(idx)] = False
+        lo = np.where(valid[None], np.minimum(lo, sh), lo)
+        hi = np.where(valid[None], np.maximum(hi, sh), hi)
+    return lo.reshape(nv, -1), hi.reshape(nv, -1)
+
+
+@pytest.mark.parametrize("dim,n,seed", [(2, (40, 30), 3), (2, (33, 41), 8), (3, (14, 12, 10), 2)])
+def test_mixing_is_conservative_and_convex(dim, n, seed):
+    """Reading 16 on random physical states over a random multi-material
+    geometry: the mixing pass conserves every material's content, and every
+    mixed per-volume state lies within the range of the pre-mixing states of
+    its 3^d block (the weight sums are limited to one, so no pair exchange
+    extrapolates)."""
+    case = cs.random_case(dim, n, 3, seed)
+    o = orc.Oracle(case)
+    st = o.state()
+    alpha = st["alpha"]
+    rng = np.random.default_rng(seed)
+    N, NV, cells = case.nmat, case.nv, case.cells
+    Q = np.zeros((N, NV, cells))
+    g = np.asarray(case.gamma)
+    for m in range(N):
+        rho = rng.uniform(0.5, 2.0, cells)
+        vel = rng.uniform(-1.0, 1.0, (dim, cells))
+        p = rng.uniform(0.5, 2.0, cells)
+        E = p / (g[m] - 1.0) + 0.5 * rho * (vel ** 2).sum(0)
+        U = np.concatenate([rho[None], rho * vel, E[None]])
+        Q[m] = alpha[m] * U
+    o.set_conserved(Q)
+    tot0, _ = o.totals()
+    o.mix_only()
+    assert o.counters()["small"] > 20 and o.counters()["merge"] == 0
+    tot1, _ = o.totals()
+    assert np.abs(tot1 - tot0).max() <= 1e-13 * np.abs(tot0).max()
+    Q1 = o.state()["Q"]
+    changed = 0
+    for m in range(N):
+        on = alpha[m] > 0
+        U0 = np.where(on, Q[m] / np.where(on, alpha[m], 1.0), 0.0)
+        U1 = np.where(on, Q1[m] / np.where(on, alpha[m], 1.0), 0.0)
+        lo, hi = _neighbourhood_bounds(U0, on, case.n, dim)
+        moved = on & np.any(Q1[m] != Q[m], axis=0)
+        changed += int(moved.sum())
+        tol = 1e-12 * np.abs(U0).max()
+        assert np.all(U1[:, moved] >= lo[:, moved] - tol)
+        assert np.all(U1[:, moved] <= hi[:, moved] + tol)
+    assert changed > 20
+
+
+def test_mixing_limit_keeps_a_crowded_target_in_range():
+    """A disc of radius 1.1 h centred on a cell: its eight rim cells are small
+    (alpha 0.46 on the sides, 0.07 on the corners) and all mix into the
+    centre cell, whose weights then sum to about 1.34. Unlimited pair
+    exchanges would take the centre's density below every state around it
+    (2 - 1.34 (2 - 1) = 0.66 < 1); the limit of reading 16 keeps it at the
+    rim's density (a convex combination), and the content of the disc
+    material is conserved."""
+    n, r0 = 9, 1.1
+    x, y = cs.centres((n, n), (0.0, 0.0), (float(n), float(n)))
+    r = np.hypot(x - 4.5, y - 4.5)
+    chi = (r < r0).astype(np.int32)
+    phi = np.abs(r - r0)
+    prim = np.zeros((2, 4, n * n))
+    prim[:, 0] = 1.0
+    prim[:, 3] = 1.0
+    case = cs.Case("disc", 2, (n, n), (0.0, 0.0), (float(n), float(n)), [[1, 1], [1, 1]], [1.4, 1.4], [0.0, 0.0],
+                   phi, chi, prim, 1.0)
+    o = orc.Oracle(case)
+    st = o.state()
+    alpha = st["alpha"]
+    centre = 4 * n + 4
+    assert alpha[1, centre] > 0.9
+    rim = [c for c in range(n * n) if 0.0 < alpha[1, c] < 0.5]
+    assert len(rim) == 8
+    # per-volume states of the disc material: density 2 at the centre, 1 on the rim
+    Q = st["Q"].copy()
+    U = np.zeros((4, n * n))
+    U[0] = 1.0
+    U[0, centre] = 2.0
+    U[3] = 1.0 / 0.4
+    Q[1] = alpha[1] * U
+    o.set_conserved(Q)
+    tot0, _ = o.totals()
+    o.mix_only()
+    Q1 = o.state()["Q"]
+    tot1, _ = o.totals()
+    assert abs(tot1[1, 0] - tot0[1, 0]) <= 1e-14 * tot0[1, 0]
+    rho_c = Q1[1, 0, centre] / alpha[1, centre]
+    assert rho_c >= 1.0 - 1e-12          # not below the rim's density
+    assert rho_c < 1.2                   # the centre did mix
