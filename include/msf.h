@@ -171,7 +171,12 @@ msf_status msf_set_levelset(msf_ctx* ctx, int32_t instance, const double* phi, c
 /* Advance every instance by up to n_steps full TVD-RK3 steps (three stages of
  * Eq. discretized_equ with the beta_s weights of Eq. local-advection), or
  * until t_end: the last time step is clipped so that t lands on t_end; an
- * instance already at t_end does nothing. Work is enqueued on opt.stream.
+ * instance already at t_end does nothing. The time step is
+ * cfl / max over the cells of sum_d (|u_d| + c) / h_d over the materials
+ * present (Sec. 3), on a grid with a free surface also over |u*| / h of its
+ * cut cells (the surface moves at the u* of its wave curve). The stages are
+ * those of opt.rk_stages (3, or the 2 of Sec. 3). Work is enqueued on
+ * opt.stream.
  * sync = 1: wait and report device-detected errors (MSF_ENONFINITE,
  * MSF_ENEGATIVE, MSF_EBAND); sync = 0: return after enqueueing (errors are
  * reported by the next synchronising call). After a device-detected error the
