@@ -619,3 +619,38 @@ def test_mixing_limit_keeps_a_crowded_target_in_range():
     rho_c = Q1[1, 0, centre] / alpha[1, centre]
     assert rho_c >= 1.0 - 1e-12          # not below the rim's density
     assert rho_c < 1.2                   # the centre did mix
+
+
+def test_triple_point_light_side_shock_runs_ahead():
+    """Sec. 3.3: the shock in the light upper gas runs ahead of the shock in
+    the dense lower gas (rho2 c2 > rho3 c3). Near the walls y = 0 and y = 3
+    the flow is still one-dimensional at t = 1, so each shock sits where the
+    exact solution of its Riemann problem puts it (mid-pressure crossing,
+    within one cell)."""
+    nx, ny = 112, 48
+    case = cs.triple_point(nx, ny)
+    o = orc.Oracle(case)
+    assert o.step(100000, 1.0) == 0
+    st = o.state()
+    x, _ = cs.centres((nx, ny), (0.0, 0.0), (7.0, 3.0))
+    g = np.asarray(case.gamma)
+    p = np.zeros(nx * ny)
+    for m in range(3):
+        on = st["alpha"][m] > 0.5
+        q = st["Q"][m][:, on] / st["alpha"][m, on]
+        p[on] = (g[m] - 1.0) * (q[3] - 0.5 * (q[1] ** 2 + q[2] ** 2) / q[0])
+    P, X = p.reshape(ny, nx), x.reshape(ny, nx)[0]
+    h = 7.0 / nx
+    fronts = {}
+    for name, rows, right in (("upper", slice(ny - 6, ny), er.Side(0.125, 0.0, 0.1, 1.5, 0.0)),
+                              ("lower", slice(0, 6), er.Side(1.0, 0.0, 0.1, 1.4, 0.0))):
+        rp = er.Riemann(er.Side(1.0, 0.0, 1.0, 1.5, 0.0), right)
+        kind, speed = rp.right_wave()
+        assert kind == "shock"
+        pr = P[rows].mean(0)
+        mid = 0.5 * (0.1 + rp.ps)
+        i = np.nonzero(pr > mid)[0].max()                 # last cell above mid-pressure
+        xf = X[i] + h * (pr[i] - mid) / (pr[i] - pr[i + 1])
+        assert abs(xf - (1.0 + speed * 1.0)) < h, (name, xf, 1.0 + speed)
+        fronts[name] = xf
+    assert fronts["upper"] > fronts["lower"] + 0.5
