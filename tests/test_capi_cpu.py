@@ -70,7 +70,12 @@ def _args(msf, **over):
 
 @pytest.mark.parametrize("bad", [
     dict(n=[0, 1, 1]), dict(dim=0), dict(lo=[1.0, 0, 0], hi=[0.0, 1, 1]),
-    dict(bc=[[5, 0], [0, 0], [0, 0]]), dict(cfl=0.0), dict(ext_sweeps=0)])
+    dict(bc=[[5, 0], [0, 0], [0, 0]]), dict(cfl=0.0), dict(ext_sweeps=0),
+    # axisymmetric grid below the axis, unknown geometry, free-surface ambient
+    # out of range, without density, with a drive ramp that ends before it starts
+    dict(geom=1, lo=[-0.5, 0.0, 0.0]), dict(geom=2), dict(fs_mat=7),
+    dict(fs_mat=2, fs_rho=0.0, fs_p0=1.0, fs_t0=0.0, fs_t1=1.0, fs_p1=1.0),
+    dict(fs_mat=2, fs_rho=1.0, fs_p0=1.0, fs_t0=1.0, fs_t1=0.5, fs_p1=1.0)])
 def test_create_rejects_bad_arguments_on_host(msf, bad):
     g, eos, o = _args(msf, **bad)
     h = C.c_void_p()
