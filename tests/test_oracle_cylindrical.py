@@ -184,3 +184,35 @@ def test_icf_quarter_plane_matches_cylindrical_grid():
     r_in1, r_out1 = np.sqrt(2 * v0), np.sqrt(2 * (v0 + v1))
     assert r_in1 < 0.5 and r_out1 < 0.7          # both interfaces have moved in
     assert abs(r_in2 - r_in1) < 2e-3 and abs(r_out2 - r_out1) < 2e-3
+
+
+def _icf_inner_radius_history(n, t_end=0.3, chunk=20):
+    case = cs.icf_implosion(n, t_end=t_end)
+    o = orc.Oracle(case)
+    (x,) = cs.centres((n,), (0.0,), (1.0,))
+    hist = []
+    while True:
+        assert o.step(chunk, t_end) == 0
+        st = o.state()
+        v0 = (st["alpha"][0] * x).sum() / n
+        hist.append((st["t"], np.sqrt(2.0 * v0)))
+        if st["t"] >= t_end:
+            return np.array(hist)
+
+
+def test_icf_inner_interface_stagnates_and_reexpands():
+    """Sec. 3.2: driven by p(t), the shell pushes the core inwards, the inner
+    interface decelerates to a minimum radius (stagnation) and the core then
+    re-expands; the minimum radius agrees between 160 and 320 cells to 2 %."""
+    h160 = _icf_inner_radius_history(160)
+    h320 = _icf_inner_radius_history(320)
+    mins = []
+    for h in (h160, h320):
+        k = int(np.argmin(h[:, 1]))
+        t_min, r_min = h[k]
+        assert 0.12 < t_min < 0.26                    # after the drive's ramp, before the end
+        assert r_min < 0.3 * 0.6                      # compressed well below r1 = 0.6
+        assert h[-1, 1] > r_min * 1.05                # re-expanded by t = 0.3
+        assert np.all(np.diff(h[: k + 1, 1]) <= 1e-12)   # monotone implosion up to stagnation
+        mins.append(r_min)
+    assert abs(mins[0] - mins[1]) < 0.02 * mins[1]
