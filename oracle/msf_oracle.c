@@ -33,9 +33,20 @@
  *   level set  local advection of each phi^r, HJ-WENO5 derivatives, then the
  *              reconstruction operator R (Sec. 2.2).
  *   mixing     conservative exchange of small-volume-fraction cells with
- *              neighbours along the normal after each sub-step (Sec. 2.3.2).
+ *              neighbours along the normal after each sub-step (Sec. 2.3.2);
+ *              non-physical states mix like small cells and every pair is
+ *              scaled so that the weights of a cell sum to at most one.
  *   scale sep. oddball cells, indicator swap and distance re-assignment
  *              (Sec. 2.3.3).
+ *   Case II    axisymmetric grid of one dimension (face areas r_f, volumes
+ *              r_i h, source p alpha / r of the radial momentum) and a held
+ *              free-surface ambient driven by p(t), u* from the two-shock wave
+ *              curve of the solved side, |u*| in the CFL bound (Sec. 3.2).
+ * Parity unpinned beyond agreement with the CUDA path and the invariants
+ * (conservation, equilibrium, symmetry, convergence, convexity) the tests
+ * check, because the paper prints no values for them: the ghost-extension
+ * and interface-velocity-extension sweeps, the mixing weights and band
+ * maintenance (reinitialisation of the non-cut band).
  * Compile with -ffp-contract=off: no fused multiply-add anywhere.
  */
 #include "msf_oracle.h"
