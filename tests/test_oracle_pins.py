@@ -654,3 +654,36 @@ def test_triple_point_light_side_shock_runs_ahead():
         assert abs(xf - (1.0 + speed * 1.0)) < h, (name, xf, 1.0 + speed)
         fronts[name] = xf
     assert fronts["upper"] > fronts["lower"] + 0.5
+
+
+def test_ghost_states_extend_along_the_normal():
+    """Reading 8: the ghost state of a material beyond a planar interface is its
+    real state carried along the interface normal. With the interface at
+    x = const and a density that varies only along y (a contact equilibrium at
+    rest), every ghost cell of the left material holds exactly the real state
+    of its own row; averaging over neighbours across rows would not."""
+    nx, ny = 24, 16
+    x, y = (a.ravel() for a in cs.centres((nx, ny), (0.0, 0.0), (1.5, 1.0)))
+    x0 = 0.7031
+    chi = (x > x0).astype(np.int32)
+    phi = np.abs(x - x0)
+    prim = np.zeros((2, 4, nx * ny))
+    prim[0, 0] = 1.0 + 0.5 * np.sin(2.0 * np.pi * y)
+    prim[0, 3] = 1.0
+    prim[1, 0] = 0.2
+    prim[1, 3] = 1.0
+    case = cs.Case("planar", 2, (nx, ny), (0.0, 0.0), (1.5, 1.0), [[1, 1], [1, 1]], [1.4, 1.6], [0.0, 0.0],
+                   phi, chi, prim, 1.0)
+    o = orc.Oracle(case, scale_sep=0, reinit=0)
+    assert o.step(1, 1.0) == 0
+    uh = o.debug(1).reshape(2, 4, ny, nx)            # stencil states [m][v][y][x]
+    st = o.state()
+    a0 = st["alpha"][0].reshape(ny, nx)
+    i_last = int(np.nonzero(a0[0] == 1.0)[0].max())  # last full cell of material 0 in a row
+    ghost = [i for i in range(i_last + 2, nx) if np.all(np.isfinite(uh[0, 0, :, i]))]
+    assert len(ghost) >= 3
+    for i in ghost:
+        for v in range(4):
+            assert np.array_equal(uh[0, v, :, i], uh[0, v, :, i_last]), (i, v)
+    # and the rows differ, so a cross-row average would show
+    assert np.ptp(uh[0, 0, :, i_last]) > 0.5
