@@ -687,3 +687,37 @@ def test_ghost_states_extend_along_the_normal():
             assert np.array_equal(uh[0, v, :, i], uh[0, v, :, i_last]), (i, v)
     # and the rows differ, so a cross-row average would show
     assert np.ptp(uh[0, 0, :, i_last]) > 0.5
+
+
+def test_moving_contact_is_carried_exactly():
+    """Two materials at one pressure and one velocity u (a contact moving at
+    u, Sec. 2.3.2's interface condition): the HLLC interface velocity is u,
+    its extension into the band (reading 12) carries u to every band cell, the
+    level set (reading 15) moves the interface to x0 + u t, and velocity and
+    pressure stay uniform (no oscillations at the moving interface)."""
+    nx, ny, u, t_end = 48, 8, 0.3, 0.5
+    x, y = (a.ravel() for a in cs.centres((nx, ny), (0.0, 0.0), (1.5, 0.25)))
+    x0 = 0.4031
+    chi = (x > x0).astype(np.int32)
+    phi = np.abs(x - x0)
+    prim = np.zeros((2, 4, nx * ny))
+    prim[0, 0], prim[0, 1], prim[0, 3] = 1.0, u, 1.0
+    prim[1, 0], prim[1, 1], prim[1, 3] = 0.2, u, 1.0
+    case = cs.Case("moving_contact", 2, (nx, ny), (0.0, 0.0), (1.5, 0.25), [[0, 0], [1, 1]], [1.4, 1.6],
+                   [0.0, 0.0], phi, chi, prim, t_end)
+    o = orc.Oracle(case)
+    assert o.step(100000, t_end) == 0
+    st = o.state()
+    h = 1.5 / nx
+    x_int = st["alpha"][0].reshape(ny, nx).sum(1) * h
+    assert np.abs(x_int - (x0 + u * t_end)).max() < 1e-5 * h
+    vel = o.debug(3).reshape(3, ny, nx)[0]
+    band = vel != 0.0
+    assert band.sum() >= 5 * ny and np.abs(vel[band] - u).max() < 1e-6
+    g = np.asarray(case.gamma)
+    for m in range(2):
+        on = st["alpha"][m] > 0
+        q = st["Q"][m][:, on] / st["alpha"][m, on]
+        um = q[1] / q[0]
+        pm = (g[m] - 1.0) * (q[3] - 0.5 * (q[1] ** 2 + q[2] ** 2) / q[0])
+        assert np.abs(um - u).max() < 1e-6 and np.abs(pm - 1.0).max() < 1e-6
