@@ -711,6 +711,12 @@ def test_moving_contact_is_carried_exactly():
     h = 1.5 / nx
     x_int = st["alpha"][0].reshape(ny, nx).sum(1) * h
     assert np.abs(x_int - (x0 + u * t_end)).max() < 1e-5 * h
+    # the level set stays the distance to the interface near it (band maintenance,
+    # reading 18) and the indicator is the exact side
+    d = np.abs(x - (x0 + u * t_end))
+    near = d < 5 * h
+    assert np.abs(st["phi"][near] - d[near]).max() < 1e-5 * h
+    assert np.array_equal(st["chi"], (x > x0 + u * t_end).astype(np.int32))
     vel = o.debug(3).reshape(3, ny, nx)[0]
     band = vel != 0.0
     assert band.sum() >= 5 * ny and np.abs(vel[band] - u).max() < 1e-6
