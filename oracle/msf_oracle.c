@@ -42,11 +42,13 @@
  *              r_i h, source p alpha / r of the radial momentum) and a held
  *              free-surface ambient driven by p(t), u* from the two-shock wave
  *              curve of the solved side, |u*| in the CFL bound (Sec. 3.2).
- * Parity unpinned beyond agreement with the CUDA path and the invariants
- * (conservation, equilibrium, symmetry, convergence, convexity) the tests
- * check, because the paper prints no values for them: the ghost-extension
- * and interface-velocity-extension sweeps, the mixing weights and band
- * maintenance (reinitialisation of the non-cut band).
+ * The paper prints no values for the ghost-extension and interface-velocity
+ * sweeps, the mixing weights and band maintenance (reinitialisation of the
+ * non-cut band); the tests pin them through special cases with exact answers
+ * (a planar interface: ghost states of their own row; a moving contact: the
+ * velocity u in the band, the interface at x0 + u t, phi its distance; a
+ * crowded mixing target kept in range) and invariants (conservation,
+ * equilibrium, symmetry, convexity), not through general values.
  * Compile with -ffp-contract=off: no fused multiply-add anywhere.
  */
 #include "msf_oracle.h"
