@@ -727,3 +727,32 @@ def test_moving_contact_is_carried_exactly():
         um = q[1] / q[0]
         pm = (g[m] - 1.0) * (q[3] - 0.5 * (q[1] ** 2 + q[2] ** 2) / q[0])
         assert np.abs(um - u).max() < 1e-6 and np.abs(pm - 1.0).max() < 1e-6
+
+
+@pytest.mark.parametrize("dim,n,nmat,seed", [(2, (40, 31), 4, 5), (3, (12, 11, 10), 3, 2)])
+def test_volume_fractions_partition_the_cells_the_method_closes(dim, n, nmat, seed):
+    """Sec. 2.3.1: the volume fractions lie in [0, 1]; in a cell with more than
+    two materials the conservation correction (Eq. vol_corr2) makes them sum
+    to one, and in a cell whose 3^d block holds at most two materials the two
+    simplex fractions are complementary. (Next to a junction, a cell with one
+    or two positive fractions whose block holds three materials is not closed
+    by the method: its fractions can sum to less than one.)"""
+    import itertools
+    case = cs.random_case(dim, n, nmat, seed)
+    o = orc.Oracle(case)
+    st = o.state()
+    a, chi = st["alpha"], st["chi"]
+    assert a.min() >= 0.0 and a.max() <= 1.0
+    s = a.sum(0)
+    multi = (a > 0).sum(0) >= 3
+    assert multi.sum() >= 1
+    assert np.abs(s[multi] - 1.0).max() < 1e-14
+    shape = tuple(case.n[::-1])
+    cg = chi.reshape(shape)
+    seen = np.zeros(shape + (case.nmat,), bool)
+    for off in itertools.product((-1, 0, 1), repeat=dim):
+        sh = np.roll(cg, shift=off, axis=tuple(range(dim)))
+        for m in range(case.nmat):
+            seen[..., m] |= sh == m
+    two = (seen.sum(-1) <= 2).reshape(-1)
+    assert np.abs(s[two] - 1.0).max() < 1e-14
