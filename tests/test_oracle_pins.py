@@ -756,3 +756,35 @@ def test_volume_fractions_partition_the_cells_the_method_closes(dim, n, nmat, se
             seen[..., m] |= sh == m
     two = (seen.sum(-1) <= 2).reshape(-1)
     assert np.abs(s[two] - 1.0).max() < 1e-14
+
+
+def test_stiffened_gas_interface_converges_to_exact():
+    """A stiffened gas (gamma 3, pinf 1) against an ideal gas (Sec. 2.1's two
+    EOS in one Riemann problem): a rarefaction into the stiffened gas, the
+    material interface and a shock into the ideal gas. L1(rho) against the
+    exact solution (cell averages) falls at first order or better."""
+    L = (1.0, 0.0, 2.0, 3.0, 1.0)     # rho, u, p, gamma, pinf
+    R = (0.5, 0.0, 0.5, 1.4, 0.0)
+    t_end, x0 = 0.15, 0.5
+    rp = er.Riemann(er.Side(*L), er.Side(*R))
+    assert rp.left_wave()[0] == "fan" and rp.right_wave()[0] == "shock"
+    errs = []
+    for n in (100, 200, 400):
+        (x,) = cs.centres((n,), (0.0,), (1.0,))
+        chi = (x > x0).astype(np.int32)
+        phi = np.abs(x - x0)
+        prim = np.zeros((2, 3, n))
+        prim[0] = np.array(L[:3])[:, None]
+        prim[1] = np.array(R[:3])[:, None]
+        case = cs.Case("stiff_tube", 1, (n,), (0.0,), (1.0,), [[0, 0]], [L[3], R[3]], [L[4], R[4]], phi, chi,
+                       prim, t_end)
+        o = orc.Oracle(case)
+        assert o.step(100000, t_end) == 0
+        rho = o.state()["Q"][:, 0].sum(0)
+        h = 1.0 / n
+        sub = (np.arange(16) + 0.5) / 16 - 0.5
+        exact = np.array([np.mean([rp.sample((xi + s * h - x0) / t_end)[0] for s in sub]) for xi in x])
+        errs.append(np.abs(rho - exact).sum() * h)
+    assert errs[0] < 5e-3
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 0.6, (errs, rates)
