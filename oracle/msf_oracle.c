@@ -241,13 +241,13 @@ double orc_weno5(double a, double b, double c, double d, double e, double eps) {
   s2 = 13.0 / 12.0 * t * t;
   t = 3.0 * c - 4.0 * d + e;
   s2 = s2 + 0.25 * t * t;
+  /* Jiang & Shu's unnormalised weights a_k = d_k / (eps + beta_k)^2 with the
+     ideal weights d = (1/10, 6/10, 3/10); the value is sum_k w_k q_k with the
+     normalised weights w_k = a_k / sum_j a_j */
   double b0 = eps + s0, b1 = eps + s1, b2 = eps + s2;
-  /* the weights 0.1/b0^2, 0.6/b1^2, 0.3/b2^2, each multiplied by
-     b0^2 b1^2 b2^2: the normalised weights are unchanged */
-  double p0 = b0 * b0, p1 = b1 * b1, p2 = b2 * b2;
-  double a0 = 0.1 * (p1 * p2);
-  double a1 = 0.6 * (p0 * p2);
-  double a2 = 0.3 * (p0 * p1);
+  double a0 = 0.1 / (b0 * b0);
+  double a1 = 0.6 / (b1 * b1);
+  double a2 = 0.3 / (b2 * b2);
   return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
 }
 
@@ -556,16 +556,29 @@ static void geometry(orc* o, const double* Qs) {
       }
     }
     /* the materials partition every face: apertures divided by their sum over
-       the local materials (two-material faces already sum to one) */
+       the local materials (two-material faces already sum to one). Next to a
+       junction the averaged vertex values can leave a face on which every
+       local field is <= 0; such a face goes to the indicators of the two cells
+       that share it (whole when they agree, half each otherwise), so that
+       every face is closed and both cells see the same apertures */
     for (int d = 0; d < D; d++)
       for (int side = 0; side < 2; side++) {
         double* A = side ? o->Ahi : o->Alo;
         double s = 0.0;
         for (int m = 0; m < N; m++)
           if ((o->xs[c] >> m) & 1u) s += A[AI(o, d, m, c)];
-        if (s > 0.0)
+        if (s > 0.0) {
           for (int m = 0; m < N; m++)
             if ((o->xs[c] >> m) & 1u) A[AI(o, d, m, c)] = A[AI(o, d, m, c)] / s;
+        } else {
+          int ca = o->chi[side ? c : c - o->st[d]], cb = o->chi[side ? c + o->st[d] : c];
+          if (ca == cb) {
+            A[AI(o, d, ca, c)] = 1.0;
+          } else {
+            A[AI(o, d, ca, c)] = 0.5;
+            A[AI(o, d, cb, c)] = 0.5;
+          }
+        }
       }
     /* conservation correction (Sec. 2.3.1, Eq. vol_corr2) */
     int np = 0;
@@ -1718,9 +1731,17 @@ void orc_set_state(orc* o, const double* Q, const double* phi, const int32_t* ch
 
 /* overwrite the conserved state of the interior cells (SoA [N][NV][cells]),
  * keeping the level set, the time and the counters */
-/* the mixing pass alone on the current state and geometry (a test hook: the
-   properties of reading 16 are pinned on it) */
+/* the mixing pass alone on the current state and geometry (a test hook: its
+   conservation, convexity and weight limit are pinned on it) */
 void orc_mix_only(orc* o) { mixing(o, o->Q); }
+
+/* the scale-separation pass alone on the current level set and geometry (a
+   test hook: the oddball choice and the distance re-assignment of Sec. 2.3.3
+   are pinned on it) */
+void orc_scale_sep_only(orc* o) {
+  scale_separation(o);
+  bc_phichi(o);
+}
 
 void orc_set_conserved(orc* o, const double* Q) {
   int N = o->N, NV = o->NV;
@@ -1778,6 +1799,12 @@ void orc_debug_field(const orc* o, int32_t which, double* out) {
         break;
       case 4: out[q] = o->mixed[c]; break;
       case 5: out[q] = o->smask[c]; break;
+      case 6:
+      case 7:
+        for (int d = 0; d < 3; d++)
+          for (int m = 0; m < N; m++)
+            out[((long)d * N + m) * ni + q] = (which == 6 ? o->Alo : o->Ahi)[AI(o, d, m, c)];
+        break;
       default: break;
     }
   }

@@ -68,6 +68,9 @@ int orc_replay_step(orc* o, const double* tphi, const uint8_t* tchi, double dt);
 void orc_set_conserved(orc* o, const double* Q);
 /* the mixing pass (Sec. 2.3.2) alone on the current state and geometry */
 void orc_mix_only(orc* o);
+/* the scale-separation pass (Sec. 2.3.3) alone on the current level set and
+   geometry, then the boundary fill of (phi, chi) */
+void orc_scale_sep_only(orc* o);
 void orc_get_state(const orc* o, double* Q, double* alpha, double* phi, int32_t* chi, double* t);
 void orc_set_state(orc* o, const double* Q, const double* phi, const int32_t* chi, double t);
 void orc_totals(const orc* o, double* totals, double* ledger);
@@ -75,7 +78,8 @@ void orc_counters(const orc* o, int64_t* c);
 double orc_last_dt(const orc* o);
 int orc_error(const orc* o);
 /* intermediate fields of the last stage, interior cells: 0 alpha [N], 1 Uhat [N][nv],
-   2 exchange X [N][nv], 3 interface velocity [3], 4 mixed flag, 5 step mask */
+   2 exchange X [N][nv], 3 interface velocity [3], 4 mixed flag, 5 step mask,
+   6 lower-face apertures [3][N], 7 upper-face apertures [3][N] */
 void orc_debug_field(const orc* o, int32_t which, double* out);
 
 /* building blocks, exported for pins */

@@ -69,6 +69,7 @@ def lib():
         _lib.orc_replay_step.argtypes = [P, dp, u8p, C.c_double]
         _lib.orc_set_conserved.argtypes = [P, dp]
         _lib.orc_mix_only.argtypes = [P]
+        _lib.orc_scale_sep_only.argtypes = [P]
         _lib.orc_totals.argtypes = [P, dp, dp]
         _lib.orc_counters.argtypes = [P, C.POINTER(C.c_int64)]
         _lib.orc_last_dt.restype = C.c_double
@@ -171,6 +172,10 @@ class Oracle:
         """The mixing pass alone on the current state and geometry."""
         lib().orc_mix_only(self.h)
 
+    def scale_sep_only(self):
+        """The scale-separation pass alone on the current level set and geometry."""
+        lib().orc_scale_sep_only(self.h)
+
     def step_taped(self, t_end=np.inf):
         """One step that records its replay tape (the level set at the start of
         each stage and after the last level-set stage, and the time step);
@@ -209,7 +214,7 @@ class Oracle:
         return lib().orc_last_dt(self.h)
 
     def debug(self, which):
-        sizes = {0: self.N, 1: self.N * self.NV, 2: self.N * self.NV, 3: 3, 4: 1, 5: 1}
+        sizes = {0: self.N, 1: self.N * self.NV, 2: self.N * self.NV, 3: 3, 4: 1, 5: 1, 6: 3 * self.N, 7: 3 * self.N}
         out = np.zeros(sizes[which] * self.cells)
         lib().orc_debug_field(self.h, int(which), _dp(out))
         return out
