@@ -50,12 +50,21 @@
  * crowded mixing target kept in range) and invariants (conservation,
  * equilibrium, symmetry, convexity), not through general values.
  * Compile with -ffp-contract=off: no fused multiply-add anywhere.
+ *
+ * Built twice: single-threaded (the tests' oracle), and with -fopenmp for
+ * the timed CPU baseline on all host cores. The OpenMP pragmas only split
+ * loops whose iterations each write their own cell; shared error flags and
+ * counters are updated atomically, maxima are order-free and every sum keeps
+ * its serial order, so both builds give the same bits.
  */
 #include "msf_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define G 4 /* halo layers */
 
@@ -129,6 +138,15 @@ static int popc(unsigned x) {
   while (x) { k += (int)(x & 1u); x >>= 1; }
   return k;
 }
+/* sticky error flag and event counters, shared by the cells of a loop */
+static void set_err(orc* o, int f) {
+#pragma omp atomic
+  o->err |= f;
+}
+static void count(orc* o, int k) {
+#pragma omp atomic
+  o->cnt[k]++;
+}
 
 /* ------------------------------------------------------------------ */
 /* EOS (Sec. 2.1, 2.3.2): stiffened gas, or Tait's equation             */
@@ -170,7 +188,7 @@ static double sound2(const orc* o, int m, double rho, double p) {
 static double sound(orc* o, int m, double rho, double p) {
   double c2 = sound2(o, m, rho, p);
   if (!(rho > 0.0) || !(c2 > 0.0)) {
-    o->err |= ORC_ENEGATIVE;
+    set_err(o, ORC_ENEGATIVE);
     c2 = c2 > 0.0 ? c2 : 0.0;
   }
   return sqrt(c2);
@@ -214,6 +232,7 @@ static void hold_ambient(orc* o, double* Qc, double t) {
   w[0] = o->p.fs_rho;
   w[o->D + 1] = fs_pressure(o, t);
   prim_to_cons(o, F, w, u);
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) {
     if (!interior_c(o, c)) continue;
     double a = o->alpha[MI(o, F, c)];
@@ -464,6 +483,7 @@ static int bc_src(const orc* o, int d, int idx, int* side, int* flip) {
 }
 static void bc_phichi(orc* o) {
   for (int d = 0; d < o->D; d++) {
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < o->ncell; c++) {
       int ijk[3], side;
       coords(o, c, ijk);
@@ -488,6 +508,7 @@ static void bc_phichi(orc* o) {
 /* ------------------------------------------------------------------ */
 static void compute_xs(orc* o) {
   int D = o->D;
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) {
     int ijk[3];
     coords(o, c, ijk);
@@ -506,6 +527,7 @@ static void step_band(orc* o) {
   int D = o->D;
   const int R = 4;
   compute_xs(o);
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) {
     o->smask[c] = 0;
     o->inB[c] = 0;
@@ -530,6 +552,7 @@ static void geometry(orc* o, const double* Qs) {
   /* Qs == NULL: raw volume fractions, no correction */
   int N = o->N, D = o->D;
   compute_xs(o);
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) {
     o->mixed[c] = 0;
     if (!interior_c(o, c)) continue;
@@ -586,9 +609,9 @@ static void geometry(orc* o, const double* Qs) {
     for (int m = 0; m < N; m++)
       if (o->alpha[MI(o, m, c)] > 0.0) { np++; sum += o->alpha[MI(o, m, c)]; }
     if (np >= 3 && Qs) {
-      o->cnt[ORC_C_MULTI]++;
+      count(o, ORC_C_MULTI);
       double rem = 1.0 - sum;
-      if (rem != 0.0) o->cnt[ORC_C_CORRECTED]++;
+      if (rem != 0.0) count(o, ORC_C_CORRECTED);
       /* apply to the lightest material (alpha rho = Q_rho); overflow below zero
          moves on to the next lightest */
       uint8_t used = 0;
@@ -647,6 +670,7 @@ static void prim_extend(orc* o, const double* Qs) {
   int N = o->N, NV = o->NV, D = o->D;
   double nanv = nan("");
   for (int m = 0; m < N; m++) {
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < o->ncell; c++) {
       o->fill[MI(o, m, c)] = 0;
       o->isreal[MI(o, m, c)] = 0;
@@ -662,10 +686,12 @@ static void prim_extend(orc* o, const double* Qs) {
       }
     }
     for (int sw = 0; sw < o->p.ext_sweeps; sw++) {
+#pragma omp parallel for schedule(static)
       for (long c = 0; c < o->ncell; c++) {
         o->fillt[MI(o, m, c)] = o->fill[MI(o, m, c)];
         for (int v = 0; v < NV; v++) o->Wt[QI(o, m, v, c)] = o->W[QI(o, m, v, c)];
       }
+#pragma omp parallel for schedule(static)
       for (long c = 0; c < o->ncell; c++) {
         if (!o->inB[c] || !((o->smask[c] >> m) & 1u) || o->isreal[MI(o, m, c)]) continue;
         double n[3];
@@ -697,6 +723,7 @@ static void prim_extend(orc* o, const double* Qs) {
   }
   /* stencil state of every interior cell */
   for (int m = 0; m < N; m++)
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < o->ncell; c++) {
       if (!interior_c(o, c)) continue;
       double u[5];
@@ -726,6 +753,7 @@ static void prim_extend(orc* o, const double* Qs) {
 static void bc_uhat(orc* o) {
   int N = o->N, NV = o->NV, D = o->D;
   for (int d = 0; d < D; d++)
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < o->ncell; c++) {
       int ijk[3], side;
       coords(o, c, ijk);
@@ -759,6 +787,7 @@ static void bc_uhat(orc* o) {
 static void compute_dt(orc* o, double t_end) {
   int N = o->N, D = o->D;
   double lam = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : lam)
   for (long c = 0; c < o->ncell; c++) {
     if (!interior_c(o, c)) continue;
     for (int m = 0; m < N; m++) {
@@ -775,6 +804,7 @@ static void compute_dt(orc* o, double t_end) {
   /* a free surface moves at the u* of its wave curve, which the material
      states do not bound: its cut cells enter the bound with |u*| */
   if (o->p.fs_mat >= 0)
+#pragma omp parallel for schedule(static) reduction(max : lam)
     for (long c = 0; c < o->ncell; c++) {
       if (!o->cut[c] || !(o->alpha[MI(o, o->p.fs_mat, c)] > 0.0)) continue;
       double s = 0.0;
@@ -791,7 +821,9 @@ static void compute_dt(orc* o, double t_end) {
 /* ------------------------------------------------------------------ */
 static void interface_exchange(orc* o, const double* Qs, double ts) {
   int N = o->N, NV = o->NV, D = o->D;
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < (long)N * NV * o->ncell; i++) o->X[i] = 0.0;
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) {
     o->cut[c] = 0;
     for (int d = 0; d < 3; d++) o->vel[d * o->ncell + c] = 0.0;
@@ -801,7 +833,7 @@ static void interface_exchange(orc* o, const double* Qs, double ts) {
       if (present(o, c, m)) np++;
     if (np < 2) continue;
     o->cut[c] = 1;
-    o->cnt[ORC_C_CUT]++;
+    count(o, ORC_C_CUT);
     /* the heaviest two present materials by alpha rho */
     int eta = -1, xi = -1;
     for (int m = 0; m < N; m++)
@@ -815,7 +847,7 @@ static void interface_exchange(orc* o, const double* Qs, double ts) {
     normal_m(o, c, R, n); /* normal of the heavier material, pointing into it */
     double uL[5], uR[5], wL[5], wR[5];
     for (int v = 0; v < NV; v++) { uL[v] = o->Uh[QI(o, L, v, c)]; uR[v] = o->Uh[QI(o, R, v, c)]; }
-    if (isnan(uL[0]) || isnan(uR[0])) { o->err |= ORC_EBAND; continue; }
+    if (isnan(uL[0]) || isnan(uR[0])) { set_err(o, ORC_EBAND); continue; }
     cons_to_prim(o, L, uL, wL);
     cons_to_prim(o, R, uR, wR);
     double unl = 0.0, unr = 0.0;
@@ -842,10 +874,13 @@ static void interface_exchange(orc* o, const double* Qs, double ts) {
     /* the pair's interface state acts on the boundary segment of every other
        present material, S^m = sum_f A^m_f |f| n_f^out (pointing into m);
        material R takes minus their sum, so sum_m X^m = 0 exactly and with
-       two materials X^R = -X^L as in the reduced model */
+       two materials X^R = -X^L as in the reduced model. For comparison,
+       literal_reduced lets only the pair exchange (X^R from S^R, X^L = -X^R,
+       the other materials nothing), and literal_normal uses |S^m| n^m. */
     double XR[5] = {0, 0, 0, 0, 0};
+    const int lit = o->p.literal_reduced;
     for (int m = 0; m < N; m++) {
-      if (m == R || !present(o, c, m)) continue;
+      if (lit ? m != R : (m == R || !present(o, c, m))) continue;
       double S[3] = {0, 0, 0}, nS = 0.0;
       if (cyl(o)) {
         /* interface area r_I n: the faces' r_f A_f less the wedge side alpha h */
@@ -855,6 +890,13 @@ static void interface_exchange(orc* o, const double* Qs, double ts) {
       } else {
         for (int d = 0; d < D; d++) S[d] = (o->Ahi[AI(o, d, m, c)] - o->Alo[AI(o, d, m, c)]) * o->farea[d];
       }
+      if (o->p.literal_normal) {
+        double nm[3], len = 0.0;
+        normal_m(o, c, m, nm);
+        for (int d = 0; d < D; d++) len += S[d] * S[d];
+        len = sqrt(len);
+        for (int d = 0; d < D; d++) S[d] = len * nm[d];
+      }
       for (int d = 0; d < D; d++) nS += n[d] * S[d];
       for (int d = 0; d < D; d++) {
         o->X[QI(o, m, 1 + d, c)] = ps * S[d];
@@ -863,7 +905,10 @@ static void interface_exchange(orc* o, const double* Qs, double ts) {
       o->X[QI(o, m, D + 1, c)] = ps * us * nS;
       XR[D + 1] -= ps * us * nS;
     }
-    for (int v = 1; v < NV; v++) o->X[QI(o, R, v, c)] = XR[v];
+    if (lit)
+      for (int v = 1; v < NV; v++) o->X[QI(o, L, v, c)] = XR[v];
+    else
+      for (int v = 1; v < NV; v++) o->X[QI(o, R, v, c)] = XR[v];
     for (int d = 0; d < D; d++) o->vel[d * o->ncell + c] = us * n[d];
   }
 }
@@ -871,12 +916,15 @@ static void interface_exchange(orc* o, const double* Qs, double ts) {
 /* interface velocity extended into the band (used by Eq. local-advection) */
 static void extend_velocity(orc* o) {
   int D = o->D;
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) o->vf[c] = o->cut[c];
   for (int sw = 0; sw < o->p.vel_sweeps; sw++) {
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < o->ncell; c++) {
       o->vft[c] = o->vf[c];
       for (int d = 0; d < 3; d++) o->velt[d * o->ncell + c] = o->vel[d * o->ncell + c];
     }
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < o->ncell; c++) {
       if (!o->inB[c] || o->cut[c]) continue;
       double acc[3] = {0, 0, 0}, acc2[3] = {0, 0, 0};
@@ -930,7 +978,7 @@ static void face_flux(orc* o, long cL, int d, int m, double* Fh) {
     double w[5];
     for (int v = 0; v < NV; v++) U[q][v] = o->Uh[QI(o, m, v, k)];
     if (isnan(U[q][0])) {
-      o->err |= ORC_EBAND;
+      set_err(o, ORC_EBAND);
       for (int v = 0; v < NV; v++) Fh[v] = 0.0;
       return;
     }
@@ -959,7 +1007,8 @@ static void flux_update(orc* o, int s, const double* Qs, double* Qout) {
   double Fb[ORC_MAXM][5];
   memset(Fb, 0, sizeof(Fb));
   /* face fluxes: lower face of every cell with interior index 0..n_d along d */
-  for (int d = 0; d < D; d++)
+  for (int d = 0; d < D; d++) {
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < o->ncell; c++) {
       int ijk[3];
       coords(o, c, ijk);
@@ -975,18 +1024,38 @@ static void flux_update(orc* o, int s, const double* Qs, double* Qout) {
         double A = face_aperture(o, cL, c, d, m);
         if (A > 0.0 && m != o->p.fs_mat) {
           int lin = interior_c(o, cL), rin = interior_c(o, c);
-          if ((lin && !((o->smask[cL] >> m) & 1u)) || (rin && !((o->smask[c] >> m) & 1u))) o->err |= ORC_EBAND;
+          if ((lin && !((o->smask[cL] >> m) & 1u)) || (rin && !((o->smask[c] >> m) & 1u))) set_err(o, ORC_EBAND);
           face_flux(o, cL, d, m, Fh);
         }
         for (int v = 0; v < NV; v++) o->F[((long)(d * N + m) * NV + v) * o->ncell + c] = Fh[v];
+      }
+    }
+  }
+  /* boundary ledger: net inflow through the domain boundary faces, summed in
+     face order */
+  for (int d = 0; d < D; d++)
+    for (long c = 0; c < o->ncell; c++) {
+      int ijk[3];
+      coords(o, c, ijk);
+      int r = ijk[d] - o->off[d];
+      if (r != 0 && r != o->n[d]) continue;
+      int ok = 1;
+      for (int e = 0; e < D; e++)
+        if (e != d && (ijk[e] < o->off[e] || ijk[e] >= o->off[e] + o->n[e])) ok = 0;
+      if (!ok) continue;
+      long cL = c - o->st[d];
+      for (int m = 0; m < N; m++) {
+        double A = face_aperture(o, cL, c, d, m);
         double fa = cyl(o) ? face_r(o, ijk[0]) : o->farea[d];
-        if (r == 0)
-          for (int v = 0; v < NV; v++) Fb[m][v] += A * Fh[v] * fa;
-        if (r == o->n[d])
-          for (int v = 0; v < NV; v++) Fb[m][v] -= A * Fh[v] * fa;
+        for (int v = 0; v < NV; v++) {
+          double Fh = o->F[((long)(d * N + m) * NV + v) * o->ncell + c];
+          if (r == 0) Fb[m][v] += A * Fh * fa;
+          if (r == o->n[d]) Fb[m][v] -= A * Fh * fa;
+        }
       }
     }
   double beta = rk_beta(o, s), omb = 1.0 - rk_beta(o, s), dt = o->dt;
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) {
     if (!interior_c(o, c)) continue;
     for (int m = 0; m < N; m++) {
@@ -1028,7 +1097,7 @@ static void flux_update(orc* o, int s, const double* Qs, double* Qout) {
         if (m == o->p.fs_mat) L = 0.0;
         double qn = o->Q[QI(o, m, v, c)], qs = Qs[QI(o, m, v, c)];
         double q = beta * qn + omb * (qs + dt * L);
-        if (!isfinite(q)) o->err |= ORC_ENONFINITE;
+        if (!isfinite(q)) set_err(o, ORC_ENONFINITE);
         Qout[QI(o, m, v, c)] = q;
       }
     }
@@ -1046,10 +1115,12 @@ static double phir_at(const orc* o, long c, int r) { return phim(o, c, r); }
 static void levelset_stage(orc* o, int s) {
   int N = o->N, D = o->D;
   double beta = rk_beta(o, s), omb = 1.0 - rk_beta(o, s), dt = o->dt, eps = o->p.weno_eps;
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) {
     o->phit[c] = o->phi[c];
     o->chit[c] = o->chi[c];
   }
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) {
     if (!o->inB[c]) continue;
     double best = 0.0;
@@ -1088,6 +1159,7 @@ static void levelset_stage(orc* o, int s) {
     o->phit[c] = ph;
     o->chit[c] = (uint8_t)arg;
   }
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) {
     o->phi[c] = o->phit[c];
     o->chi[c] = o->chit[c];
@@ -1226,12 +1298,13 @@ static void mixing(orc* o, double* Qc) {
   mixrec* rec = (mixrec*)calloc((size_t)N * nc, sizeof(mixrec));
   uint8_t* mergef = (uint8_t*)calloc((size_t)N * nc, 1);
   for (int m = 0; m < N; m++)
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < nc; c++) {
       if (!o->inB[c] || !((o->smask[c] >> m) & 1u)) continue;
       int fail, merge;
       mix_source(o, Qc, c, m, &rec[MI(o, m, c)], &fail, &merge);
-      if (rec[MI(o, m, c)].small) o->cnt[ORC_C_SMALL]++;
-      if (fail) o->cnt[ORC_C_MIXFAIL]++;
+      if (rec[MI(o, m, c)].small) count(o, ORC_C_SMALL);
+      if (fail) count(o, ORC_C_MIXFAIL);
       if (merge && m != o->chi[c]) mergef[MI(o, m, c)] = 1;
     }
   /* Weight limit (a reading of the mixing of Sec. 2.3.2): a pair exchange
@@ -1248,6 +1321,7 @@ static void mixing(orc* o, double* Qc) {
    * adds nothing to its target's T (w_t = 0): its exchanges stay whole, so
    * its content always leaves. */
   double* Tw = (double*)calloc((size_t)N * nc, sizeof(double));
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < nc; c++) {
     if (!o->inB[c]) continue;
     int ijk[3];
@@ -1272,6 +1346,7 @@ static void mixing(orc* o, double* Qc) {
   }
   double* Qnew = (double*)malloc(sizeof(double) * (size_t)N * NV * nc);
   memcpy(Qnew, Qc, sizeof(double) * (size_t)N * NV * nc);
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < nc; c++) {
     if (!o->inB[c]) continue;
     int ijk[3];
@@ -1313,7 +1388,7 @@ static void mixing(orc* o, double* Qc) {
         Qnew[QI(o, pm, v, c)] = Qnew[QI(o, pm, v, c)] + Qnew[QI(o, m, v, c)];
         Qnew[QI(o, m, v, c)] = 0.0;
       }
-      o->cnt[ORC_C_MERGE]++;
+      count(o, ORC_C_MERGE);
     }
   }
   memcpy(Qc, Qnew, sizeof(double) * (size_t)N * NV * nc);
@@ -1329,10 +1404,12 @@ static void mixing(orc* o, double* Qc) {
 static void scale_separation(orc* o) {
   int N = o->N, D = o->D;
   double eps = o->eps_ss;
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) {
     o->phit[c] = o->phi[c];
     o->chit[c] = o->chi[c];
   }
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) {
     if (!o->inB[c] || !o->mixed[c]) continue;
     int np = 0;
@@ -1352,7 +1429,7 @@ static void scale_separation(orc* o) {
         }
     if (near_minus) continue;
     /* oddball: new indicator = the other material of largest volume fraction */
-    o->cnt[ORC_C_ODDBALL]++;
+    count(o, ORC_C_ODDBALL);
     int chs = -1;
     for (int m = 0; m < N; m++) {
       if (m == chi1 || !((o->xs[c] >> m) & 1u)) continue;
@@ -1384,6 +1461,7 @@ static void scale_separation(orc* o) {
     if (found) o->phit[c] = fabs(dmin - eps);
     o->chit[c] = (uint8_t)chs;
   }
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) {
     o->phi[c] = o->phit[c];
     o->chi[c] = o->chit[c];
@@ -1430,13 +1508,16 @@ static double godunov(const orc* o, long c) {
 static void reinit(orc* o) {
   compute_xs(o);
   for (int it = 0; it < o->p.reinit_iters; it++) {
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < o->ncell; c++) o->phit[c] = o->phi[c];
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < o->ncell; c++) {
       if (!o->inB[c] || popc(o->xs[c]) >= 2) continue;
       double ph = godunov(o, c);
       if (ph > o->cap) ph = o->cap;
       o->phit[c] = ph;
     }
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < o->ncell; c++) o->phi[c] = o->phit[c];
   }
 }
@@ -1531,6 +1612,14 @@ int orc_step(orc* o, int32_t nsteps, double t_end) {
 }
 
 long orc_ncell(const orc* o) { return o->ncell; }
+
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 int orc_step_taped(orc* o, double t_end, double* tphi, uint8_t* tchi, double* tdt) {
   if (o->err) return o->err;

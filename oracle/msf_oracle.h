@@ -40,6 +40,14 @@ typedef struct {
    * falling linearly to fs_p1 at fs_t1, fs_p1 after */
   int32_t fs_mat;
   double fs_rho, fs_p0, fs_t0, fs_t1, fs_p1;
+  /* reduced interaction model of Sec. 2.3.2, for comparison with the reading
+   * the method runs by default (0: the heavier material R of the pair takes
+   * minus the exchange of every other present material, whose area vector
+   * S^m carries the pair's interface state): literal_reduced = 1 lets only the
+   * pair exchange, X^R = [0, p* S^R, p* u* n.S^R], X^L = -X^R, other
+   * materials 0; literal_normal = 1 replaces each area vector S^m by
+   * |S^m| n^m (the material's own level-set normal) */
+  int32_t literal_reduced, literal_normal;
 } orc_params;
 
 typedef struct orc orc;
@@ -63,6 +71,9 @@ int orc_step(orc* o, int32_t nsteps, double t_end);
  * orc_replay_step takes one step from the current conserved state with the
  * interface evolution frozen to the tape (the flow part of the step only). */
 long orc_ncell(const orc* o);
+/* threads the loops over cells use: 1 in the plain build, the OpenMP
+   maximum in the -fopenmp build (same results either way) */
+int orc_threads(void);
 int orc_step_taped(orc* o, double t_end, double* tphi, uint8_t* tchi, double* tdt);
 int orc_replay_step(orc* o, const double* tphi, const uint8_t* tchi, double dt);
 void orc_set_conserved(orc* o, const double* Q);
