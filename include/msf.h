@@ -125,7 +125,21 @@ typedef struct {
  *   stream       cudaStream_t for all work of this context
  *   rk_stages    3: three-stage TVD Runge-Kutta (default); 2: the two-stage
  *                TVD Runge-Kutta the paper uses (Sec. 3), beta_s = (0, 1/2)
- *                in the form of Eq. local-advection */
+ *                in the form of Eq. local-advection
+ *   literal_reduced  0 (default): in a cut cell the interface state of the
+ *                heaviest pair acts on the boundary of every other present
+ *                material m through its area vector S^m (pointing into m),
+ *                and the heavier material R of the pair takes minus their
+ *                sum (sum_m X^m = 0; with two materials X^R = -X^L exactly as
+ *                in Sec. 2.3.2). 1: the reduced model as printed in Sec. 2.3.2,
+ *                only the pair exchanges, X^R = [0, p* S^R, p* u* n.S^R],
+ *                X^L = -X^R, the other materials get nothing (for comparison:
+ *                a resting junction then does not stay at rest)
+ *   literal_normal   1: each area vector S^m replaced by |S^m| n^m, the
+ *                material's own level-set normal (the printed form of the
+ *                exchange flux of Sec. 2.3.2); 0 (default): S^m itself
+ * Tapes and the adjoint step refuse contexts with a literal option set
+ * (MSF_EUNSUPPORTED). */
 typedef struct {
   int32_t precision;
   double cfl, weno_eps, mix_alpha;
@@ -135,6 +149,7 @@ typedef struct {
   int32_t use_graph, profile, batch_mode;
   void* stream;
   int32_t rk_stages;
+  int32_t literal_reduced, literal_normal;
 } msf_options;
 
 /* Fill opt with the defaults above for a grid of dimension dim. */
@@ -303,17 +318,23 @@ msf_status msf_profile_read(msf_ctx* ctx, double* flux_ms);
  *   U       device [dim + 2][cells] conservative state (rho, rho u_d, rho E)
  *   cells   1 .. MSF_NOALLOC_MAX_CELLS (larger: MSF_EINVAL)
  *   eos     host pointer, the material; h host [dim] cell sizes
- *   dt_out  device pointer to one double, written asynchronously
+ *   dt_out  device pointer to one double, written asynchronously; NaN when
+ *           any cell has rho <= 0, c^2 <= 0 (p + pinf <= 0) or a non-finite
+ *           value (the states msf_step reports as MSF_ENEGATIVE or
+ *           MSF_ENONFINITE), so a bad state never yields a finite step
  *   stream  cudaStream_t for the two kernels (NULL: legacy default stream)
  * Calls no cudaMalloc/cudaFree and no allocating library routine: its scratch
  * is a fixed array compiled into the library, present on every device that
  * loads it until the process exits. The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress) with the device current; make
- * that first call before any stream capture. Every call shares the array and
- * writes every slot it reads, so nothing needs clearing between calls; calls
- * that overlap on the GPU (other streams, other threads) race on it and must
- * be ordered by the caller. Errors: MSF_EINVAL (message via
- * msf_last_error(NULL)), MSF_ECUDA. */
+ * array's device address (cudaGetSymbolAddress) with the device current;
+ * later calls look it up again unless their stream is being captured, when
+ * the address of the last call outside capture is used, so make the first
+ * call on each device before any stream capture (a capturing first call
+ * returns MSF_ESTATE). Every call shares the array and writes every slot it
+ * reads, so nothing needs clearing between calls; calls that overlap on the
+ * GPU (other streams, other threads) race on it and must be ordered by the
+ * caller. Errors: MSF_EINVAL (message via msf_last_error(NULL)), MSF_ECUDA,
+ * MSF_ESTATE. */
 msf_status msf_cfl_dt_noalloc(const double* U, int64_t cells, int32_t dim, const msf_eos* eos, const double* h,
                               double cfl, double* dt_out, void* stream);
 

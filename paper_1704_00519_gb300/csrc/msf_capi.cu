@@ -108,6 +108,8 @@ extern "C" msf_status msf_default_options(int32_t dim, msf_options* opt) {
   opt->batch_mode = 0;
   opt->stream = nullptr;
   opt->rk_stages = 3;
+  opt->literal_reduced = 0;
+  opt->literal_normal = 0;
   return MSF_OK;
 }
 
@@ -133,7 +135,8 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
   if (!(opt->cfl > 0.0 && opt->cfl <= 1.0) || !(opt->weno_eps > 0.0) || !(opt->mix_alpha >= 0.0 && opt->mix_alpha < 1.0) ||
       opt->ext_sweeps < 1 || opt->ext_sweeps > 64 || opt->vel_sweeps < 0 || opt->vel_sweeps > 64 ||
       opt->reinit_iters < 0 || opt->reinit_iters > 64 || !(opt->phi_cap_h >= 4.0) || !(opt->scale_eps_h >= 0.0) ||
-      (opt->rk_stages != 2 && opt->rk_stages != 3))
+      (opt->rk_stages != 2 && opt->rk_stages != 3) || (opt->literal_reduced != 0 && opt->literal_reduced != 1) ||
+      (opt->literal_normal != 0 && opt->literal_normal != 1))
     return fail(nullptr, MSF_EINVAL, "option out of range");
   for (int i = 0; i < n_instances; i++) {
     const msf_grid& gr = grids[i];
@@ -269,6 +272,7 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
     g.reinit_iters = opt->reinit_iters;
     g.scale_sep = opt->scale_sep;
     g.reinit = opt->reinit;
+    g.literal = (opt->literal_reduced ? 1 : 0) | (opt->literal_normal ? 2 : 0);
     // Shu-Osher TVD Runge-Kutta in the beta form; the ledger weight of stage s
     // is the coefficient of dt L(Q^(s)) in Q^{n+1}
     g.rk = opt->rk_stages;
@@ -944,6 +948,8 @@ static msf_status check_single(msf_ctx* c) {
   if (c->ninst != 1 || c->batched) return fail(c, MSF_EUNSUPPORTED, "tapes and the adjoint need a single-instance context");
   if (c->inst[0].g.geom != 0 || c->inst[0].g.fs_mat >= 0)
     return fail(c, MSF_EUNSUPPORTED, "tapes and the adjoint take Cartesian grids without a free surface");
+  if (c->inst[0].g.literal != 0)
+    return fail(c, MSF_EUNSUPPORTED, "tapes and the adjoint take the default interaction model (literal options off)");
   if (c->sticky) return fail(c, MSF_ESTATE, "context holds a device-detected error; reset with msf_set_state");
   return MSF_OK;
 }
@@ -989,7 +995,7 @@ static bool tape_aligned(const void* p) { return ((uintptr_t)p & 255u) == 0; }
 extern "C" msf_status msf_tape_bytes(const msf_ctx* c, int64_t* bytes) {
   if (!c || !bytes) return MSF_EINVAL;
   if (c->ninst != 1 || c->batched) return MSF_EUNSUPPORTED;
-  if (c->inst[0].g.geom != 0 || c->inst[0].g.fs_mat >= 0) return MSF_EUNSUPPORTED;
+  if (c->inst[0].g.geom != 0 || c->inst[0].g.fs_mat >= 0 || c->inst[0].g.literal != 0) return MSF_EUNSUPPORTED;
   *bytes = (int64_t)tape_layout(c->inst[0].g).total;
   return MSF_OK;
 }

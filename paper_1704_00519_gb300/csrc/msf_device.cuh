@@ -42,6 +42,7 @@ struct Grid {
   double cfl, weno_eps, mix_alpha;
   int ext_sweeps, vel_sweeps, reinit_iters, scale_sep, reinit;
   int rk;                       // Runge-Kutta stages (2 or 3)
+  int literal;                  // bit 0: printed reduced model, bit 1: |S| n area vectors
   double rk_beta[3], rk_lw[3];  // beta_s of Eq. local-advection; ledger weight of stage s
   int bc[3][2], inflow_mat[3][2];
   double inflow_prim[3][2][5];
@@ -193,21 +194,10 @@ __device__ inline T weno5(T a, T b, T c, T d, T e, T eps) {
   t = T(3) * c - T(4) * d + e;
   s2 = s2 + T(0.25) * t * t;
   T b0 = eps + s0, b1 = eps + s1, b2 = eps + s2;
-  T a0, a1, a2;
-  if constexpr (sizeof(T) == 8) {
-    // FP64: the weights 0.1/b0^2, 0.6/b1^2, 0.3/b2^2, each multiplied by
-    // b0^2 b1^2 b2^2 (the normalised weights are unchanged; one FP64
-    // division instead of four)
-    const T p0 = b0 * b0, p1 = b1 * b1, p2 = b2 * b2;
-    a0 = T(0.1) * (p1 * p2);
-    a1 = T(0.6) * (p0 * p2);
-    a2 = T(0.3) * (p0 * p1);
-  } else {
-    // FP32: the products could leave the FP32 range for large fluxes
-    a0 = T(0.1) / (b0 * b0);
-    a1 = T(0.6) / (b1 * b1);
-    a2 = T(0.3) / (b2 * b2);
-  }
+  // Jiang & Shu's weights d_k / (eps + beta_k)^2, normalised by their sum
+  const T a0 = T(0.1) / (b0 * b0);
+  const T a1 = T(0.6) / (b1 * b1);
+  const T a2 = T(0.3) / (b2 * b2);
   return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
 }
 

@@ -244,16 +244,27 @@ __device__ __forceinline__ void phase_geom_cell(const Grid& g, const Bufs& b, co
       continue;
     }
     b.gflag[c] = GF_MIXED;
-    // the materials partition every face
+    // the materials partition every face; a face on which every local field
+    // is <= 0 (the averaged vertex values can give one next to a junction)
+    // goes to the indicators of its two cells, whole or half each
     for (int d = 0; d < D; d++)
       for (int side = 0; side < 2; side++) {
         double* A = side ? b.Ahi : b.Alo;
         double s = 0.0;
         for (int m = 0; m < N; m++)
           if ((bits >> m) & 1u) s += A[aidx(g, d, m, c)];
-        if (s > 0.0)
+        if (s > 0.0) {
           for (int m = 0; m < N; m++)
             if ((bits >> m) & 1u) A[aidx(g, d, m, c)] = A[aidx(g, d, m, c)] / s;
+        } else {
+          const int ca = b.chi[side ? c : c - g.st[d]], cb = b.chi[side ? c + g.st[d] : c];
+          if (ca == cb) {
+            A[aidx(g, d, ca, c)] = 1.0;
+          } else {
+            A[aidx(g, d, ca, c)] = 0.5;
+            A[aidx(g, d, cb, c)] = 0.5;
+          }
+        }
       }
     const double* Mref = Qs ? Qs : mass;
     if (!Mref) continue;
@@ -730,9 +741,13 @@ __device__ __forceinline__ void phase_interface_d(const Grid& g, const Bufs& b, 
                    (T)g.pinf[R], &us, &ps, g.eos_kind[L] == 1, g.eos_kind[R] == 1);
     }
     const double psd = (double)ps, usd = (double)us;
+    // every other present material's boundary carries the pair's interface
+    // state and R takes minus their sum; the printed reduced model
+    // (literal bit 0) lets only the pair exchange, bit 1 uses |S^m| n^m
+    const bool lit = (g.literal & 1) != 0;
     double XR[5] = {0, 0, 0, 0, 0};
     for (int m = 0; m < N; m++) {
-      if (m == R || !present(g, b, c, m)) continue;
+      if (lit ? m != R : (m == R || !present(g, b, c, m))) continue;
       double S[3] = {0, 0, 0}, nS = 0.0;
       if (g.geom == 1) {
         // interface area r_I n: the faces' r_f A_f less the wedge side alpha h
@@ -742,6 +757,13 @@ __device__ __forceinline__ void phase_interface_d(const Grid& g, const Bufs& b, 
       } else {
         for (int d = 0; d < D; d++) S[d] = (b.Ahi[aidx(g, d, m, c)] - b.Alo[aidx(g, d, m, c)]) * g.farea[d];
       }
+      if (g.literal & 2) {
+        double nm[3], len = 0.0;
+        stored_normal(g, b, c, m, nm);
+        for (int d = 0; d < D; d++) len += S[d] * S[d];
+        len = sqrt(len);
+        for (int d = 0; d < D; d++) S[d] = len * nm[d];
+      }
       for (int d = 0; d < D; d++) nS += n[d] * S[d];
       for (int d = 0; d < D; d++) {
         b.X[qidx(g, m, 1 + d, c)] = psd * S[d];
@@ -750,7 +772,7 @@ __device__ __forceinline__ void phase_interface_d(const Grid& g, const Bufs& b, 
       b.X[qidx(g, m, D + 1, c)] = psd * usd * nS;
       XR[D + 1] -= psd * usd * nS;
     }
-    for (int v = 1; v < NV; v++) b.X[qidx(g, R, v, c)] = XR[v];
+    for (int v = 1; v < NV; v++) b.X[qidx(g, lit ? L : R, v, c)] = XR[v];
     for (int d = 0; d < D; d++) b.vel0[d * g.ncell + c] = usd * n[d];
   }
   if (ncut) atomicAdd(&b.ctl->cnt[C_CUT], ncut);

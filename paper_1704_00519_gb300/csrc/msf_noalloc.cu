@@ -30,7 +30,11 @@ struct CflArgs {
   double gamma, pinf, gm1, gpi, rh[3];
 };
 
-// one thread per cell: sum_d (|u_d| + c) / h_d of the state, block maximum to scratch
+// maximum that keeps a NaN: a non-physical cell must not vanish in the reduction
+__device__ inline double max_keep_nan(double a, double b) { return (a != a || b != b) ? a + b : fmax(a, b); }
+
+// one thread per cell: sum_d (|u_d| + c) / h_d of the state, block maximum to
+// scratch; a cell with rho <= 0, c^2 <= 0 or a non-finite value gives NaN
 __global__ void k_cfl_partial(const double* U, long long cells, CflArgs a, double* partial) {
   const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
   double s = 0.0;
@@ -43,33 +47,38 @@ __global__ void k_cfl_partial(const double* U, long long cells, CflArgs a, doubl
     for (int d = 0; d < D; d++) q += vel[d] * vel[d];
     const double ke = 0.5 * rho * q;
     const double p = a.gm1 * (U[(long long)(D + 1) * cells + i] - ke) - a.gpi;
-    double c2 = (a.gamma * (p + a.pinf)) / rho;
-    if (!(rho > 0.0) || !(c2 > 0.0)) c2 = c2 > 0.0 ? c2 : 0.0;
-    const double c = sqrt(c2);
-    for (int d = 0; d < D; d++) s += (fabs(vel[d]) + c) * a.rh[d];
+    const double c2 = (a.gamma * (p + a.pinf)) / rho;
+    if (!(rho > 0.0) || !(c2 > 0.0)) {
+      s = __longlong_as_double(0x7ff8000000000000LL);
+    } else {
+      const double c = sqrt(c2);
+      for (int d = 0; d < D; d++) s += (fabs(vel[d]) + c) * a.rh[d];
+      if (!isfinite(s)) s = __longlong_as_double(0x7ff8000000000000LL);
+    }
   }
   __shared__ double red[kThreads];
   red[threadIdx.x] = s;
   __syncthreads();
   for (int k = kThreads / 2; k > 0; k >>= 1) {
-    if (threadIdx.x < k) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + k]);
+    if (threadIdx.x < k) red[threadIdx.x] = max_keep_nan(red[threadIdx.x], red[threadIdx.x + k]);
     __syncthreads();
   }
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
-// one block: maximum over the partials of this call, then dt = cfl / max
+// one block: maximum over the partials of this call, then dt = cfl / max; a
+// NaN partial (a non-physical cell) or a zero bound gives dt = NaN
 __global__ void k_cfl_final(const double* partial, int nblocks, double cfl, double* dt_out) {
   double m = 0.0;
-  for (int k = threadIdx.x; k < nblocks; k += kThreads) m = fmax(m, partial[k]);
+  for (int k = threadIdx.x; k < nblocks; k += kThreads) m = max_keep_nan(m, partial[k]);
   __shared__ double red[kThreads];
   red[threadIdx.x] = m;
   __syncthreads();
   for (int k = kThreads / 2; k > 0; k >>= 1) {
-    if (threadIdx.x < k) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + k]);
+    if (threadIdx.x < k) red[threadIdx.x] = max_keep_nan(red[threadIdx.x], red[threadIdx.x + k]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) *dt_out = cfl / red[0];
+  if (threadIdx.x == 0) *dt_out = red[0] > 0.0 ? cfl / red[0] : __longlong_as_double(0x7ff8000000000000LL);
 }
 
 std::mutex g_mu;
@@ -115,11 +124,19 @@ extern "C" msf_status msf_cfl_dt_noalloc(const double* U, int64_t cells, int32_t
     msf_internal_set_error("msf_cfl_dt_noalloc: no current CUDA device");
     return MSF_ECUDA;
   }
+  cudaStream_t s = (cudaStream_t)stream;
+  // Device address of the scratch array, looked up with this device current.
+  // The first call on a device does it; later calls look it up again unless
+  // the stream is being captured (the module may have been reloaded at a new
+  // address after a context reset), and a capturing call uses the address the
+  // last call outside capture found.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool capturing = cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone;
+  if (capturing) cudaGetLastError();  // clear a refused query
   double* scratch = nullptr;
   {
-    // first call on a device: look up the device address of the scratch array
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch[dev]) {
+    if (!capturing) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_partial_max);
       if (e != cudaSuccess || !p) {
@@ -127,11 +144,13 @@ extern "C" msf_status msf_cfl_dt_noalloc(const double* U, int64_t cells, int32_t
         return MSF_ECUDA;
       }
       g_scratch[dev] = (double*)p;
+    } else if (!g_scratch[dev]) {
+      msf_internal_set_error("msf_cfl_dt_noalloc: the first call on a device must come before any stream capture");
+      return MSF_ESTATE;
     }
     scratch = g_scratch[dev];
   }
   const int nblocks = (int)((cells + kThreads - 1) / kThreads);
-  cudaStream_t s = (cudaStream_t)stream;
   k_cfl_partial<<<nblocks, kThreads, 0, s>>>(U, cells, a, scratch);
   k_cfl_final<<<1, kThreads, 0, s>>>(scratch, nblocks, cfl, dt_out);
   cudaError_t e = cudaGetLastError();

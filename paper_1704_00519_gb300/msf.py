@@ -56,7 +56,8 @@ class msf_options(C.Structure):
                 ("ext_sweeps", C.c_int32), ("vel_sweeps", C.c_int32), ("reinit_iters", C.c_int32),
                 ("scale_sep", C.c_int32), ("reinit", C.c_int32), ("scale_eps_h", C.c_double),
                 ("phi_cap_h", C.c_double), ("use_graph", C.c_int32), ("profile", C.c_int32),
-                ("batch_mode", C.c_int32), ("stream", C.c_void_p), ("rk_stages", C.c_int32)]
+                ("batch_mode", C.c_int32), ("stream", C.c_void_p), ("rk_stages", C.c_int32),
+                ("literal_reduced", C.c_int32), ("literal_normal", C.c_int32)]
 
 
 class MsfError(RuntimeError):
@@ -168,6 +169,8 @@ def make_options(p: dict, precision=MSF_FP64, stream=None, use_graph=1, profile=
         setattr(o, k, float(p[k]))
     for k in ("ext_sweeps", "vel_sweeps", "reinit_iters", "scale_sep", "reinit", "rk_stages"):
         setattr(o, k, int(p[k]))
+    o.literal_reduced = int(p.get("literal_reduced", 0))
+    o.literal_normal = int(p.get("literal_normal", 0))
     o.use_graph = int(use_graph)
     o.profile = int(profile)
     o.stream = stream

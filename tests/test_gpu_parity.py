@@ -2,9 +2,10 @@
 inputs, element by element.
 
 FP64 mode: the strict build (-fmad=false on the device, -ffp-contract=off in
-the oracle) evaluates every expression in the same order, so the states are
-expected to agree to the last bit; the gate is the benchmark spec's tolerance, L1
-relative density error <= 1e-10, plus max |dQ| <= 1e-12 * max|Q|.
+the oracle) evaluates every expression as the oracle states it (the WENO5
+weights as Jiang and Shu define them included), so the states are expected
+to agree to the last bit; the gate is L1 relative density error <= 1e-10,
+plus max |dQ| <= 1e-12 * max|Q|.
 FP32-bulk mode: L1 relative density error <= 2e-5.
 """
 import numpy as np
@@ -141,6 +142,63 @@ def test_scale_separation_filament_fp64(msf):
     o, s, eo = run_pair(msf, case, 2, t_end=10.0)
     compare(o, s, FP64_L1, exact=True)
     assert not np.any(s.state()["chi"] == 2)
+
+
+@pytest.mark.parametrize("dim,n,nmat,seed", [(2, (23, 19), 3, 3), (2, (23, 19), 4, 5), (3, (10, 9, 8), 3, 3),
+                                             (2, (23, 19), 3, 1), (2, (30, 26), 4, 3)])
+def test_junction_equilibrium_fp64(msf, dim, n, nmat, seed):
+    """Resting junctions (the conservation correction firing, and faces that
+    no local field covers closed by the indicators of their two cells): the
+    GPU keeps u = 0, p = 1 to round-off and equals the oracle."""
+    from test_oracle_pins import _max_dev
+    case = cs.random_case(dim, n, nmat, seed, at_rest=True, p_equal=True)
+    o, s, eo = run_pair(msf, case, 10, t_end=10.0, scale_sep=0, reinit=0)
+    assert eo == 0
+    compare(o, s, FP64_L1, exact=True)
+    du, dp = _max_dev(case, s.state())
+    assert du < 1e-12 and dp < 1e-12
+
+
+@pytest.mark.parametrize("lit,ln", [(1, 0), (0, 1), (1, 1)])
+def test_literal_interaction_options_fp64(msf, lit, ln):
+    """The printed forms of the reduced model (Sec. 2.3.2), kept for
+    comparison: the GPU equals the oracle with each switch, on a resting
+    triple point (which drifts under them) and on a random network."""
+    from test_oracle_pins import _resting_triple_point
+    for case, steps in ((_resting_triple_point(), 20), (cs.random_case(2, (37, 29), 3, 1), 10)):
+        o, s, eo = run_pair(msf, case, steps, t_end=10.0, scale_sep=0, reinit=0, literal_reduced=lit,
+                            literal_normal=ln)
+        assert eo == 0
+        compare(o, s, FP64_L1, exact=True)
+
+
+def test_correction_choice_at_start_up_fp64(msf):
+    """The T-junction of the oracle pin: with each material made the lightest
+    in turn, and with densities where the lightest by mass is neither the
+    lightest by density nor the smallest fraction, the GPU's corrected volume
+    fractions at start-up equal the oracle's."""
+    from test_oracle_pins import _t_junction
+    r = np.array([0.5588756756756762, 0.1844666212111825, 0.23894901960784248])
+    configs = [[1e-3, 1.0, 1.0], [1.0, 1e-3, 1.0], [1.0, 1.0, 1e-3],
+               [1.0, 5.45, 0.9 * r[0] / r[2]]]
+    for rho in configs:
+        case = _t_junction(rho)
+        a, b = msf.Solver(case).state()["alpha"], orc.Oracle(case).state()["alpha"]
+        assert np.abs(a - b).max() <= 1e-15, rho
+
+
+@pytest.mark.parametrize("y0,y1,new_chi", [(0.42, 0.49, 0), (0.41, 0.48, 1)])
+def test_scale_separation_by_hand_fp64(msf, y0, y1, new_chi):
+    """The one-row filament of the oracle pin, one step at rest: the GPU equals
+    the oracle, and the filament row took chi_1* with phi* = 0.04."""
+    from test_oracle_pins import _one_row_filament
+    case = _one_row_filament(y0, y1)
+    o, s, eo = run_pair(msf, case, 1, t_end=10.0, reinit=0)
+    assert eo == 0
+    compare(o, s, FP64_L1, exact=True)
+    st = s.state()
+    assert np.all(st["chi"][40:50] == new_chi)
+    assert np.abs(st["phi"][40:50] - 0.04).max() < 1e-12
 
 
 @pytest.mark.parametrize("maker,steps", [(lambda: cs.triple_point(112, 48), 60), (lambda: cs.shock_bubbles(96, 32), 30),
