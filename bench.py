@@ -1,14 +1,18 @@
 #!/usr/bin/env python3
 """Throughput of the cut-cell multi-material update on GB300.
 
-Workload: the 2D triple-point problem, 896 x 384 cells, three materials
-(configs of the paper's Sec. 3.3 shape, synthetic initial data). One step is
-one full TVD-RK3 step (three stages of every step of the method) over the
-whole grid; the metric is cell-stage updates per second (cells x 3 per step).
+Headline workload: the 3D Mach-1.22 shock on a heavy sphere, 256 x 128 x 128
+cells, two stiffened gases (the largest single-GPU configuration; synthetic
+initial data). One step is one full TVD-RK3 step (three stages of every step
+of the method) over the whole grid; the metric is cell-stage updates per
+second (cells x 3 per step). The headline value is the FP32-bulk form; the
+plain FP64 path runs beside it on the same workload, and the difference of the
+two after the same steps is reported for every output (density, velocity,
+pressure, volume fractions, level set, totals).
 
-The headline value is the FP32-bulk form; the plain FP64 path runs beside it
-on the same workload and its throughput, and the L1 density difference of the
-two after the same number of steps, are reported in the same JSON line.
+Side keys: the 2D triple point (896 x 384: first steps and a window from
+t = 0.3), the two-bubble shock (2048 x 512), the batched 1D problems, Case II's
+shell study and the adjoint step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl msf|reference]
 
@@ -33,7 +37,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="triple_point_896x384", nx=896, ny=384)
+WORKLOAD = dict(name="shock_sphere_256x128x128", n=(256, 128, 128))
 METRIC = "cell-stage updates/s: FP32/batched/adjoint vs plain FP64 on GB300 at stated L1"
 UNIT = "cell-stage updates/s"
 FALLBACK_HBM_GBS = 6800.0
@@ -47,6 +51,8 @@ def parse():
     ap.add_argument("--impl", default="msf", choices=["msf", "reference"])
     ap.add_argument("--only", default=None, choices=["fp32", "fp64"],
                     help="profiling aid: run warm-up and timed steps of one precision only, print nothing else")
+    ap.add_argument("--case", default="sphere", choices=["sphere", "triple", "bubbles"],
+                    help="workload of --only (default: the headline sphere)")
     return ap.parse_args()
 
 
@@ -57,23 +63,33 @@ def dist_env():
     return rank, world, local
 
 
-def make_case():
+def make_case(which="sphere"):
     import paper_1704_00519_gb300.cases as cs
-    return cs.triple_point(WORKLOAD["nx"], WORKLOAD["ny"])
+    if which == "triple":
+        return cs.triple_point(896, 384)
+    if which == "bubbles":
+        return cs.shock_bubbles(2048, 512)
+    return cs.shock_sphere(WORKLOAD["n"])
 
 
 # ------------------------------------------------------------ reference arm
-def oracle_rate(case, steps, warmup):
-    """Time the CPU oracle as it stands (single thread) on full steps of the
-    workload; returns (cell-stages/s, seconds, steps timed)."""
-    from oracle.oracle import Oracle
-    o = Oracle(case)
+def oracle_rate(case, steps, warmup, openmp=True, budget_s=None):
+    """Time the CPU oracle as it stands on full steps of the workload (the
+    OpenMP build on every host core, or the plain build on one); with a time
+    budget, fewer steps are timed when one step is slow. Returns
+    (cell-stages/s, seconds, steps timed, threads)."""
+    from oracle.oracle import Oracle, threads
+    o = Oracle(case, openmp=openmp)
+    t0 = time.perf_counter()
     if warmup:
         o.step(warmup, case.t_end)
+    per_step = (time.perf_counter() - t0) / warmup if warmup else None
+    if budget_s and per_step:
+        steps = max(1, min(steps, int(budget_s / per_step)))
     t0 = time.perf_counter()
     o.step(steps, case.t_end)
     dt = time.perf_counter() - t0
-    return case.cells * 3 * steps / dt, dt, steps
+    return case.cells * 3 * steps / dt, dt, steps, threads(openmp)
 
 
 def run_reference(args):
@@ -81,19 +97,19 @@ def run_reference(args):
     if rank != 0:
         return 0
     from oracle import oracle as orc
-    orc.build()
+    orc.build(openmp=True)
     case = make_case()
-    # one full oracle step of the workload takes ~2 s: bound the run to a few minutes
-    steps = max(1, min(args.steps, 30))
-    warm = max(0, min(args.warmup, 3))
-    val, secs, steps = oracle_rate(case, steps, warm)
+    # one OpenMP oracle step of the workload takes seconds: bound the run to a few minutes
+    warm = max(1, min(args.warmup, 1))
+    val, secs, steps, nthr = oracle_rate(case, args.steps, warm, openmp=True, budget_s=150.0)
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
         "n_gpus": 0, "steps": steps, "warmup": warm, "ms_per_step": 1e3 * secs / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD["name"], "cells": case.cells, "materials": case.nmat},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{steps} full TVD-RK3 steps of the {WORKLOAD['name']} workload after {warm} warm-up steps"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": nthr, "kind": "oracle",
+                         "sample": f"{steps} full TVD-RK3 steps of the {WORKLOAD['name']} workload after {warm} "
+                                   f"warm-up step(s), OpenMP oracle on {nthr} threads (capped at 150 s of timed steps)"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -121,7 +137,7 @@ def flux_kernel_hash():
 def profiled_traffic(precision):
     """DRAM bytes per flux-update launch from the committed ncu summary, when
     it was taken on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "flux_update_triple_point_traffic.json")
+    p = os.path.join(ROOT, "profiles", "flux_update_shock_sphere_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -243,13 +259,13 @@ def batched_rates(msf, torch, stream, K_persistent, K_sequence):
 
 
 def workload_rates(msf, torch, stream, K):
-    """Forward throughput of the two-bubble (2D, 2048 x 512) and sphere (3D,
-    256 x 128 x 128) shock workloads, FP32-bulk and FP64, device-timed, with
+    """Forward throughput of the two-bubble (2D, 2048 x 512) and triple-point
+    (2D, 896 x 384) workloads from their first steps, FP32-bulk and FP64, device-timed, with
     the L1 density difference of the two after the same steps."""
     import paper_1704_00519_gb300.cases as cs
     out = {}
     for name, maker in (("shock_bubbles_2048x512", lambda: cs.shock_bubbles(2048, 512)),
-                        ("shock_sphere_256x128x128", lambda: cs.shock_sphere((256, 128, 128)))):
+                        ("triple_point_896x384", lambda: cs.triple_point(896, 384))):
         case = maker()
         r = {"cells": case.cells, "steps": K}
         rho = {}
@@ -315,7 +331,7 @@ def later_window(msf, torch, stream, flush, K, t_start=0.3):
     """Triple point advanced to t = t_start (the waves have spread over much of
     the domain, so fewer tiles are idle), then K device-timed steps per
     precision. A device-detected error is reported, not raised."""
-    case = make_case()
+    case = make_case("triple")
     out = {"t_start": t_start, "steps": K}
     for key, prec in (("fp32", msf.MSF_FP32_BULK), ("fp64", msf.MSF_FP64)):
         s = msf.Solver(case, precision=prec, stream=stream)
@@ -348,6 +364,19 @@ def pairs_per_cell(s):
     return int(sum(bin(int(v)).count("1") * int(c) for v, c in zip(vals, counts)))
 
 
+def flux_flops_per_pair_stage(dim):
+    """Floating-point operations of the flux update per (cell, material) pair
+    and stage, counted from the operations the kernels execute (a division or
+    square root counts as one): one WENO5 value 67 (three candidate values 16,
+    smoothness indicators 34, weights and normalisation 17), the split fluxes
+    of one variable over the 6-cell stencil 39, so one face and variable
+    2 * 67 + 39 + 1 = 174, one face nv * 174 + 6 (wave-speed maximum); per
+    pair dim faces, plus 17 for the primitive quantities and 19 * nv for the
+    aperture-weighted difference, the exchange and the RK combination."""
+    nv = dim + 2
+    return dim * (nv * 174 + 6) + 17 + 19 * nv
+
+
 def flux_bytes_per_step(case, npairs):
     """Algorithmic DRAM bytes of the three flux-update launches of one step:
     per (cell, material) pair the stage state is read and the new state written
@@ -377,6 +406,41 @@ def job_rate(units_per_rank, world, seconds):
 
 
 # ------------------------------------------------------------------ GPU arm
+def output_errors(case, a, b):
+    """Difference of state a (FP32-bulk form) from state b (plain FP64 path)
+    for every output: L1 relative of the density summed over materials, of
+    each material's velocity and pressure where both give it a volume, of the
+    volume fractions; the largest level-set difference in cells h; the largest
+    relative difference of the per-material totals is taken separately."""
+    N, D = case.nmat, case.dim
+    Qa, Qb, aa, ab = a["Q"], b["Q"], a["alpha"], b["alpha"]
+    out = {}
+    ra, rb = Qa[:, 0].sum(0), Qb[:, 0].sum(0)
+    out["rho_l1"] = float(np.abs(ra - rb).sum() / np.abs(rb).sum())
+    du = dun = dp = dpn = 0.0
+    for m in range(N):
+        on = (aa[m] > 0) & (ab[m] > 0) & (Qa[m, 0] > 0) & (Qb[m, 0] > 0)
+        if not on.any():
+            continue
+        Ua, Ub = Qa[m][:, on] / aa[m, on], Qb[m][:, on] / ab[m, on]
+        va, vb = Ua[1:1 + D] / Ua[0], Ub[1:1 + D] / Ub[0]
+        g, pi = case.gamma[m], case.pinf[m]
+        pa = (g - 1) * (Ua[D + 1] - 0.5 * Ua[0] * (va ** 2).sum(0)) - g * pi
+        pb = (g - 1) * (Ub[D + 1] - 0.5 * Ub[0] * (vb ** 2).sum(0)) - g * pi
+        w = ab[m, on]
+        du += float((w * np.abs(va - vb).sum(0)).sum())
+        dun += float((w * np.sqrt((vb ** 2).sum(0))).sum())
+        dp += float((w * np.abs(pa - pb)).sum())
+        dpn += float((w * np.abs(pb)).sum())
+    out["u_l1"] = du / max(dun, 1e-300)
+    out["p_l1"] = dp / max(dpn, 1e-300)
+    out["alpha_l1"] = float(np.abs(aa - ab).sum() / np.abs(ab).sum())
+    h = min((case.hi[d] - case.lo[d]) / case.n[d] for d in range(D))
+    out["phi_max_over_h"] = float(np.abs(a["phi"] - b["phi"]).max() / h)
+    out["chi_cells_differ"] = int((a["chi"] != b["chi"]).sum())
+    return out
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -394,22 +458,22 @@ def run_gpu(args):
     import paper_1704_00519_gb300.msf as msf
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
-    case = make_case()
+    case = make_case(args.case if args.only else "sphere")
     cells, stages = case.cells, 3
     K, W = args.steps, max(3, args.warmup)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
-    def timed(precision):
+    def timed(precision, k_steps):
         s = msf.Solver(case, precision=precision, stream=sptr, profile=1)
         s.step(W, case.t_end)
-        step_ms, flux_ms = [], []
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        flux_ms = []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k_steps)]
         clocks = ClockSampler(local)
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         clocks.start()
-        for k in range(K):
+        for k in range(k_steps):
             flush.fill_(float(k))
             ev[k][0].record(stream)
             s.step(1, case.t_end, sync=False)
@@ -423,20 +487,19 @@ def run_gpu(args):
         return s, step_ms, flux_ms, clk
 
     if args.only:
-        s, ms, fl, _ = timed(msf.MSF_FP32_BULK if args.only == "fp32" else msf.MSF_FP64)
+        s, ms, fl, _ = timed(msf.MSF_FP32_BULK if args.only == "fp32" else msf.MSF_FP64, K)
         if rank == 0:
-            print(json.dumps({"only": args.only, "ms_per_step": sum(ms) / K, "flux_ms_per_step": sum(map(sum, fl)) / K}))
+            print(json.dumps({"only": args.only, "case": args.case, "ms_per_step": sum(ms) / K,
+                              "flux_ms_per_step": sum(map(sum, fl)) / K}))
         return 0
-    s32, ms32, fl32, clk = timed(msf.MSF_FP32_BULK)
-    s64, ms64, fl64, _ = timed(msf.MSF_FP64)
+    K64 = min(K, 20)
+    s32, ms32, fl32, clk = timed(msf.MSF_FP32_BULK, K)
+    s64, ms64, fl64, _ = timed(msf.MSF_FP64, K64)
     total32 = sum(ms32) / 1e3
     total64 = sum(ms64) / 1e3
     total32, total64 = max_over_ranks([total32, total64], dev)
     value = job_rate(cells * stages * K, world, total32)
-    value64 = job_rate(cells * stages * K, world, total64)
-    a, b = s32.state(), s64.state()
-    ra, rb = a["Q"][:, 0].sum(0), b["Q"][:, 0].sum(0)
-    l1 = float(np.abs(ra - rb).sum() / np.abs(rb).sum())
+    value64 = job_rate(cells * stages * K64, world, total64)
 
     # roofline of the dominant kernel (flux update), FP32-bulk form
     npairs = pairs_per_cell(s32)
@@ -445,6 +508,29 @@ def run_gpu(args):
     achieved = bytes_step / flux_s / 1e9
     peak, peak_kind = measured_peaks()
     traffic = profiled_traffic("fp32_bulk")
+    flux64_s = sum(sum(x) for x in fl64) / 1e3 / K64
+    npairs64 = pairs_per_cell(s64)
+    s32.close()
+    s64.close()
+    fma64 = msf.fma_peak(msf.MSF_FP64, sptr)
+    fma32 = msf.fma_peak(msf.MSF_FP32_BULK, sptr)
+    flops64 = npairs64 * 3 * flux_flops_per_pair_stage(case.dim)
+    achieved64 = flops64 / flux64_s
+
+    # every output of the FP32-bulk form against the plain FP64 path after the
+    # same steps from the same start
+    errs = {}
+    pair = []
+    for prec in (msf.MSF_FP32_BULK, msf.MSF_FP64):
+        s = msf.Solver(case, precision=prec, stream=sptr)
+        s.step(W + K64, case.t_end)
+        pair.append((s.state(), s.totals()[0]))
+        s.close()
+    errs = output_errors(case, pair[0][0], pair[1][0])
+    t32, t64 = pair[0][1], pair[1][1]
+    errs["totals_max_rel"] = float(np.abs(t32 - t64).max() / np.abs(t64).sum())
+    errs["steps"] = W + K64
+    del pair
 
     # end to end through the public API with host buffers: initial data in,
     # K steps, final state out (wall clock)
@@ -463,24 +549,24 @@ def run_gpu(args):
     e2e_val = job_rate(cells * stages * K, world, e2e_s)
     h2d = phi.nbytes + chi.nbytes + prim.nbytes
     d2h = st["Q"].nbytes + st["alpha"].nbytes + st["phi"].nbytes + st["chi"].nbytes
+    launches = se.launches_per_step() * K
+    se.close()
+    del st
 
-    launches = s32.launches_per_step() * K
     batched = batched_rates(msf, torch, sptr, max(K, 10), 3)
     icf = icf_rates(msf, torch, sptr, 50)
-    s32.close()
-    s64.close()
-    se.close()
     workloads = workload_rates(msf, torch, sptr, 10)
     later = later_window(msf, torch, sptr, flush, 10)
     adjoint = adjoint_rates(msf, torch, sptr, 4)
-    adjoint["vs_fp64_forward"] = adjoint["value"] / workloads["shock_sphere_256x128x128"]["fp64"]["value"]
+    adjoint["vs_fp64_forward"] = adjoint["value"] / value64
     if rank != 0:
         return 0
 
-    # CPU oracle on a bounded sample of the same workload
+    # CPU oracle on a bounded sample of the same workload: one full step on
+    # every host core (OpenMP build; the plain build gives the same bits)
     from oracle import oracle as orc
-    orc.build()
-    cpu_val, cpu_secs, cpu_steps = oracle_rate(case, 2, 0)
+    orc.build(openmp=True)
+    cpu_val, cpu_secs, cpu_steps, cpu_thr = oracle_rate(case, 1, 0, openmp=True)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -488,27 +574,34 @@ def run_gpu(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD["name"], "cells": cells, "materials": case.nmat,
                    "precision": "fp32_bulk (FP32 fluxes, FP64 storage/geometry/correction/totals)",
-                   "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+                   "l2": "flushed between timed steps (256 MiB write outside the timed events); the state (1.1 GB) exceeds L2",
                    "parallelism": f"replicas{world}"},
-        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * total64 / K,
-                 "flux_ms_per_step": sum(sum(x) for x in fl64) / K},
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * total64 / K64, "steps": K64,
+                 "flux_ms_per_step": 1e3 * flux64_s},
         "fp32_over_fp64": value / value64,
-        "l1_rho_fp32_vs_fp64": l1,
-        "roofline": {"kernel": "k_flux_update<2,float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+        "roofline_fp64": {"kernel": "k_flux_update<3,double>", "bound": "alu", "achieved": achieved64 / 1e12,
+                          "peak": fma64 / 1e12, "unit": "TFLOP/s", "frac": achieved64 / fma64,
+                          "peak_source": "measured here: msf_fma_peak FP64 (independent FMA chains on every SM)",
+                          "flops_per_pair_stage": flux_flops_per_pair_stage(case.dim),
+                          "flux_ms_per_step": 1e3 * flux64_s},
+        "fma_peak_tflops": {"fp64": fma64 / 1e12, "fp32": fma32 / 1e12},
+        "fp32_error_vs_fp64": errs,
+        "roofline": {"kernel": "k_flux_update<3,float>", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                      "algorithmic_bytes_per_step": bytes_step, "flux_ms_per_step": 1e3 * flux_s,
                      "flux_share_of_step": flux_s / (total32 / K)},
-        "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{cpu_steps} full TVD-RK3 steps of {WORKLOAD['name']} (single thread)"},
+        "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": cpu_thr, "kind": "oracle",
+                         "sample": f"{cpu_steps} full TVD-RK3 step of {WORKLOAD['name']} from its initial state "
+                                   f"({cpu_secs:.1f} s), OpenMP oracle on {cpu_thr} threads"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                 "how": "wall clock: msf_set_levelset from host arrays, K steps, msf_get_state to host"},
         "gpu_launches": launches,
         "clocks": clk,
+        "workloads": workloads,
+        "triple_point_from_t_0.3": later,
         "batched_1d": batched,
         "icf_shell_study": icf,
-        "triple_point_from_t_0.3": later,
-        "workloads": workloads,
         "adjoint": adjoint,
     }
     print(json.dumps(line), flush=True)

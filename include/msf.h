@@ -138,8 +138,15 @@ typedef struct {
  *   literal_normal   1: each area vector S^m replaced by |S^m| n^m, the
  *                material's own level-set normal (the printed form of the
  *                exchange flux of Sec. 2.3.2); 0 (default): S^m itself
- * Tapes and the adjoint step refuse contexts with a literal option set
- * (MSF_EUNSUPPORTED). */
+ *   positivity   1: every face flux is limited towards the first-order
+ *                Lax-Friedrichs flux just enough that the density and
+ *                p + pinf of the two half states it feeds stay positive
+ *                (Hu, Adams & Shu, J. Comput. Phys. 242, 2013), for long runs
+ *                that reach near-vacuum states; 0 (default): the plain
+ *                WENO5-LLF flux of Sec. 3 (the paper has no positivity
+ *                treatment)
+ * Tapes and the adjoint step refuse contexts with a literal option or the
+ * positivity limiter set (MSF_EUNSUPPORTED). */
 typedef struct {
   int32_t precision;
   double cfl, weno_eps, mix_alpha;
@@ -150,6 +157,7 @@ typedef struct {
   void* stream;
   int32_t rk_stages;
   int32_t literal_reduced, literal_normal;
+  int32_t positivity;
 } msf_options;
 
 /* Fill opt with the defaults above for a grid of dimension dim. */
@@ -337,6 +345,15 @@ msf_status msf_profile_read(msf_ctx* ctx, double* flux_ms);
  * MSF_ESTATE. */
 msf_status msf_cfl_dt_noalloc(const double* U, int64_t cells, int32_t dim, const msf_eos* eos, const double* h,
                               double cfl, double* dt_out, void* stream);
+
+/* FMA throughput of the CUDA cores of the current device, in flop/s (two
+ * flops per fused multiply-add): precision MSF_FP64 measures FP64, any other
+ * valid precision (MSF_FP32_BULK) FP32. The paper has no counterpart: this is
+ * a measurement service, the denominator of the arithmetic roofline of the
+ * flux kernels. Runs independent FMA chains on every SM (best of five
+ * launches, CUDA events on `stream`), synchronises, allocates nothing.
+ * Errors: MSF_EINVAL (message via msf_last_error(NULL)), MSF_ECUDA. */
+msf_status msf_fma_peak(int32_t precision, double* flops_per_s, void* stream);
 
 /* Human-readable message for the last non-OK status of this context
  * (or of msf_create when ctx is NULL). Never NULL. */

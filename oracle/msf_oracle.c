@@ -969,6 +969,67 @@ static const double RKC3[4] = {0.0, 1.0, 0.5, 1.0};
 static const double RKC2[3] = {0.0, 1.0, 1.0};
 static double rk_c(const orc* o, int s) { return o->S == 2 ? RKC2[s] : RKC3[s]; }
 
+/* Positivity-preserving limiting of one face flux (Hu, Adams & Shu, J.
+ * Comput. Phys. 242, 2013), a reading added for long runs (the paper has no
+ * positivity treatment). The update of the two cells sharing the face is a
+ * convex combination of half states u_L - lam F and u_R + lam F with
+ * lam = 2 D dt / h_d; the first-order Lax-Friedrichs flux
+ * F_LF = (F(u_L) + F(u_R) - a (u_R - u_L)) / 2 (a the stencil's wave-speed
+ * maximum) keeps them physical under the CFL bound. The high-order flux F is
+ * replaced by F_LF + theta (F - F_LF) with the largest theta in [0, 1] for
+ * which the half states keep rho and p + pinf at or above
+ * eps = min(1e-13, the values of the Lax-Friedrichs half states): first the
+ * density (linear in theta), then p + pinf along the segment from the
+ * Lax-Friedrichs half state to the density-limited one (p is concave in the
+ * conserved variables, so the linear bound is safe). Tait materials take
+ * the density step only (their p + pinf is positive with rho). A flux whose
+ * half states need no limiting is kept bit for bit. */
+static void pp_limit(const orc* o, int m, int d, const double* uL, const double* uR, const double* FL,
+                     const double* FR, double a, double* Fh) {
+  const int D = o->D, NV = o->NV;
+  const double lam = ((2.0 * D) * o->dt) * o->rh[d];
+  double Flf[5], hl[2][5], hh[2][5];
+  for (int v = 0; v < NV; v++) Flf[v] = 0.5 * ((FL[v] + FR[v]) - a * (uR[v] - uL[v]));
+  for (int v = 0; v < NV; v++) {
+    hl[0][v] = uL[v] - lam * Flf[v];
+    hl[1][v] = uR[v] + lam * Flf[v];
+    hh[0][v] = uL[v] - lam * Fh[v];
+    hh[1][v] = uR[v] + lam * Fh[v];
+  }
+  /* density */
+  double eps = fmin(1e-13, fmin(hl[0][0], hl[1][0]));
+  double th = 1.0;
+  for (int s = 0; s < 2; s++)
+    if (hh[s][0] < eps) th = fmin(th, (hl[s][0] - eps) / (hl[s][0] - hh[s][0]));
+  /* a flux that needs no limiting is kept as it is */
+  double F1[5];
+  for (int v = 0; v < NV; v++) F1[v] = th < 1.0 ? Flf[v] + th * (Fh[v] - Flf[v]) : Fh[v];
+  if (o->p.eos_kind[m] != 1) {
+    /* p + pinf = (gamma - 1)(E - |rho u|^2 / (2 rho)) - gamma pinf + pinf */
+    double ql[2], q1[2];
+    for (int s = 0; s < 2; s++) {
+      const double* u = s ? uR : uL;
+      const double sg = s ? 1.0 : -1.0;
+      double h1[5];
+      for (int v = 0; v < NV; v++) h1[v] = u[v] + sg * (lam * F1[v]);
+      double kl = 0.0, k1 = 0.0;
+      for (int e = 0; e < D; e++) {
+        kl += hl[s][1 + e] * hl[s][1 + e];
+        k1 += h1[1 + e] * h1[1 + e];
+      }
+      ql[s] = (o->gm1[m] * (hl[s][D + 1] - 0.5 * kl / hl[s][0]) - o->gpi[m]) + o->p.pinf[m];
+      q1[s] = (o->gm1[m] * (h1[D + 1] - 0.5 * k1 / h1[0]) - o->gpi[m]) + o->p.pinf[m];
+    }
+    double epq = fmin(1e-13, fmin(ql[0], ql[1]));
+    double tp = 1.0;
+    for (int s = 0; s < 2; s++)
+      if (q1[s] < epq) tp = fmin(tp, (ql[s] - epq) / (ql[s] - q1[s]));
+    if (tp < 1.0)
+      for (int v = 0; v < NV; v++) F1[v] = Flf[v] + tp * (F1[v] - Flf[v]);
+  }
+  for (int v = 0; v < NV; v++) Fh[v] = F1[v];
+}
+
 static void face_flux(orc* o, long cL, int d, int m, double* Fh) {
   int NV = o->NV, D = o->D;
   long s = o->st[d];
@@ -1000,6 +1061,7 @@ static void face_flux(orc* o, long cL, int d, int m, double* Fh) {
     }
     Fh[v] = orc_weno5(fp[0], fp[1], fp[2], fp[3], fp[4], eps) + orc_weno5(fm[5], fm[4], fm[3], fm[2], fm[1], eps);
   }
+  if (o->p.positivity) pp_limit(o, m, d, U[2], U[3], Fd[2], Fd[3], a, Fh);
 }
 
 static void flux_update(orc* o, int s, const double* Qs, double* Qout) {

@@ -48,6 +48,11 @@ typedef struct {
    * materials 0; literal_normal = 1 replaces each area vector S^m by
    * |S^m| n^m (the material's own level-set normal) */
   int32_t literal_reduced, literal_normal;
+  /* positivity = 1: every face flux is limited towards the first-order
+   * Lax-Friedrichs flux so that the density and p + pinf of the two half
+   * states it feeds stay positive (Hu, Adams & Shu 2013); the paper describes
+   * no positivity treatment, so this is off by default */
+  int32_t positivity;
 } orc_params;
 
 typedef struct orc orc;

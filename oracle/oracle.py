@@ -50,7 +50,7 @@ class Params(C.Structure):
         ("tait_rho0", C.c_double * MAXM), ("tait_p0", C.c_double * MAXM),
         ("geom", C.c_int32), ("fs_mat", C.c_int32), ("fs_rho", C.c_double), ("fs_p0", C.c_double),
         ("fs_t0", C.c_double), ("fs_t1", C.c_double), ("fs_p1", C.c_double),
-        ("literal_reduced", C.c_int32), ("literal_normal", C.c_int32),
+        ("literal_reduced", C.c_int32), ("literal_normal", C.c_int32), ("positivity", C.c_int32),
     ]
 
 
@@ -131,6 +131,7 @@ def make_params(p: dict) -> Params:
         setattr(s, k, float(p.get(k, 0.0)))
     s.literal_reduced = int(p.get("literal_reduced", 0))
     s.literal_normal = int(p.get("literal_normal", 0))
+    s.positivity = int(p.get("positivity", 0))
     return s
 
 

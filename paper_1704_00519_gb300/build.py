@@ -19,7 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I", os.path.join(HERE, "..", "include")]
 UNITS = [("msf_f64.cu", ["-fmad=false"]), ("msf_f32.cu", ["-fmad=true", "-use_fast_math"]), ("msf_capi.cu", ["-fmad=false"]),
-         ("msf_noalloc.cu", ["-fmad=false"])]
+         ("msf_noalloc.cu", ["-fmad=false"]), ("msf_peak.cu", ["-fmad=true"])]
 
 
 def nvcc():

@@ -85,7 +85,7 @@ class Case:
 def default_options(dim):
     return dict(cfl=0.6, weno_eps=1e-6, mix_alpha=0.5, ext_sweeps=dim + 3, vel_sweeps=6,
                 reinit_iters=6, scale_sep=1, reinit=1, scale_eps_h=0.0, phi_cap_h=8.0, rk_stages=3,
-                literal_reduced=0, literal_normal=0)
+                literal_reduced=0, literal_normal=0, positivity=0)
 
 
 def centres(n, lo, hi):

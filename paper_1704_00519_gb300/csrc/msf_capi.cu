@@ -110,6 +110,7 @@ extern "C" msf_status msf_default_options(int32_t dim, msf_options* opt) {
   opt->rk_stages = 3;
   opt->literal_reduced = 0;
   opt->literal_normal = 0;
+  opt->positivity = 0;
   return MSF_OK;
 }
 
@@ -136,7 +137,7 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
       opt->ext_sweeps < 1 || opt->ext_sweeps > 64 || opt->vel_sweeps < 0 || opt->vel_sweeps > 64 ||
       opt->reinit_iters < 0 || opt->reinit_iters > 64 || !(opt->phi_cap_h >= 4.0) || !(opt->scale_eps_h >= 0.0) ||
       (opt->rk_stages != 2 && opt->rk_stages != 3) || (opt->literal_reduced != 0 && opt->literal_reduced != 1) ||
-      (opt->literal_normal != 0 && opt->literal_normal != 1))
+      (opt->literal_normal != 0 && opt->literal_normal != 1) || (opt->positivity != 0 && opt->positivity != 1))
     return fail(nullptr, MSF_EINVAL, "option out of range");
   for (int i = 0; i < n_instances; i++) {
     const msf_grid& gr = grids[i];
@@ -273,6 +274,7 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
     g.scale_sep = opt->scale_sep;
     g.reinit = opt->reinit;
     g.literal = (opt->literal_reduced ? 1 : 0) | (opt->literal_normal ? 2 : 0);
+    g.positivity = opt->positivity;
     // Shu-Osher TVD Runge-Kutta in the beta form; the ledger weight of stage s
     // is the coefficient of dt L(Q^(s)) in Q^{n+1}
     g.rk = opt->rk_stages;
@@ -360,6 +362,7 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
       b.mixT = (double*)carve(8 * nbmax * N);
       b.phir = (double*)carve(8 * nbmax * N);
       b.bflux = (double*)carve(8 * std::max<long long>(1, in.nbnd) * N * NV);
+      b.lpart = (double*)carve(8 * ((std::max<long long>(1, in.nbnd) + NTHREADS - 1) / NTHREADS) * N * NV);
       b.ctl = (Ctl*)carve(sizeof(Ctl));
       if (batched) {
         in.Fface = carve(ts * N * NV * (g.n[0] + 1));
@@ -449,7 +452,9 @@ static long long count_launches(const msf_ctx* c) {
     const Grid& g = in.g;
     const long long ext = tiled_ext(c, g) ? 1 : g.ext_sweeps;
     const long long vel = tiled_vel(c, g) ? 1 : g.vel_sweeps, re = 2LL * g.reinit_iters;
-    const long long per_stage = 1 + ext + 1 + 1 + 1 + vel + 1 + 1 + 1 + 1 + 1 + 2 + 4;
+    // prim, ext, cons, bc_uhat, interface, vel, flux, ledger (2), level set (2),
+    // bc_phichi, geometry (2), mixing (4)
+    const long long per_stage = 1 + ext + 1 + 1 + 1 + vel + 1 + 2 + 2 + 1 + 2 + 4;
     n += 1 + 1 + (2 + g.D) + 2 + 1 + g.rk * per_stage + 2 + 1;
     if (g.fs_mat >= 0) n += 1 + g.rk;
     if (g.scale_sep) n += 2 + 1;
@@ -948,8 +953,8 @@ static msf_status check_single(msf_ctx* c) {
   if (c->ninst != 1 || c->batched) return fail(c, MSF_EUNSUPPORTED, "tapes and the adjoint need a single-instance context");
   if (c->inst[0].g.geom != 0 || c->inst[0].g.fs_mat >= 0)
     return fail(c, MSF_EUNSUPPORTED, "tapes and the adjoint take Cartesian grids without a free surface");
-  if (c->inst[0].g.literal != 0)
-    return fail(c, MSF_EUNSUPPORTED, "tapes and the adjoint take the default interaction model (literal options off)");
+  if (c->inst[0].g.literal != 0 || c->inst[0].g.positivity != 0)
+    return fail(c, MSF_EUNSUPPORTED, "tapes and the adjoint take the default scheme (literal options and positivity off)");
   if (c->sticky) return fail(c, MSF_ESTATE, "context holds a device-detected error; reset with msf_set_state");
   return MSF_OK;
 }
@@ -995,7 +1000,8 @@ static bool tape_aligned(const void* p) { return ((uintptr_t)p & 255u) == 0; }
 extern "C" msf_status msf_tape_bytes(const msf_ctx* c, int64_t* bytes) {
   if (!c || !bytes) return MSF_EINVAL;
   if (c->ninst != 1 || c->batched) return MSF_EUNSUPPORTED;
-  if (c->inst[0].g.geom != 0 || c->inst[0].g.fs_mat >= 0 || c->inst[0].g.literal != 0) return MSF_EUNSUPPORTED;
+  if (c->inst[0].g.geom != 0 || c->inst[0].g.fs_mat >= 0 || c->inst[0].g.literal != 0 || c->inst[0].g.positivity != 0)
+    return MSF_EUNSUPPORTED;
   *bytes = (int64_t)tape_layout(c->inst[0].g).total;
   return MSF_OK;
 }

@@ -43,6 +43,7 @@ struct Grid {
   int ext_sweeps, vel_sweeps, reinit_iters, scale_sep, reinit;
   int rk;                       // Runge-Kutta stages (2 or 3)
   int literal;                  // bit 0: printed reduced model, bit 1: |S| n area vectors
+  int positivity;               // 1: positivity-preserving limiting of every face flux
   double rk_beta[3], rk_lw[3];  // beta_s of Eq. local-advection; ledger weight of stage s
   int bc[3][2], inflow_mat[3][2];
   double inflow_prim[3][2][5];
@@ -351,6 +352,46 @@ __device__ inline void cell_geom(const Grid& g, const double* phi, const uint8_t
     }
     *alpha = vol * (1.0 / 24.0);
   }
+}
+
+// one face f (axis f >> 1, side f & 1) of a 3D cell for material m: the raw
+// aperture of the face and the four tetrahedron fractions between the face and
+// the cell centre, each evaluated exactly as cell_geom<3> evaluates them (so
+// that a caller summing them in cell_geom<3>'s order gets the same bits)
+__device__ inline void face_geom3(const Grid& g, const double* phi, const uint8_t* chi, long long c, int m, int f,
+                                  double& ap, double (&t)[4]) {
+  int q[3];
+  coords(g, c, q);
+  const int i = q[0], j = q[1], k = q[2];
+  const double vc = phi_m(phi, chi, c, m);
+  const int d = f >> 1, side = f & 1;
+  const double fc = facec_val(g, phi, chi, c, d, side, m);
+  // corner (e, b, a) of the cell is grid vertex (i + e, j + b, k + a)
+  double p[4];
+  if (d == 0) {
+    p[0] = vertex_val(g, phi, chi, i + side, j, k, m);
+    p[1] = vertex_val(g, phi, chi, i + side, j + 1, k, m);
+    p[2] = vertex_val(g, phi, chi, i + side, j + 1, k + 1, m);
+    p[3] = vertex_val(g, phi, chi, i + side, j, k + 1, m);
+  } else if (d == 1) {
+    p[0] = vertex_val(g, phi, chi, i, j + side, k, m);
+    p[1] = vertex_val(g, phi, chi, i + 1, j + side, k, m);
+    p[2] = vertex_val(g, phi, chi, i + 1, j + side, k + 1, m);
+    p[3] = vertex_val(g, phi, chi, i, j + side, k + 1, m);
+  } else {
+    p[0] = vertex_val(g, phi, chi, i, j, k + side, m);
+    p[1] = vertex_val(g, phi, chi, i + 1, j, k + side, m);
+    p[2] = vertex_val(g, phi, chi, i + 1, j + 1, k + side, m);
+    p[3] = vertex_val(g, phi, chi, i, j + 1, k + side, m);
+  }
+  ap = 0.0;
+#pragma unroll
+  for (int e = 0; e < 4; e++) {
+    const double p0 = p[e], p1 = p[(e + 1) & 3];
+    ap += frac_tri(fc, p0, p1);
+    t[e] = frac_tet(vc, fc, p0, p1);
+  }
+  ap = ap * 0.25;
 }
 
 // min / max of phi^m over the simplex vertices of cell c (centre, corners, 3D face centres)

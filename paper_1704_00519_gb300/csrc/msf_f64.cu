@@ -192,7 +192,9 @@ void launch_set_tend_all(const BatchEntry* tab, int n, double t_end, cudaStream_
   k_set_tend_all<<<(n + 255) / 256, 256, 0, s>>>(tab, n, t_end);
 }
 void launch_ledger(const Grid& g, const Bufs& b, int nbnd, double w, cudaStream_t s) {
-  k_ledger<<<g.N * g.NV, NTHREADS, 0, s>>>(g, b, nbnd, w);
+  const int nparts = (nbnd + NTHREADS - 1) / NTHREADS;
+  if (nparts > 0) k_ledger_partial<<<nparts, NTHREADS, 0, s>>>(g, b, nbnd);
+  k_ledger<<<1, NTHREADS, 0, s>>>(g, b, nparts, w);
 }
 void launch_levelset(const Grid& g, const Bufs& b, const double* vel, double beta, double omb, int nblk,
                      cudaStream_t s) {

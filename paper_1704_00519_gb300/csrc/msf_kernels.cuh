@@ -216,10 +216,82 @@ __device__ __forceinline__ void phase_geom_mat_d(const Grid& g, const Bufs& b, i
     }
   }
 }
+// 3D: the same per-item results, with the simplex geometry of the items whose
+// 3^d block holds two or more materials (a fifth of the band, each a long FP64
+// chain of 24 tetrahedra) spread over the warp: the lanes holding such items
+// are gathered by a ballot and taken five at a time, six lanes per item (one
+// per face); the owning lane then sums the 24 tetrahedron fractions in
+// cell_geom<3>'s order. first_ and stride_ must be warp-aligned (lane l of a
+// warp starts at a multiple of 32 plus l, stride a multiple of 32).
+__device__ __forceinline__ void phase_geom_mat3(const Grid& g, const Bufs& b, int first_, int stride_) {
+  const int nb = b.ctl->nband, N = g.N;
+  const int total = nb * N;
+  const int lane = threadIdx.x & 31;
+  const unsigned FULL = 0xffffffffu;
+  for (int base = first_ - lane; base < total; base += stride_) {
+    const int it = base + lane;
+    int m = 0;
+    long long c = 0;
+    bool heavy = false;
+    if (it < total) {
+      m = it / nb;
+      c = b.band[it - m * nb];
+      int q[3];
+      coords(g, c, q);
+      const unsigned bits = block_bits(g, b.chi, q);
+      if ((b.smask[c] >> m) & 1u) {
+        double n[3];
+        normal_m(g, b.phi, b.chi, c, m, n);
+        for (int d = 0; d < 3; d++) b.nrm[((long long)m * 3 + d) * g.ncell + c] = n[d];
+      }
+      heavy = popcount8(bits) >= 2 && ((bits >> m) & 1u);
+      if (!heavy) {
+        const double a = (popcount8(bits) < 2 && b.chi[c] == m) ? 1.0 : 0.0;
+        b.alpha[midx(g, m, c)] = a;
+        for (int d = 0; d < 3; d++) {
+          b.Alo[aidx(g, d, m, c)] = a;
+          b.Ahi[aidx(g, d, m, c)] = a;
+        }
+      }
+    }
+    unsigned pend = __ballot_sync(FULL, heavy);
+    while (pend) {
+      // slot s of this round: the s-th pending lane; lanes 30 and 31 idle
+      const int slot = lane / 6, f = lane - 6 * slot;
+      unsigned mm = pend;
+      for (int s2 = 0; s2 < slot; s2++) mm &= mm - 1;
+      const int src = (slot < 5 && mm) ? __ffs(mm) - 1 : -1;
+      const long long ci = __shfl_sync(FULL, c, src < 0 ? 0 : src);
+      const int mi = __shfl_sync(FULL, m, src < 0 ? 0 : src);
+      double ap = 0.0, t[4] = {0.0, 0.0, 0.0, 0.0};
+      if (src >= 0) face_geom3(g, b.phi, b.chi, ci, mi, f, ap, t);
+      const bool mine = (pend >> lane) & 1u;
+      const int my_slot = __popc(pend & ((1u << lane) - 1u));
+      const bool owner = mine && my_slot < 5;
+      const int from = (owner ? my_slot : 0) * 6;
+      double vol = 0.0, apv[6];
+#pragma unroll
+      for (int ff = 0; ff < 6; ff++) {
+        apv[ff] = __shfl_sync(FULL, ap, from + ff);
+#pragma unroll
+        for (int e = 0; e < 4; e++) vol += __shfl_sync(FULL, t[e], from + ff);
+      }
+      if (owner) {
+        b.alpha[midx(g, m, c)] = vol * (1.0 / 24.0);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          b.Alo[aidx(g, d, m, c)] = apv[2 * d];
+          b.Ahi[aidx(g, d, m, c)] = apv[2 * d + 1];
+        }
+      }
+      for (int s2 = 0; s2 < 5 && pend; s2++) pend &= pend - 1;
+    }
+  }
+}
 __device__ __forceinline__ void phase_geom_mat(const Grid& g, const Bufs& b, int first_, int stride_) {
   if (g.D == 1) phase_geom_mat_d<1>(g, b, first_, stride_);
   else if (g.D == 2) phase_geom_mat_d<2>(g, b, first_, stride_);
-  else phase_geom_mat_d<3>(g, b, first_, stride_);
+  else phase_geom_mat3(g, b, first_, stride_);
 }
 __global__ void k_geom_mat(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
   if (!ctl_active(b)) return;
@@ -934,10 +1006,11 @@ __device__ __forceinline__ void stencil_prim(const T* u, T gm1, T gpi, T gam, T 
 }
 
 // WENO5 of the Lax-Friedrichs split fluxes through one face along axis d from
-// its 6-cell stencil: U[q][v] states, un normal velocity, pr pressure, cs sound speed
+// its 6-cell stencil: U[q][v] states, un normal velocity, pr pressure, cs sound
+// speed; returns the splitting's wave-speed bound a (the stencil maximum)
 template <int D, typename T>
-__device__ __forceinline__ void face_flux_regs(const T (&U)[6][D + 2], const T (&un)[6], const T (&pr)[6],
-                                               const T (&cs)[6], int d, T eps, T* Fh) {
+__device__ __forceinline__ T face_flux_regs(const T (&U)[6][D + 2], const T (&un)[6], const T (&pr)[6],
+                                            const T (&cs)[6], int d, T eps, T* Fh) {
   constexpr int NV = D + 2;
   T a = T(0);
 #pragma unroll
@@ -960,10 +1033,86 @@ __device__ __forceinline__ void face_flux_regs(const T (&U)[6][D + 2], const T (
     }
     Fh[v] = weno5<T>(fp[0], fp[1], fp[2], fp[3], fp[4], eps) + weno5<T>(fm[5], fm[4], fm[3], fm[2], fm[1], eps);
   }
+  return a;
+}
+
+// Positivity-preserving limiting of one face flux (Hu, Adams & Shu 2013; an
+// option, the paper has no positivity treatment): Fh is blended towards the
+// Lax-Friedrichs flux F_LF = (F(uL) + F(uR) - a (uR - uL)) / 2 with the largest
+// theta in [0, 1] that keeps rho, then p + pinf, of the half states
+// uL - lam F and uR + lam F (lam = 2 D dt / h_d) at or above
+// eps = min(1e-13, their Lax-Friedrichs values); the pressure step runs along
+// the segment from the Lax-Friedrichs half state (p is concave in the
+// conserved variables) and is skipped for Tait materials; a flux that needs no
+// limiting is kept bit for bit. Same operations, in the same order, as the
+// oracle.
+struct PosArgs {
+  int on;
+  double dt2d;  // 2 D dt of the stage
+  double gm1, gpi, pinf;
+  int tait;
+};
+template <int D, typename T>
+__device__ __forceinline__ void pp_limit(const T* uL, const T* uR, T unL, T unR, T pL, T pR, T a, int d,
+                                         const PosArgs& pa, T lam, T* Fh) {
+  constexpr int NV = D + 2;
+  T FL[NV], FR[NV], Flf[NV], F1[NV];
+  FL[0] = uL[1 + d];
+  FR[0] = uR[1 + d];
+#pragma unroll
+  for (int e = 0; e < D; e++) {
+    FL[1 + e] = e == d ? uL[1 + e] * unL + pL : uL[1 + e] * unL;
+    FR[1 + e] = e == d ? uR[1 + e] * unR + pR : uR[1 + e] * unR;
+  }
+  FL[D + 1] = unL * (uL[D + 1] + pL);
+  FR[D + 1] = unR * (uR[D + 1] + pR);
+#pragma unroll
+  for (int v = 0; v < NV; v++) Flf[v] = T(0.5) * ((FL[v] + FR[v]) - a * (uR[v] - uL[v]));
+  const T hl0 = uL[0] - lam * Flf[0], hl1 = uR[0] + lam * Flf[0];
+  const T hh0 = uL[0] - lam * Fh[0], hh1 = uR[0] + lam * Fh[0];
+  const T eps = fmin(T(1e-13), fmin(hl0, hl1));
+  T th = T(1);
+  if (hh0 < eps) th = fmin(th, (hl0 - eps) / (hl0 - hh0));
+  if (hh1 < eps) th = fmin(th, (hl1 - eps) / (hl1 - hh1));
+#pragma unroll
+  for (int v = 0; v < NV; v++) F1[v] = th < T(1) ? Flf[v] + th * (Fh[v] - Flf[v]) : Fh[v];
+  if (!pa.tait) {
+    const T gm1 = (T)pa.gm1, gpi = (T)pa.gpi, pinf = (T)pa.pinf;
+    T ql[2], q1[2];
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      const T* u = s ? uR : uL;
+      const T sg = s ? T(1) : T(-1);
+      T hl[NV], h1[NV];
+#pragma unroll
+      for (int v = 0; v < NV; v++) {
+        hl[v] = s ? u[v] + lam * Flf[v] : u[v] - lam * Flf[v];
+        h1[v] = u[v] + sg * (lam * F1[v]);
+      }
+      T kl = T(0), k1 = T(0);
+#pragma unroll
+      for (int e = 0; e < D; e++) {
+        kl += hl[1 + e] * hl[1 + e];
+        k1 += h1[1 + e] * h1[1 + e];
+      }
+      ql[s] = (gm1 * (hl[D + 1] - T(0.5) * kl / hl[0]) - gpi) + pinf;
+      q1[s] = (gm1 * (h1[D + 1] - T(0.5) * k1 / h1[0]) - gpi) + pinf;
+    }
+    const T epq = fmin(T(1e-13), fmin(ql[0], ql[1]));
+    T tp = T(1);
+    if (q1[0] < epq) tp = fmin(tp, (ql[0] - epq) / (ql[0] - q1[0]));
+    if (q1[1] < epq) tp = fmin(tp, (ql[1] - epq) / (ql[1] - q1[1]));
+    if (tp < T(1))
+#pragma unroll
+      for (int v = 0; v < NV; v++) F1[v] = Flf[v] + tp * (F1[v] - Flf[v]);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; v++) Fh[v] = F1[v];
 }
 
 template <int D, typename T>
-__device__ inline void face_flux_smem(const T* U, const T* P, int s0, int sstride, int d, int NS, T eps, T* Fh) {
+__device__ inline void face_flux_smem(const T* U, const T* P, int s0, int sstride, int d, int NS, T eps,
+                                      const PosArgs& pa, const double* rh, T* Fh) {
   // U[v*NS + s], P[e*NS + s] with e: 0..D-1 velocities, D pressure, D+1 sound speed
   constexpr int NV = D + 2;
   T u[6][NV], un[6], pr[6], cs[6];
@@ -976,7 +1125,8 @@ __device__ inline void face_flux_smem(const T* U, const T* P, int s0, int sstrid
     pr[q] = P[D * NS + s];
     cs[q] = P[(D + 1) * NS + s];
   }
-  face_flux_regs<D, T>(u, un, pr, cs, d, eps, Fh);
+  const T a = face_flux_regs<D, T>(u, un, pr, cs, d, eps, Fh);
+  if (pa.on) pp_limit<D, T>(u[2], u[3], un[2], un[3], pr[2], pr[3], a, d, pa, (T)(pa.dt2d * rh[d]), Fh);
 }
 
 // one face of a flux tile: aperture, WENO5-LLF flux and the boundary ledger.
@@ -984,7 +1134,7 @@ __device__ inline void face_flux_smem(const T* U, const T* P, int s0, int sstrid
 template <int D, typename T, int DIR>
 __device__ inline void flux_face(const Grid& g, const Bufs& b, const T* U, const T* P, T* F, double* A,
                                  const uint8_t* bad, const BndBase& bb, int f, int r, int x0, int y0, int z0, int m,
-                                 bool anyband, T eps, unsigned& err) {
+                                 bool anyband, T eps, const PosArgs& pa, unsigned& err) {
   using S = FluxSmem<D, T>;
   constexpr int NV = D + 2, TX = S::TX, TY = S::TY, SX = S::SX, SY = S::SY, NS = S::NS;
   int fx, fy, fz;
@@ -1028,7 +1178,7 @@ __device__ inline void flux_face(const Grid& g, const Bufs& b, const T* U, const
         err |= ERR_BAND;
       } else {
         if (isbad) err |= ERR_NEGATIVE;
-        face_flux_smem<D, T>(U, P, sL, sstride, DIR, NS, eps, Fh);
+        face_flux_smem<D, T>(U, P, sL, sstride, DIR, NS, eps, pa, g.rh, Fh);
       }
     }
     // boundary ledger: net inflow through the domain boundary
@@ -1152,6 +1302,13 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
     if (!((uni >> m) & 1u)) continue;
     const T mgm1 = T(g.gm1[m]), mgpi = T(g.gpi[m]), mgam = T(g.gamma[m]), mpinf = T(g.pinf[m]);
     const TaitK mtk = tait_of(g, m);
+    PosArgs pa;
+    pa.on = g.positivity;
+    pa.dt2d = (2.0 * D) * dt;
+    pa.gm1 = g.gm1[m];
+    pa.gpi = g.gpi[m];
+    pa.pinf = g.pinf[m];
+    pa.tait = mtk.on;
     // stage the stencil state and its primitive quantities
 #pragma unroll 1
     for (int s = tid; s < NS; s += blockDim.x) {
@@ -1228,11 +1385,11 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
     if (!idle)
       for (int f = tid; f < S::NF; f += blockDim.x) {
         if (f < S::NFX)
-          flux_face<D, T, 0>(g, b, U, P, F, A, bad, bb, f, f, x0, y0, z0, m, anyband, eps, err);
+          flux_face<D, T, 0>(g, b, U, P, F, A, bad, bb, f, f, x0, y0, z0, m, anyband, eps, pa, err);
         else if (D >= 2 && f < S::NFX + S::NFY)
-          flux_face<D, T, 1>(g, b, U, P, F, A, bad, bb, f, f - S::NFX, x0, y0, z0, m, anyband, eps, err);
+          flux_face<D, T, 1>(g, b, U, P, F, A, bad, bb, f, f - S::NFX, x0, y0, z0, m, anyband, eps, pa, err);
         else if (D >= 3)
-          flux_face<D, T, 2>(g, b, U, P, F, A, bad, bb, f, f - S::NFX - S::NFY, x0, y0, z0, m, anyband, eps, err);
+          flux_face<D, T, 2>(g, b, U, P, F, A, bad, bb, f, f - S::NFX - S::NFY, x0, y0, z0, m, anyband, eps, pa, err);
       }
     __syncthreads();
     // cell update
@@ -1315,21 +1472,41 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z, sizeof(T) 
   }
 }
 
-// sum the boundary-face fluxes of the stage (one block per material and
-// variable, fixed-order tree reduction) and add them to the ledger
-__global__ void k_ledger(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, int nbnd, double w) {
+// sum the boundary-face fluxes of the stage into the ledger, in two fixed-order
+// passes: each block adds NTHREADS faces for every (material, variable) by a
+// tree in shared memory, then one block adds the partial sums of all blocks
+__global__ void k_ledger_partial(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, int nbnd) {
   if (!ctl_active(b)) return;
-  const int NMV = g.N * g.NV, mv = blockIdx.x;
-  double s = 0.0;
-  for (int f = threadIdx.x; f < nbnd; f += blockDim.x) s += b.bflux[(long long)f * NMV + mv];
+  const int NMV = g.N * g.NV;
+  const int f = blockIdx.x * NTHREADS + threadIdx.x;
   __shared__ double red[NTHREADS];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+  for (int mv = 0; mv < NMV; mv++) {
+    red[threadIdx.x] = f < nbnd ? b.bflux[(long long)f * NMV + mv] : 0.0;
+    __syncthreads();
+    for (int k = NTHREADS / 2; k > 0; k >>= 1) {
+      if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) b.lpart[(long long)blockIdx.x * NMV + mv] = red[0];
     __syncthreads();
   }
-  if (threadIdx.x == 0) b.ctl->ledger[mv / g.NV][mv % g.NV] += w * b.ctl->dt * red[0];
+}
+__global__ void k_ledger(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, int nparts, double w) {
+  if (!ctl_active(b)) return;
+  const int NMV = g.N * g.NV;
+  __shared__ double red[NTHREADS];
+  for (int mv = 0; mv < NMV; mv++) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += NTHREADS) s += b.lpart[(long long)k * NMV + mv];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = NTHREADS / 2; k > 0; k >>= 1) {
+      if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) b.ctl->ledger[mv / g.NV][mv % g.NV] += w * b.ctl->dt * red[0];
+    __syncthreads();
+  }
 }
 
 // --------------------------------------------- level-set stage (a9) + R
@@ -1969,7 +2146,17 @@ __device__ __forceinline__ void flux1d_faces(const Grid& g, const Bufs& b, const
           err |= ERR_BAND;
         } else {
           if (isbad) err |= ERR_NEGATIVE;
-          face_flux_regs<1, T>(u, un, pr, cs, 0, eps, Fh);
+          const T a = face_flux_regs<1, T>(u, un, pr, cs, 0, eps, Fh);
+          if (g.positivity) {
+            PosArgs pa;
+            pa.on = 1;
+            pa.dt2d = 2.0 * b.ctl->dt;
+            pa.gm1 = g.gm1[m];
+            pa.gpi = g.gpi[m];
+            pa.pinf = g.pinf[m];
+            pa.tait = mtk.on;
+            pp_limit<1, T>(u[2], u[3], un[2], un[3], pr[2], pr[3], a, 0, pa, (T)(pa.dt2d * g.rh[0]), Fh);
+          }
         }
       }
     }

@@ -37,6 +37,7 @@ struct Bufs {
   double* mixT;             // [nbandmax][N] weight sum of the mixing pairs of the cell
   double* phir;             // [nbandmax][N] new local level-set values
   double* bflux;            // [nbnd][N][NV] boundary-face fluxes of the stage
+  double* lpart;            // [ceil(nbnd / NTHREADS)][N][NV] per-block partial sums of bflux
   Ctl* ctl;
 };
 

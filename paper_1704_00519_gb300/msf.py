@@ -57,7 +57,7 @@ class msf_options(C.Structure):
                 ("scale_sep", C.c_int32), ("reinit", C.c_int32), ("scale_eps_h", C.c_double),
                 ("phi_cap_h", C.c_double), ("use_graph", C.c_int32), ("profile", C.c_int32),
                 ("batch_mode", C.c_int32), ("stream", C.c_void_p), ("rk_stages", C.c_int32),
-                ("literal_reduced", C.c_int32), ("literal_normal", C.c_int32)]
+                ("literal_reduced", C.c_int32), ("literal_normal", C.c_int32), ("positivity", C.c_int32)]
 
 
 class MsfError(RuntimeError):
@@ -95,6 +95,7 @@ def _load():
         "msf_batch_block_size": ([P, C.POINTER(C.c_int32)], C.c_int),
         "msf_instance_info": ([P, C.c_int32, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)], C.c_int),
         "msf_cfl_dt_noalloc": ([P, C.c_int64, C.c_int32, C.POINTER(msf_eos), dp, C.c_double, P, P], C.c_int),
+        "msf_fma_peak": ([C.c_int32, dp, P], C.c_int),
         "msf_last_error": ([P], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -128,6 +129,14 @@ msf_profile_read = _lib.msf_profile_read
 msf_batch_block_size = _lib.msf_batch_block_size
 msf_instance_info = _lib.msf_instance_info
 msf_cfl_dt_noalloc = _lib.msf_cfl_dt_noalloc
+msf_fma_peak = _lib.msf_fma_peak
+
+
+def fma_peak(precision, stream=None):
+    """Measured FMA throughput (flop/s) of the current device's CUDA cores."""
+    out = C.c_double()
+    _check(msf_fma_peak(int(precision), C.byref(out), stream), None)
+    return out.value
 msf_last_error = _lib.msf_last_error
 
 
@@ -171,6 +180,7 @@ def make_options(p: dict, precision=MSF_FP64, stream=None, use_graph=1, profile=
         setattr(o, k, int(p[k]))
     o.literal_reduced = int(p.get("literal_reduced", 0))
     o.literal_normal = int(p.get("literal_normal", 0))
+    o.positivity = int(p.get("positivity", 0))
     o.use_graph = int(use_graph)
     o.profile = int(profile)
     o.stream = stream

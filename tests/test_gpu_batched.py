@@ -101,3 +101,28 @@ def test_batched_rk2_matches_oracle(msf):
         a, b = batch.state(i), o.state()
         assert np.array_equal(a["Q"][:c.nmat], b["Q"]), i
         assert np.array_equal(a["phi"], b["phi"])
+
+
+def test_batched_positivity_limiter_matches_oracle(msf):
+    """The persistent batched kernel with the positivity limiter: FP64
+    bit-identical to the oracle per instance, LeBlanc's problem among the
+    instances (it runs to its end only with the limiter)."""
+    from test_oracle_pins import _leblanc
+    steps, t_end = 40, 6.0
+    rng = np.random.default_rng(5)
+    pairs = []
+    while len(pairs) < 6:
+        c = cs.riemann_1d(rng, ncell=int(rng.integers(60, 420)))
+        o = orc.Oracle(c, positivity=1)
+        if o.step(steps, t_end) == 0:
+            pairs.append((c, o))
+    lb = _leblanc(300)
+    o = orc.Oracle(lb, positivity=1)
+    assert o.step(steps, t_end) == 0
+    pairs.append((lb, o))
+    batch = msf.Batch([c for c, _ in pairs], precision=0, positivity=1)
+    batch.step(steps, t_end)
+    for i, (c, o) in enumerate(pairs):
+        a, b = batch.state(i), o.state()
+        assert np.array_equal(a["Q"][:c.nmat], b["Q"]), i
+        assert np.array_equal(a["phi"], b["phi"])

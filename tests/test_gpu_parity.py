@@ -37,9 +37,9 @@ def l1_rho(Qa, Qb):
     return float(np.abs(ra - rb).sum() / np.abs(rb).sum())
 
 
-def run_pair(msf, case, steps, t_end=None, precision=0, **opts):
+def run_pair(msf, case, steps, t_end=None, precision=0, openmp=False, **opts):
     t_end = case.t_end if t_end is None else t_end
-    o = orc.Oracle(case, **opts)
+    o = orc.Oracle(case, openmp=openmp, **opts)
     eo = o.step(steps, t_end)
     s = msf.Solver(case, precision=precision, **opts)
     s.step(steps, t_end)
@@ -172,6 +172,26 @@ def test_literal_interaction_options_fp64(msf, lit, ln):
         compare(o, s, FP64_L1, exact=True)
 
 
+@pytest.mark.parametrize("maker,steps", [
+    (lambda: __import__("test_oracle_pins")._leblanc(400), 100000),
+    (lambda: __import__("test_oracle_pins")._leblanc(400, two=True), 100000),
+    (lambda: cs.triple_point(112, 48), 60),
+    (lambda: cs.shock_bubbles(96, 32), 30),
+    (lambda: cs.random_case(3, (18, 13, 11), 2, 4), 4),
+], ids=["leblanc", "leblanc_interface", "triple_point", "bubbles_inflow", "random_3d"])
+def test_positivity_limiter_fp64_and_fp32(msf, maker, steps):
+    """The positivity-preserving flux limiter (option positivity = 1): FP64
+    equals the oracle (LeBlanc's problem runs to t = 6 only with it); the
+    FP32-bulk form is within the FP32 tolerance."""
+    case = maker()
+    o, s, eo = run_pair(msf, case, steps, positivity=1)
+    assert eo == 0
+    compare(o, s, FP64_L1, exact=True)
+    s32 = msf.Solver(case, precision=msf.MSF_FP32_BULK, positivity=1)
+    s32.step(steps, case.t_end)
+    compare(o, s32, FP32_L1)
+
+
 def test_correction_choice_at_start_up_fp64(msf):
     """The T-junction of the oracle pin: with each material made the lightest
     in turn, and with densities where the lightest by mass is neither the
@@ -264,6 +284,33 @@ def test_full_size_fp32_form_against_fp64(msf, maker, steps):
         states.append(st)
         s.close()
     assert l1_rho(states[1]["Q"], states[0]["Q"]) <= FP32_L1
+
+
+@pytest.mark.parametrize("maker", [lambda: cs.shock_sphere((48, 32, 32)),
+                                   lambda: cs.random_case(3, (48, 32, 32), 3, 8)], ids=["sphere", "random3"])
+def test_3d_fp64_many_tiles(msf, maker):
+    """3D at 48 x 32 x 32 (6 x 4 x 8 flux tiles of 8 x 8 x 4, persistent CTAs
+    taking them from the counter, band and idle tiles among them) for 10
+    steps (the random network: junctions where the correction fires): the
+    FP64 path equals the oracle."""
+    case = maker()
+    o, s, eo = run_pair(msf, case, 10, openmp=True)
+    assert eo == 0
+    compare(o, s, FP64_L1, exact=True)
+
+
+def test_two_bubbles_512x128_50_steps(msf):
+    """The two-bubble shock (inflow, walls, two heavy and light bubbles) at
+    512 x 128, 50 steps: 256 flux tiles of 32 x 8, persistent-CTA scheduling
+    and idle tiles with many tiles in flight; FP64 equals the oracle, the
+    FP32-bulk form is within the FP32 tolerance."""
+    case = cs.shock_bubbles(512, 128)
+    o, s, eo = run_pair(msf, case, 50, openmp=True)
+    assert eo == 0
+    compare(o, s, FP64_L1, exact=True)
+    s32 = msf.Solver(case, precision=msf.MSF_FP32_BULK)
+    s32.step(50, case.t_end)
+    compare(o, s32, FP32_L1)
 
 
 @pytest.mark.parametrize("gamma_right", [1.667, 1.249])
