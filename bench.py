@@ -327,6 +327,64 @@ def adjoint_rates(msf, torch, stream, K):
             "how": "msf_adjoint_step per step (recomputes the stages from the tape); events on the context stream"}
 
 
+def adjoint_gradient(msf, torch, stream, steps=200):
+    """The adjoint form at the configured scale: d(J1, J2)/d(rho_bubble,
+    gamma_bubble, Mach) of the 3D shock-sphere workload (256 x 128 x 128,
+    FP32-bulk context) over `steps` TVD-RK3 steps, through the autograd
+    function MsfStep (taped forward steps, msf_adjoint_step in the backward
+    pass). Only the tapes (the stage checkpoints) stay resident between the
+    passes, with the wall rows J2 needs; the step count is reduced when the
+    device has no room for the tapes."""
+    from paper_1704_00519_gb300 import adjoint as adj
+    import paper_1704_00519_gb300.cases as cs
+    prob = adj.ShockBubble((256, 128, 128))
+    th0 = prob.theta0()
+    case0 = prob.case(th0)
+    solver = msf.Solver(case0, precision=msf.MSF_FP32_BULK, stream=stream)
+    free, _ = torch.cuda.mem_get_info()
+    tb = solver.tape_bytes()
+    fit = int(0.8 * free / (tb + 4 * 1024 * 1024))
+    K = max(1, min(steps, fit))
+    st0 = solver.state()
+    alpha0 = torch.tensor(st0["alpha"], device="cuda")
+    xs = torch.tensor(cs.centres(prob.n, case0.lo, case0.hi)[0].ravel(), device="cuda")
+    wall = torch.tensor(np.nonzero(cs.centres(prob.n, case0.lo, case0.hi)[1].ravel() < 1.0 / prob.n[1])[0],
+                        device="cuda")
+    h = [(case0.hi[d] - case0.lo[d]) / prob.n[d] for d in range(3)]
+    farea = h[0] * h[2]
+    torch.cuda.reset_peak_memory_stats()
+    theta = th0.clone().cuda().requires_grad_(True)
+    eos = prob.eos(theta)
+    inflow = prob.inflow(theta)
+    Q0 = prob.conserved(prob.prim(theta, "cuda"), eos, alpha0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Q, tapes, J2 = Q0, [], 0.0
+    alpha = torch.empty_like(alpha0)
+    for _ in range(K):
+        Q = adj.MsfStep.apply(Q, eos, inflow, solver, case0.t_end, tapes)
+        solver.get_alpha_device(alpha)
+        J2 = J2 + adj.tape_dt(tapes[-1]) * adj.wall_pressure_rows(Q, eos, alpha[:, wall].clone(), wall, farea)
+    J1 = adj.mass_centroid_x(Q, 1, xs) - adj.mass_centroid_x(Q0, 1, xs)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    g1 = torch.autograd.grad(J1, theta, retain_graph=True)[0]
+    g2 = torch.autograd.grad(J2, theta)[0]
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    out = {"workload": "shock_sphere_256x128x128", "precision": "fp32_bulk", "steps": K,
+           "theta": ["rho_bubble", "gamma_bubble", "mach"], "theta0": th0.tolist(),
+           "J1": float(J1), "J2": float(J2), "dJ1_dtheta": g1.cpu().tolist(), "dJ2_dtheta": g2.cpu().tolist(),
+           "forward_ms_per_step": 1e3 * (t1 - t0) / K, "backward_ms_per_step": 1e3 * (t2 - t1) / (2 * K),
+           "tape_bytes_per_step": tb, "peak_device_bytes": int(torch.cuda.max_memory_allocated()),
+           "how": "taped forward steps through MsfStep (tapes are torch allocations), two autograd.grad calls "
+                  "(each runs the K adjoint steps); wall clock with synchronisation, Python included"}
+    del tapes, Q, Q0, J1, J2
+    solver.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def later_window(msf, torch, stream, flush, K, t_start=0.3):
     """Triple point advanced to t = t_start (the waves have spread over much of
     the domain, so fewer tiles are idle), then K device-timed steps per
@@ -559,6 +617,7 @@ def run_gpu(args):
     later = later_window(msf, torch, sptr, flush, 10)
     adjoint = adjoint_rates(msf, torch, sptr, 4)
     adjoint["vs_fp64_forward"] = adjoint["value"] / value64
+    adjoint["gradient_200_steps"] = adjoint_gradient(msf, torch, sptr, 200)
     if rank != 0:
         return 0
 

@@ -1522,6 +1522,18 @@ static void scale_separation(orc* o) {
         }
     if (found) o->phit[c] = fabs(dmin - eps);
     o->chit[c] = (uint8_t)chs;
+    /* the cell now belongs to chi_1*; when chi_1* holds no content in it
+       (its volume appeared with the new topology, as in the droplet demo's
+       neck), the content of chi_1 becomes chi_1*'s: the totals are kept,
+       per-material mass knowingly not (counted with the merges), and chi_1,
+       left with a small volume and no content, is a small cell for mixing */
+    if (o->Q[QI(o, chs, 0, c)] == 0.0 && o->Q[QI(o, chi1, 0, c)] > 0.0) {
+      for (int v = 0; v < o->NV; v++) {
+        o->Q[QI(o, chs, v, c)] = o->Q[QI(o, chi1, v, c)];
+        o->Q[QI(o, chi1, v, c)] = 0.0;
+      }
+      count(o, ORC_C_MERGE);
+    }
   }
 #pragma omp parallel for schedule(static)
   for (long c = 0; c < o->ncell; c++) {

@@ -165,3 +165,19 @@ def wall_pressure(Q, eos, alpha, wall, farea):
     ap = (gam - 1.0) * (q[:, NV - 1] - 0.5 * mom2 / safe) - gam * pinf * alpha[:, wall]
     ap = torch.where(rho > 0, ap, torch.zeros_like(ap))
     return ap.sum() * farea
+
+
+def wall_pressure_rows(Q, eos, alpha_wall, wall, farea):
+    """wall_pressure with the volume fractions of the wall cells only
+    (alpha_wall [N, len(wall)]), for long runs that keep no full alpha."""
+    N, NV = Q.shape[0], Q.shape[1]
+    D = NV - 2
+    gam = eos[:, 0].view(N, 1)
+    pinf = eos[:, 1].view(N, 1)
+    q = Q[:, :, wall]
+    rho = q[:, 0]
+    mom2 = (q[:, 1:1 + D] ** 2).sum(1)
+    safe = torch.where(rho > 0, rho, torch.ones_like(rho))
+    ap = (gam - 1.0) * (q[:, NV - 1] - 0.5 * mom2 / safe) - gam * pinf * alpha_wall
+    ap = torch.where(rho > 0, ap, torch.zeros_like(ap))
+    return ap.sum() * farea

@@ -325,6 +325,8 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
       const long long nc = g.ncell, N = n_mat, NV = g.NV, nbmax = g.n_interior;
       Bufs& b = in.b;
       for (int k = 0; k < 3; k++) b.Q[k] = (double*)carve(8 * N * NV * nc);
+      b.Qf[0] = nullptr;
+      for (int k = 1; k < 3; k++) b.Qf[k] = ts == 4 ? (float*)carve(4 * N * NV * nc) : nullptr;
       b.phi = (double*)carve(8 * nc);
       b.phin = (double*)carve(8 * nc);
       b.chi = (uint8_t*)carve(nc);
@@ -360,6 +362,8 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
       b.mixbeta = (double*)carve(8 * nbmax * N * MIX_MAXT);
       b.mixin = (unsigned*)carve(4 * nbmax * N);
       b.mixT = (double*)carve(8 * nbmax * N);
+      b.mixlist = (int*)carve(4 * nbmax * N);
+      b.mixtouch = (uint8_t*)carve(nbmax);
       b.phir = (double*)carve(8 * nbmax * N);
       b.bflux = (double*)carve(8 * std::max<long long>(1, in.nbnd) * N * NV);
       b.lpart = (double*)carve(8 * ((std::max<long long>(1, in.nbnd) + NTHREADS - 1) / NTHREADS) * N * NV);
@@ -557,7 +561,11 @@ static msf_status enqueue_step(msf_ctx* c, char* tape = nullptr) {
       }
       const bool prof = c->ev[0] && &in == &c->inst[0];
       if (prof) cudaEventRecord(c->ev[2 * st], s);
-      cudaError_t fe = c->ops->flux(g, b, Qs, b.Q[0], Qo, beta, 1.0 - beta, in.bb, s);
+      // FP32-bulk form: stages 1 and 2 stage their bulk states from the FP32
+      // copy the update of the stage before wrote
+      const float* Qsf = st >= 1 ? b.Qf[st] : nullptr;
+      float* Qof = st < g.rk - 1 ? b.Qf[st + 1] : nullptr;
+      cudaError_t fe = c->ops->flux(g, b, Qs, b.Q[0], Qo, beta, 1.0 - beta, in.bb, Qsf, Qof, s);
       if (fe != cudaSuccess) return fail(c, MSF_ECUDA, std::string("flux launch: ") + cudaGetErrorString(fe));
       if (prof) cudaEventRecord(c->ev[2 * st + 1], s);
       launch_ledger(g, b, in.nbnd, g.rk_lw[st], s);
@@ -1052,7 +1060,7 @@ static void enqueue_replay(msf_ctx* c, const char* tape, bool rec) {
     c->ops->cons(g, b, Qs, W[cur], F[cur], nb, s);
     c->ops->bc_uhat(g, b, Qs, s);
     c->ops->interface(g, b, Qs, st, nb, s);
-    c->ops->flux(g, b, Qs, b.Q[0], Qo, g.rk_beta[st], 1.0 - g.rk_beta[st], in.bb, s);
+    c->ops->flux(g, b, Qs, b.Q[0], Qo, g.rk_beta[st], 1.0 - g.rk_beta[st], in.bb, nullptr, nullptr, s);
     launch_ledger(g, b, in.nbnd, g.rk_lw[st], s);
     tape_slot_load(in, tape, st + 1, s);
     launch_geometry(g, b, Qo, nullptr, nb, s);

@@ -58,6 +58,7 @@ struct Ctl {
   unsigned err;
   int nband, nbnd;
   unsigned tile_ctr;  // next flux tile of the running flux-update launch
+  unsigned mix_count; // (band cell, material) items of the running mixing pass that mix
   unsigned long long cnt[NCOUNT];
   double ledger[MAXM][5];
 };

@@ -211,7 +211,7 @@ void launch_mix(const Grid& g, const Bufs& b, double* Qc, int nblk, cudaStream_t
   k_mix_scatter<<<nblk, BAND_THREADS, 0, s>>>(g, b, Qc);
 }
 void launch_scale_sep(const Grid& g, const Bufs& b, int nblk, cudaStream_t s) {
-  k_scale_sep<<<nblk, BAND_THREADS, 0, s>>>(g, b);
+  k_scale_sep<<<nblk, BAND_THREADS, 0, s>>>(g, b, b.Q[0]);
   k_scatter_phichi<<<nblk, BAND_THREADS, 0, s>>>(g, b);
 }
 void launch_reinit(const Grid& g, const Bufs& b, int nblk, cudaStream_t s) {

@@ -575,6 +575,34 @@ __device__ __forceinline__ void interior_uhat(const Grid& g, const Bufs& b, cons
     for (int v = 0; v < g.NV; v++) u[v] = nanv;
   }
 }
+// the FP32 stencil state of an interior cell from the FP32 copy of the stage
+// state (the values (float)Q that interior_uhat_n<float> converts)
+template <int NV>
+__device__ __forceinline__ void interior_uhat_f(const Grid& g, const Bufs& b, const float* Qf, long long c, int m,
+                                                float* u) {
+  const float nanv = __int_as_float(0x7fc00000);
+  const float* Uh = (const float*)b.Uh;
+  const int bi = b.bandidx[c];
+  const uint8_t ch = b.chi[c];
+  float q[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) q[v] = Qf[qidx(g, m, v, c)];
+  if (bi >= 0) {
+    if ((b.smask[c] >> m) & 1u) {
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = Uh[qidx(g, m, v, c)];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = nanv;
+    }
+  } else if (ch == m) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) u[v] = q[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; v++) u[v] = nanv;
+  }
+}
 // the same with the variable count known at compile time; the band index,
 // the indicator and the conserved state are loaded together (one round of
 // memory latency for a bulk cell)
@@ -1232,9 +1260,20 @@ __device__ __noinline__ bool stencil_uniform(const T* U, const uint8_t* bad, int
 }
 
 // one tile of the flux update (tile index over the (x, y, z) tile grid)
+// exact error of a float sum: s + x = t + e exactly (Knuth's two-sum; no
+// multiplications, so no FMA contraction applies)
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  const float t = s + x;
+  const float bp = t - s;
+  const float e = (s - (t - bp)) + (x - bp);
+  s = t;
+  c += e;
+}
+
 template <int D, typename T>
 __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const double* Qs, const double* Qn,
-                                          double* Qout, double beta, double omb, const BndBase& bb, int tile) {
+                                          double* Qout, double beta, double omb, const BndBase& bb, int tile,
+                                          const float* Qsf, float* Qof) {
   using S = FluxSmem<D, T>;
   constexpr int NV = D + 2, TX = S::TX, TY = S::TY, TZ = S::TZ, SX = S::SX, SY = S::SY, NS = S::NS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1296,6 +1335,7 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
   // roots are costly, it stages the states first and derives the primitive
   // quantities only when it is not idle
   const bool cand = !anyband && interior_tile && g.geom == 0;
+  const bool fast_sum = !anyband && g.geom == 0 && (D < 2 || g.rh[1] == g.rh[0]) && (D < 3 || g.rh[2] == g.rh[0]);
   const bool defer = cand && sizeof(T) == 8;
   const int sref = 3 + SX * (S::HY + SY * S::HZ);
   for (int m = 0; m < g.N; m++) {
@@ -1328,7 +1368,12 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
         if (D >= 2) inner = inner && gy >= g.off[1] && gy < g.off[1] + g.n[1];
         if (D >= 3) inner = inner && gz >= g.off[2] && gz < g.off[2] + g.n[2];
         if (inner) {
-          interior_uhat_n<T, NV>(g, b, Qs, gc, m, u);
+          if constexpr (sizeof(T) == 4) {
+            if (Qsf && m != g.fs_mat) interior_uhat_f<NV>(g, b, Qsf, gc, m, u);
+            else interior_uhat_n<T, NV>(g, b, Qs, gc, m, u);
+          } else {
+            interior_uhat_n<T, NV>(g, b, Qs, gc, m, u);
+          }
         } else {
           const T* Uh = (const T*)b.Uh;
 #pragma unroll
@@ -1427,20 +1472,42 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
           if (v == 1) L = L + psrc;
         } else {
           if (!idle) {
+            if (sizeof(T) == 4 && fast_sum) {
+              // FP32-bulk form, a tile without band cells (every aperture 1)
+              // on a grid with equal spacings: the FP32 face fluxes of the
+              // cell summed with their exact rounding errors, converted
+              // once; each face's flux enters its two cells as the same
+              // float, so the sum over cells still telescopes in FP64
+              float sh = 0.0f, sc = 0.0f;
 #pragma unroll
-            for (int d = 0; d < D; d++) {
-              const double fl = (double)F[v * S::NF + flo[d]], fh = (double)F[v * S::NF + fhi[d]];
-              L = L + (A[flo[d]] * fl - A[fhi[d]] * fh) * g.rh[d];
+              for (int d = 0; d < D; d++) {
+                two_sum_acc(sh, sc, (float)F[v * S::NF + flo[d]]);
+                two_sum_acc(sh, sc, -(float)F[v * S::NF + fhi[d]]);
+              }
+              L = ((double)sh + (double)sc) * g.rh[0];
+            } else {
+#pragma unroll
+              for (int d = 0; d < D; d++) {
+                const double fl = (double)F[v * S::NF + flo[d]], fh = (double)F[v * S::NF + fhi[d]];
+                L = L + (A[flo[d]] * fl - A[fhi[d]] * fh) * g.rh[d];
+              }
             }
           }
           if (cut) L = L + b.X[qidx(g, m, v, c)] * g.rV;
         }
         if (m == g.fs_mat) L = 0.0;  // the ambient is not solved
         const long long qi = qidx(g, m, v, c);
-        const double qn = Qn[qi], qs = Qs[qi];
-        const double qv = beta * qn + omb * (qs + dt * L);
+        const double qs = Qs[qi];
+        double qv;
+        if (sizeof(T) == 4 && beta == 0.0) {
+          qv = qs + dt * L;  // the first stage (beta = 0, 1 - beta = 1)
+        } else {
+          const double qn = Qn[qi];
+          qv = beta * qn + omb * (qs + dt * L);
+        }
         if (!isfinite(qv)) err |= ERR_NONFINITE;
         Qout[qi] = qv;
+        if (sizeof(T) == 4 && Qof) Qof[qi] = (float)qv;
       }
     }
     __syncthreads();
@@ -1459,7 +1526,7 @@ template <int D, typename T>
 __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z, sizeof(T) == 4 ? 4 : 1)
     k_flux_update(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs,
                   const double* Qn, double* Qout, double beta, double omb, const __grid_constant__ BndBase bb,
-                  int ntiles) {
+                  int ntiles, const float* Qsf, float* Qof) {
   if (!ctl_active(b)) return;
   __shared__ int s_tile;
   for (;;) {
@@ -1468,7 +1535,7 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z, sizeof(T) 
     const int tile = s_tile;
     __syncthreads();
     if (tile >= ntiles) break;
-    flux_tile<D, T>(g, b, Qs, Qn, Qout, beta, omb, bb, tile);
+    flux_tile<D, T>(g, b, Qs, Qn, Qout, beta, omb, bb, tile, Qsf, Qof);
   }
 }
 
@@ -1727,6 +1794,7 @@ __device__ __forceinline__ void phase_mix_mark(const Grid& g, const Bufs& b, con
 }
 __global__ void k_mix_mark(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qc) {
   if (!ctl_active(b)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) b.ctl->mix_count = 0u;  // the list is filled by k_mix_weights
   phase_mix_mark(g, b, Qc, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
@@ -1738,7 +1806,7 @@ __global__ void k_mix_mark(const __grid_constant__ Grid g, const __grid_constant
 // cell's with weight beta a_s V_s / (a_s V_s + a_t V_t).
 // T sums a cell's weights: its own pairs in target order, then the pairs of
 // the neighbours that mix into it in (z, y, x) offset order.
-template <int DD>
+template <int DD, bool LIST>
 __device__ __forceinline__ void phase_mix_weights_d(const Grid& g, const Bufs& b, int first_, int stride_) {
   const int nb = b.ctl->nband, N = g.N, D = DD;
   const int total = nb * N;
@@ -1747,6 +1815,11 @@ __device__ __forceinline__ void phase_mix_weights_d(const Grid& g, const Bufs& b
     const long long c = b.band[k];
     const long long r = (long long)k * N + m;
     double T = 0.0;
+    if (LIST && (b.mixn[r] != 0xff || b.mixin[r] != 0u)) {
+      // an item that mixes: small, or a target of a small neighbour
+      b.mixlist[atomicAdd(&b.ctl->mix_count, 1u)] = (int)r;
+      b.mixtouch[k] = 1;
+    }
     if ((b.smask[c] >> m) & 1u) {
       const double ac = b.alpha[midx(g, m, c)], vc = vfac(g, c);
       const int nown = b.mixn[r];
@@ -1785,14 +1858,16 @@ __device__ __forceinline__ void phase_mix_weights_d(const Grid& g, const Bufs& b
     b.mixT[r] = T;
   }
 }
+template <bool LIST>
 __device__ __forceinline__ void phase_mix_weights(const Grid& g, const Bufs& b, int first_, int stride_) {
-  if (g.D == 1) phase_mix_weights_d<1>(g, b, first_, stride_);
-  else if (g.D == 2) phase_mix_weights_d<2>(g, b, first_, stride_);
-  else phase_mix_weights_d<3>(g, b, first_, stride_);
+  if (g.D == 1) phase_mix_weights_d<1, LIST>(g, b, first_, stride_);
+  else if (g.D == 2) phase_mix_weights_d<2, LIST>(g, b, first_, stride_);
+  else phase_mix_weights_d<3, LIST>(g, b, first_, stride_);
 }
+// grid kernel: also lists the items that mix, for k_mix_compute and k_mix_scatter
 __global__ void k_mix_weights(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
   if (!ctl_active(b)) return;
-  phase_mix_weights(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  phase_mix_weights<true>(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // Scale of a pair exchange from the weight sums of its two cells: when a
@@ -1812,17 +1887,15 @@ __device__ inline double mix_limit(double as, double Ts, double Tt) {
 // exchanges its small neighbours send to it (lexicographic neighbour order),
 // each scaled by mix_limit
 template <int DD>
-__device__ __forceinline__ void phase_mix_compute_d(const Grid& g, const Bufs& b, const double* Qc, int first_, int stride_) {
-    const int nb = b.ctl->nband, N = g.N, NV = DD + 2, D = DD;
-  const int total = nb * N;
-  for (int it = first_; it < total; it += stride_) {
-    const int m = it / nb, k = it - m * nb;
+__device__ __forceinline__ void mix_compute_item(const Grid& g, const Bufs& b, const double* Qc, int k, int m) {
+    const int N = g.N, NV = DD + 2, D = DD;
+  {
     const long long c = b.band[k];
     const long long r = (long long)k * N + m;
     double* out = b.mixq + r * NV;
     if (!((b.smask[c] >> m) & 1u)) {
       for (int v = 0; v < NV; v++) out[v] = Qc[qidx(g, m, v, c)];
-      continue;
+      return;
     }
     int q[3];
     coords(g, c, q);
@@ -1871,23 +1944,59 @@ __device__ __forceinline__ void phase_mix_compute_d(const Grid& g, const Bufs& b
     for (int v = 0; v < NV; v++) out[v] = Qc[qidx(g, m, v, c)] + acc[v];
   }
 }
+// every (band cell, material): the mixed state into mixq
+template <int DD>
+__device__ __forceinline__ void phase_mix_compute_d(const Grid& g, const Bufs& b, const double* Qc, int first_, int stride_) {
+  const int nb = b.ctl->nband, N = g.N;
+  const int total = nb * N;
+  for (int it = first_; it < total; it += stride_) {
+    const int m = it / nb, k = it - m * nb;
+    mix_compute_item<DD>(g, b, Qc, k, m);
+  }
+}
 __device__ __forceinline__ void phase_mix_compute(const Grid& g, const Bufs& b, const double* Qc, int first_, int stride_) {
   if (g.D == 1) phase_mix_compute_d<1>(g, b, Qc, first_, stride_);
   else if (g.D == 2) phase_mix_compute_d<2>(g, b, Qc, first_, stride_);
   else phase_mix_compute_d<3>(g, b, Qc, first_, stride_);
 }
+// grid kernel: only the listed items (a fifth of the band or less; the others
+// keep their state), so that the FP64 work of the exchanges runs on full
+// warps instead of the few lanes of a warp that hold a small cell
+template <int DD>
+__device__ __forceinline__ void mix_compute_listed(const Grid& g, const Bufs& b, const double* Qc, int first_, int stride_) {
+  const int N = g.N, total = (int)b.ctl->mix_count;
+  for (int it = first_; it < total; it += stride_) {
+    const int r = b.mixlist[it];
+    mix_compute_item<DD>(g, b, Qc, r / N, r - (r / N) * N);
+  }
+}
 __global__ void k_mix_compute(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qc) {
   if (!ctl_active(b)) return;
-  phase_mix_compute(g, b, Qc, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  const int first = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  if (g.D == 1) mix_compute_listed<1>(g, b, Qc, first, stride);
+  else if (g.D == 2) mix_compute_listed<2>(g, b, Qc, first, stride);
+  else mix_compute_listed<3>(g, b, Qc, first, stride);
 }
 // write the mixed states back; a material that lost all volume and has no
 // same-material neighbour is merged into the cell's primary material
+template <bool LIST>
 __device__ __forceinline__ void phase_mix_scatter(const Grid& g, const Bufs& b, double* Qc, int first_, int stride_) {
     const int nb = b.ctl->nband, N = g.N, NV = g.NV;
   unsigned long long nmerge = 0;
   for (int k = first_; k < nb; k += stride_) {
     const long long c = b.band[k];
     double* in = b.mixq + (long long)k * N * NV;
+    if (LIST) {
+      // only cells with a listed item changed; the unlisted materials of such
+      // a cell keep their state (mixq holds the listed ones only)
+      if (!b.mixtouch[k]) continue;
+      b.mixtouch[k] = 0;
+      for (int m = 0; m < N; m++) {
+        const long long r = (long long)k * N + m;
+        if (b.mixn[r] == 0xff && b.mixin[r] == 0u)
+          for (int v = 0; v < NV; v++) in[m * NV + v] = Qc[qidx(g, m, v, c)];
+      }
+    }
     const unsigned mb = b.mixmerge[k];
     if (mb) {
       const int pm = b.chi[c];
@@ -1910,14 +2019,14 @@ __device__ __forceinline__ void phase_mix_scatter(const Grid& g, const Bufs& b, 
 }
 __global__ void k_mix_scatter(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, double* Qc) {
   if (!ctl_active(b)) return;
-  phase_mix_scatter(g, b, Qc, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  phase_mix_scatter<true>(g, b, Qc, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // ------------------------------------------------- scale separation (a12)
-__device__ __forceinline__ void phase_scale_sep(const Grid& g, const Bufs& b, int first_, int stride_) {
+__device__ __forceinline__ void phase_scale_sep(const Grid& g, const Bufs& b, double* Q, int first_, int stride_) {
     const int nb = b.ctl->nband, N = g.N, D = g.D;
   const double eps = g.eps_ss;
-  unsigned long long nodd = 0;
+  unsigned long long nodd = 0, nmove = 0;
   for (int k = first_; k < nb; k += stride_) {
     const long long c = b.band[k];
     b.phit[k] = b.phi[c];
@@ -1977,12 +2086,22 @@ __device__ __forceinline__ void phase_scale_sep(const Grid& g, const Bufs& b, in
         }
     if (found) b.phit[k] = fabs(dmin - eps);
     b.chit[k] = (uint8_t)chs;
+    // the cell now belongs to chi_1*; when chi_1* holds no content in it, the
+    // content of chi_1 becomes chi_1*'s (totals kept, counted with the merges)
+    if (Q[qidx(g, chs, 0, c)] == 0.0 && Q[qidx(g, chi1, 0, c)] > 0.0) {
+      for (int v = 0; v < g.NV; v++) {
+        Q[qidx(g, chs, v, c)] = Q[qidx(g, chi1, v, c)];
+        Q[qidx(g, chi1, v, c)] = 0.0;
+      }
+      nmove++;
+    }
   }
   if (nodd) atomicAdd(&b.ctl->cnt[C_ODDBALL], nodd);
+  if (nmove) atomicAdd(&b.ctl->cnt[C_MERGE], nmove);
 }
-__global__ void k_scale_sep(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+__global__ void k_scale_sep(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, double* Q) {
   if (!ctl_active(b)) return;
-  phase_scale_sep(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  phase_scale_sep(g, b, Q, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // --------------------------------------------- band distance maintenance
@@ -2329,11 +2448,11 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
       }
       phase_mix_mark(g, b, (const double*)Qo, t, nt);
       __syncthreads();
-      phase_mix_weights_d<1>(g, b, t, nt);
+      phase_mix_weights_d<1, false>(g, b, t, nt);
       __syncthreads();
       phase_mix_compute_d<1>(g, b, (const double*)Qo, t, nt);
       __syncthreads();
-      phase_mix_scatter(g, b, Qo, t, nt);
+      phase_mix_scatter<false>(g, b, Qo, t, nt);
       __syncthreads();
     }
     if (t == 0) {
@@ -2343,7 +2462,7 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
     }
     __syncthreads();
     if (g.scale_sep) {
-      phase_scale_sep(g, b, t, nt);
+      phase_scale_sep(g, b, b.Q[0], t, nt);
       __syncthreads();
       phase_scatter_phichi(g, b, t, nt);
       __syncthreads();

@@ -18,8 +18,10 @@ struct Ops {
   void (*bc_uhat)(const Grid&, const Bufs&, const double* Qs, cudaStream_t);
   void (*dt)(const Grid&, const Bufs&, const double* Qs, cudaStream_t);
   void (*interface)(const Grid&, const Bufs&, const double* Qs, int stage, int nblk, cudaStream_t);
+  // Qsf: FP32 copy of Qs for the bulk staging (null: convert Qs); Qof: FP32
+  // copy of Qout to write (null: none); both null in FP64 contexts
   cudaError_t (*flux)(const Grid&, const Bufs&, const double* Qs, const double* Qn, double* Qout, double beta,
-                      double omb, const BndBase&, cudaStream_t);
+                      double omb, const BndBase&, const float* Qsf, float* Qof, cudaStream_t);
   // n_steps steps of every 1D instance of a batch, one CTA of bs threads per instance
   cudaError_t (*batched)(const BatchEntry* tab, const int* order, int n_inst, int n_steps, int bs, cudaStream_t);
 };

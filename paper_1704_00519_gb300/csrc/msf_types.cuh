@@ -8,6 +8,8 @@ namespace msf {
 
 struct Bufs {
   double* Q[3];             // Q^n, Q^(1), Q^(2): [N][NV][ncell]
+  float* Qf[3];             // FP32-bulk form: FP32 copies of Q^(1), Q^(2) written by the flux
+                            // update of the stage before (index 0 unused; null in FP64 contexts)
   double *phi, *phin;       // current and step-start distance
   uint8_t *chi, *chin;      // current and step-start indicator
   uint8_t* xs;              // 3^d material bits of chi (all cells)
@@ -35,6 +37,8 @@ struct Bufs {
   double* mixbeta;          // [nbandmax][N][MIX_MAXT] normalised mixing weights
   unsigned* mixin;          // [nbandmax][N] bit (offset code) of every neighbour that mixes into the cell
   double* mixT;             // [nbandmax][N] weight sum of the mixing pairs of the cell
+  int* mixlist;             // [nbandmax * N] items (k * N + m) of the running mixing pass that mix
+  uint8_t* mixtouch;        // [nbandmax] 1: a material of band cell k mixes in this pass
   double* phir;             // [nbandmax][N] new local level-set values
   double* bflux;            // [nbnd][N][NV] boundary-face fluxes of the stage
   double* lpart;            // [ceil(nbnd / NTHREADS)][N][NV] per-block partial sums of bflux

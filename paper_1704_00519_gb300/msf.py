@@ -248,6 +248,11 @@ class Solver:
         """Copy Q into a caller-owned device tensor (torch, float64, [N, NV, cells])."""
         _check(msf_get_state(self.h, 0, C.c_void_p(Q.data_ptr()), None, None, None, None, MSF_DEVICE), self.h)
 
+    def get_alpha_device(self, alpha):
+        """Copy the volume fractions into a caller-owned device tensor (torch,
+        float64, [N, cells])."""
+        _check(msf_get_state(self.h, 0, None, C.c_void_p(alpha.data_ptr()), None, None, None, MSF_DEVICE), self.h)
+
     def set_state(self, Q, phi, chi, t):
         a, ma, ka = _ptr(Q, "f8")
         b, mb, kb = _ptr(phi, "f8")

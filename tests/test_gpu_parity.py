@@ -221,6 +221,21 @@ def test_scale_separation_by_hand_fp64(msf, y0, y1, new_chi):
     assert np.abs(st["phi"][40:50] - 0.04).max() < 1e-12
 
 
+def test_scale_separation_droplet_fp64(msf):
+    """The droplet demo of Sec. 2.3.3, 10 steps: the GPU equals the oracle
+    (the neck's two cells separated, their content following their volume,
+    two new triple points) and the totals are kept."""
+    case = cs.scale_sep_demo("droplet", n=10)
+    s0 = msf.Solver(case)
+    tot0, _ = s0.totals()
+    o, s, eo = run_pair(msf, case, 10, t_end=10.0)
+    assert eo == 0
+    compare(o, s, FP64_L1, exact=True)
+    assert s.counters()["merge"] == 2
+    tot, led = s.totals()
+    assert np.abs((tot - tot0 - led).sum(0)).max() <= 1e-13 * np.abs(tot0).sum()
+
+
 @pytest.mark.parametrize("maker,steps", [(lambda: cs.triple_point(112, 48), 60), (lambda: cs.shock_bubbles(96, 32), 30),
                                          (lambda: cs.shock_tube_3(400), 200)])
 def test_fp32_bulk_form(msf, maker, steps):

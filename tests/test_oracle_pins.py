@@ -561,6 +561,51 @@ def test_scale_separation_removes_thin_filament():
     assert np.all(np.isfinite(tot))
 
 
+def _triple_vertices(chi, n):
+    """Grid vertices whose four cells hold all three materials."""
+    g = np.asarray(chi).reshape(n, n)
+    out = []
+    for j in range(1, n):
+        for i in range(1, n):
+            if {g[j - 1, i - 1], g[j - 1, i], g[j, i - 1], g[j, i]} >= {0, 1, 2}:
+                out.append((i, j))
+    return out
+
+
+def test_scale_separation_droplet():
+    """The droplet demo of Sec. 2.3.3 (10 x 10, h = 0.1, a droplet of radius
+    1.5 h separated from the material below by a one-cell neck): the neck's
+    two cells are the only oddballs; they go to the material below, so the
+    droplet now meets both other materials and two triple points appear at
+    its lower corners, while every other cell keeps its level set bit for bit.
+    The material below had no content in the neck (the interface lay on the
+    neck's lower faces), so the neck's content follows its volume (counted
+    with the merges); the run then stays physical and the totals are kept."""
+    n = 10
+    case = cs.scale_sep_demo("droplet", n=n)
+    assert _triple_vertices(case.chi, n) == []
+    o = orc.Oracle(case)
+    before = o.state()
+    o.scale_sep_only()
+    st = o.state()
+    changed = np.where(st["chi"] != before["chi"])[0]
+    assert sorted(changed.tolist()) == [3 * n + 4, 3 * n + 5]
+    assert np.all(before["chi"][changed] == 1) and np.all(st["chi"][changed] == 0)
+    keep = np.ones(case.cells, bool)
+    keep[changed] = False
+    assert np.array_equal(st["phi"][keep], before["phi"][keep])
+    assert o.counters()["oddball"] == 2
+    o = orc.Oracle(case)
+    tot0, _ = o.totals()
+    assert o.step(10, 10.0) == 0
+    st = o.state()
+    assert o.counters()["merge"] == 2 and o.counters()["oddball"] == 2
+    assert _triple_vertices(st["chi"], n) == [(4, 4), (6, 4)]
+    assert sorted(np.where(st["chi"] == 2)[0].tolist()) == [44, 45, 54, 55, 64, 65]
+    tot, led = o.totals()
+    assert np.abs((tot - tot0 - led).sum(0)).max() <= 1e-13 * np.abs(tot0).sum()
+
+
 def test_scale_separation_keeps_resolved_shapes():
     """Resolved structures have no oddball cells: the triple point's regions
     and the two bubbles are untouched by the model."""
