@@ -283,6 +283,49 @@ __device__ inline double frac_tet(double a, double b, double c, double d) {
   return num / den;
 }
 
+// The same fractions without divergent branches, for warps whose lanes take
+// different cases: the values are sorted by a network of exact compare and
+// exchange steps (equal values can only be +0 and -0 in another order, which
+// no formula below distinguishes), every case's numerator and denominator is
+// formed with the expressions above, and one division follows the selection,
+// so the results are those of frac_tri and frac_tet bit for bit.
+__device__ __forceinline__ void cx_desc(double& a, double& b) {
+  const double hi = b > a ? b : a, lo = b > a ? a : b;
+  a = hi;
+  b = lo;
+}
+__device__ __forceinline__ double frac_tri_nb(double a, double b, double c) {
+  cx_desc(a, b);
+  cx_desc(b, c);
+  cx_desc(a, b);
+  const int np = (a > 0.0) + (b > 0.0) + (c > 0.0);
+  const int nn = (a < 0.0) + (b < 0.0) + (c < 0.0);
+  const double n1 = a * a, d1 = (a - b) * (a - c);  // np == 1
+  const double n2 = c * c, d2 = (a - c) * (b - c);  // np == 2
+  const double q = (np == 1 ? n1 : n2) / (np == 1 ? d1 : d2);
+  if (nn == 0) return np == 0 ? 0.5 : 1.0;
+  if (np == 0) return 0.0;
+  return np == 1 ? q : 1.0 - q;
+}
+__device__ __forceinline__ double frac_tet_nb(double a, double b, double c, double d) {
+  cx_desc(a, b);
+  cx_desc(c, d);
+  cx_desc(a, c);
+  cx_desc(b, d);
+  cx_desc(b, c);
+  const int np = (a > 0.0) + (b > 0.0) + (c > 0.0) + (d > 0.0);
+  const int nn = (a < 0.0) + (b < 0.0) + (c < 0.0) + (d < 0.0);
+  const double n1 = a * a * a, d1 = ((a - b) * (a - c)) * (a - d);  // np == 1
+  const double m3 = -d;
+  const double n3 = m3 * m3 * m3, d3 = ((a - d) * (b - d)) * (c - d);  // np == 3
+  const double n2 = a * a * (b * b) - a * b * (a + b) * (c + d) + c * d * (a * a + a * b + b * b);
+  const double d2 = ((a - c) * (a - d)) * ((b - c) * (b - d));  // np == 2
+  const double q = (np == 1 ? n1 : (np == 3 ? n3 : n2)) / (np == 1 ? d1 : (np == 3 ? d3 : d2));
+  if (nn == 0) return np == 0 ? 0.5 : 1.0;
+  if (np == 0) return 0.0;
+  return np == 3 ? 1.0 - q : q;
+}
+
 // ---------------------------------- local level sets (Sec. 2.2, operator C_m)
 __device__ inline double phi_m(const double* phi, const uint8_t* chi, long long c, int m) {
   return chi[c] == m ? phi[c] : -phi[c];
@@ -359,7 +402,7 @@ __device__ inline void cell_geom(const Grid& g, const double* phi, const uint8_t
 // aperture of the face and the four tetrahedron fractions between the face and
 // the cell centre, each evaluated exactly as cell_geom<3> evaluates them (so
 // that a caller summing them in cell_geom<3>'s order gets the same bits)
-__device__ inline void face_geom3(const Grid& g, const double* phi, const uint8_t* chi, long long c, int m, int f,
+__device__ __forceinline__ void face_geom3(const Grid& g, const double* phi, const uint8_t* chi, long long c, int m, int f,
                                   double& ap, double (&t)[4]) {
   int q[3];
   coords(g, c, q);
@@ -389,8 +432,8 @@ __device__ inline void face_geom3(const Grid& g, const double* phi, const uint8_
 #pragma unroll
   for (int e = 0; e < 4; e++) {
     const double p0 = p[e], p1 = p[(e + 1) & 3];
-    ap += frac_tri(fc, p0, p1);
-    t[e] = frac_tet(vc, fc, p0, p1);
+    ap += frac_tri_nb(fc, p0, p1);
+    t[e] = frac_tet_nb(vc, fc, p0, p1);
   }
   ap = ap * 0.25;
 }

@@ -987,8 +987,58 @@ struct FluxSmem {
   static constexpr int NFY = D >= 2 ? TX * (TY + 1) * TZ : 0;
   static constexpr int NFZ = D >= 3 ? TX * TY * (TZ + 1) : 0;
   static constexpr int NF = NFX + NFY + NFZ;
+  // Staged stencil slots. The face stencils read the tile and its axis-aligned
+  // halos only; in 3D those are stored compactly (interior, then the x, y and z
+  // halo slabs: 1024 slots instead of the 1960 of the bounding box, so three
+  // CTAs fit on an SM instead of two); in 1D and 2D the box layout is kept.
+  static constexpr bool COMPACT = D == 3;
+  static constexpr int B1 = TX * TY * TZ, B2 = B1 + 6 * TY * TZ, B3 = B2 + 6 * TX * TZ;
+  static constexpr int NU = COMPACT ? B3 + 6 * TX * TY : NS;
   static constexpr size_t bytes =
-      sizeof(T) * ((size_t)NS * (NV + NP) + (size_t)NF * NV) + sizeof(double) * NF + (size_t)NS;
+      sizeof(T) * ((size_t)NU * (NV + NP) + (size_t)NF * NV) + sizeof(double) * NF + (size_t)NU;
+  // slot of the stencil cell at tile-local (lx, ly, lz), at most one
+  // coordinate outside the tile
+  __device__ static __forceinline__ int slot(int lx, int ly, int lz) {
+    if constexpr (!COMPACT) {
+      return (lx + 3) + SX * ((ly + HY) + SY * (lz + HZ));
+    } else {
+      if (lx < 0) return B1 + (lx + 3) + 6 * (ly + TY * lz);
+      if (lx >= TX) return B1 + (lx - TX + 3) + 6 * (ly + TY * lz);
+      if (ly < 0) return B2 + lx + TX * ((ly + 3) + 6 * lz);
+      if (ly >= TY) return B2 + lx + TX * ((ly - TY + 3) + 6 * lz);
+      if (lz < 0) return B3 + lx + TX * (ly + TY * (lz + 3));
+      if (lz >= TZ) return B3 + lx + TX * (ly + TY * (lz - TZ + 3));
+      return lx + TX * (ly + TY * lz);
+    }
+  }
+  // tile-local coordinates of slot s; false for a box-layout slot that no
+  // stencil reads (two or more coordinates outside the tile)
+  __device__ static __forceinline__ bool coords(int s, int& lx, int& ly, int& lz) {
+    if constexpr (!COMPACT) {
+      const int sx = s % SX, sy = (s / SX) % SY, sz = s / (SX * SY);
+      lx = sx - 3;
+      ly = sy - HY;
+      lz = sz - HZ;
+      int outs = (sx < 3 || sx >= 3 + TX);
+      if (D >= 2) outs += (sy < HY || sy >= HY + TY);
+      if (D >= 3) outs += (sz < HZ || sz >= HZ + TZ);
+      return outs <= 1;
+    } else {
+      if (s < B1) {
+        lx = s % TX; ly = (s / TX) % TY; lz = s / (TX * TY);
+      } else if (s < B2) {
+        const int t = s - B1, h = t % 6;
+        lx = h < 3 ? h - 3 : TX + h - 3; ly = (t / 6) % TY; lz = t / (6 * TY);
+      } else if (s < B3) {
+        const int t = s - B2, h = (t / TX) % 6;
+        lx = t % TX; ly = h < 3 ? h - 3 : TY + h - 3; lz = t / (TX * 6);
+      } else {
+        const int t = s - B3, h = t / (TX * TY);
+        lx = t % TX; ly = (t / TX) % TY; lz = h < 3 ? h - 3 : TZ + h - 3;
+      }
+      return true;
+    }
+  }
 };
 
 // Tait's pressure of a stencil state, out of line: the stiffened-gas path of
@@ -1139,14 +1189,14 @@ __device__ __forceinline__ void pp_limit(const T* uL, const T* uR, T unL, T unR,
 }
 
 template <int D, typename T>
-__device__ inline void face_flux_smem(const T* U, const T* P, int s0, int sstride, int d, int NS, T eps,
+__device__ inline void face_flux_smem(const T* U, const T* P, const int (&sl)[6], int d, int NS, T eps,
                                       const PosArgs& pa, const double* rh, T* Fh) {
   // U[v*NS + s], P[e*NS + s] with e: 0..D-1 velocities, D pressure, D+1 sound speed
   constexpr int NV = D + 2;
   T u[6][NV], un[6], pr[6], cs[6];
 #pragma unroll
   for (int q = 0; q < 6; q++) {
-    const int s = s0 + (q - 2) * sstride;
+    const int s = sl[q];
 #pragma unroll
     for (int v = 0; v < NV; v++) u[q][v] = U[v * NS + s];
     un[q] = P[d * NS + s];
@@ -1164,7 +1214,7 @@ __device__ inline void flux_face(const Grid& g, const Bufs& b, const T* U, const
                                  const uint8_t* bad, const BndBase& bb, int f, int r, int x0, int y0, int z0, int m,
                                  bool anyband, T eps, const PosArgs& pa, unsigned& err) {
   using S = FluxSmem<D, T>;
-  constexpr int NV = D + 2, TX = S::TX, TY = S::TY, SX = S::SX, SY = S::SY, NS = S::NS;
+  constexpr int NV = D + 2, TX = S::TX, TY = S::TY, NS = S::NU;
   int fx, fy, fz;
   if (DIR == 0) {
     fx = r % (TX + 1); fy = (r / (TX + 1)) % TY; fz = r / ((TX + 1) * TY);
@@ -1193,20 +1243,23 @@ __device__ inline void flux_face(const Grid& g, const Bufs& b, const T* U, const
         const bool lin = qd - 1 >= g.off[DIR], rin = qd < g.off[DIR] + g.n[DIR];
         if ((lin && !((b.smask[cL] >> m) & 1u)) || (rin && !((b.smask[cR] >> m) & 1u))) err |= ERR_BAND;
       }
-      const int sR = (fx + 3) + SX * ((fy + S::HY) + SY * (fz + S::HZ));
-      constexpr int sstride = DIR == 0 ? 1 : (DIR == 1 ? SX : SX * SY);
-      const int sL = sR - sstride;
+      // the six stencil cells: tile-local coordinate along DIR from -3 to +2
+      // of the face's upper cell
+      int sl[6];
+#pragma unroll
+      for (int q = 0; q < 6; q++)
+        sl[q] = DIR == 0 ? S::slot(fx - 3 + q, fy, fz) : (DIR == 1 ? S::slot(fx, fy - 3 + q, fz) : S::slot(fx, fy, fz - 3 + q));
       bool avail = true, isbad = false;
 #pragma unroll
       for (int q = 0; q < 6; q++) {
-        if (isnan(U[sL + (q - 2) * sstride])) avail = false;
-        if (bad[sL + (q - 2) * sstride]) isbad = true;
+        if (isnan(U[sl[q]])) avail = false;
+        if (bad[sl[q]]) isbad = true;
       }
       if (!avail) {
         err |= ERR_BAND;
       } else {
         if (isbad) err |= ERR_NEGATIVE;
-        face_flux_smem<D, T>(U, P, sL, sstride, DIR, NS, eps, pa, g.rh, Fh);
+        face_flux_smem<D, T>(U, P, sl, DIR, NS, eps, pa, g.rh, Fh);
       }
     }
     // boundary ledger: net inflow through the domain boundary
@@ -1245,15 +1298,12 @@ __device__ inline bool same_bits(double a, double b) {
 template <int D, typename T>
 __device__ __noinline__ bool stencil_uniform(const T* U, const uint8_t* bad, int tid) {
   using S = FluxSmem<D, T>;
-  constexpr int NV = D + 2, TX = S::TX, TY = S::TY, TZ = S::TZ, SX = S::SX, SY = S::SY, NS = S::NS;
-  const int sref = 3 + SX * (S::HY + SY * S::HZ);
+  constexpr int NV = D + 2, TX = S::TX, TY = S::TY, TZ = S::TZ, NS = S::NU;
+  const int sref = S::slot(0, 0, 0);
   bool same = !bad[sref];
   for (int s = tid; s < NS && same; s += TX * TY * TZ) {
-    const int sx = s % SX, sy = (s / SX) % SY, sz = s / (SX * SY);
-    int outs = (sx < 3 || sx >= 3 + TX);
-    if (D >= 2) outs += (sy < S::HY || sy >= S::HY + TY);
-    if (D >= 3) outs += (sz < S::HZ || sz >= S::HZ + TZ);
-    if (outs > 1) continue;
+    int lx, ly, lz;
+    if (!S::coords(s, lx, ly, lz)) continue;
     for (int v = 0; v < NV; v++) same = same && same_bits(U[v * NS + s], U[v * NS + sref]);
   }
   return same;
@@ -1275,7 +1325,7 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
                                           double* Qout, double beta, double omb, const BndBase& bb, int tile,
                                           const float* Qsf, float* Qof) {
   using S = FluxSmem<D, T>;
-  constexpr int NV = D + 2, TX = S::TX, TY = S::TY, TZ = S::TZ, SX = S::SX, SY = S::SY, NS = S::NS;
+  constexpr int NV = D + 2, TX = S::TX, TY = S::TY, TZ = S::TZ, NS = S::NU;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* A = (double*)smem_raw;       // [NF] apertures (8-byte aligned first)
   T* U = (T*)(A + S::NF);              // [NV][NS]
@@ -1337,7 +1387,7 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
   const bool cand = !anyband && interior_tile && g.geom == 0;
   const bool fast_sum = !anyband && g.geom == 0 && (D < 2 || g.rh[1] == g.rh[0]) && (D < 3 || g.rh[2] == g.rh[0]);
   const bool defer = cand && sizeof(T) == 8;
-  const int sref = 3 + SX * (S::HY + SY * S::HZ);
+  const int sref = S::slot(0, 0, 0);
   for (int m = 0; m < g.N; m++) {
     if (!((uni >> m) & 1u)) continue;
     const T mgm1 = T(g.gm1[m]), mgpi = T(g.gpi[m]), mgam = T(g.gamma[m]), mpinf = T(g.pinf[m]);
@@ -1352,16 +1402,12 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
     // stage the stencil state and its primitive quantities
 #pragma unroll 1
     for (int s = tid; s < NS; s += blockDim.x) {
-      const int sx = s % SX, sy = (s / SX) % SY, sz = s / (SX * SY);
-      const int gx = x0 - 3 + sx, gy = y0 - S::HY + sy, gz = z0 - S::HZ + sz;
-      T u[NV];
-      bool ok = gx >= 0 && gx < g.pn[0] && gy >= 0 && gy < g.pn[1] && gz >= 0 && gz < g.pn[2];
+      int lx, ly, lz;
       // only the axis-aligned halo of the tile is read by face stencils
-      int outs = 0;
-      outs += (sx < 3 || sx >= 3 + TX);
-      if (D >= 2) outs += (sy < S::HY || sy >= S::HY + TY);
-      if (D >= 3) outs += (sz < S::HZ || sz >= S::HZ + TZ);
-      ok = ok && outs <= 1;
+      const bool used = S::coords(s, lx, ly, lz);
+      const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+      T u[NV];
+      const bool ok = used && gx >= 0 && gx < g.pn[0] && gy >= 0 && gy < g.pn[1] && gz >= 0 && gz < g.pn[2];
       if (ok) {
         const long long gc = cell_at(g, gx, gy, gz);
         bool inner = gx >= g.off[0] && gx < g.off[0] + g.n[0];
@@ -1460,7 +1506,7 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
         rlo = face_r(g, cx);
         rhi = face_r(g, cx + 1);
         rvc = 1.0 / (rc * g.h[0]);
-        if (a > 0.0) psrc = (double)P[D * NS + (tx + 3) + SX * ((ty + S::HY) + SY * (tz + S::HZ))] * a / rc;
+        if (a > 0.0) psrc = (double)P[D * NS + S::slot(tx, ty, tz)] * a / rc;
       }
 #pragma unroll
       for (int v = 0; v < NV; v++) {
@@ -1523,7 +1569,7 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
 // of leaving a partial last wave; each tile's arithmetic does not depend on
 // which CTA runs it.
 template <int D, typename T>
-__global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z, sizeof(T) == 4 ? 4 : 1)
+__global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z, sizeof(T) == 4 ? (D == 3 ? 3 : 4) : 1)
     k_flux_update(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs,
                   const double* Qn, double* Qout, double beta, double omb, const __grid_constant__ BndBase bb,
                   int ntiles, const float* Qsf, float* Qof) {
