@@ -325,8 +325,7 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
       const long long nc = g.ncell, N = n_mat, NV = g.NV, nbmax = g.n_interior;
       Bufs& b = in.b;
       for (int k = 0; k < 3; k++) b.Q[k] = (double*)carve(8 * N * NV * nc);
-      b.Qf[0] = nullptr;
-      for (int k = 1; k < 3; k++) b.Qf[k] = ts == 4 ? (float*)carve(4 * N * NV * nc) : nullptr;
+      for (int k = 0; k < 3; k++) b.Qf[k] = ts == 4 ? (float*)carve(4 * N * NV * nc) : nullptr;
       b.phi = (double*)carve(8 * nc);
       b.phin = (double*)carve(8 * nc);
       b.chi = (uint8_t*)carve(nc);
@@ -363,6 +362,7 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
       b.mixin = (unsigned*)carve(4 * nbmax * N);
       b.mixT = (double*)carve(8 * nbmax * N);
       b.mixlist = (int*)carve(4 * nbmax * N);
+      b.geomlist = (int*)carve(4 * nbmax * N);
       b.mixtouch = (uint8_t*)carve(nbmax);
       b.phir = (double*)carve(8 * nbmax * N);
       b.bflux = (double*)carve(8 * std::max<long long>(1, in.nbnd) * N * NV);
@@ -460,6 +460,8 @@ static long long count_launches(const msf_ctx* c) {
     // bc_phichi, geometry (2), mixing (4)
     const long long per_stage = 1 + ext + 1 + 1 + 1 + vel + 1 + 2 + 2 + 1 + 2 + 4;
     n += 1 + 1 + (2 + g.D) + 2 + 1 + g.rk * per_stage + 2 + 1;
+    if (g.D == 3) n += 1 + g.rk;  // the cut-item pass of every geometry launch
+    if (in.b.Qf[0]) n += 1;
     if (g.fs_mat >= 0) n += 1 + g.rk;
     if (g.scale_sep) n += 2 + 1;
     if (g.reinit) n += re + 1;
@@ -561,10 +563,11 @@ static msf_status enqueue_step(msf_ctx* c, char* tape = nullptr) {
       }
       const bool prof = c->ev[0] && &in == &c->inst[0];
       if (prof) cudaEventRecord(c->ev[2 * st], s);
-      // FP32-bulk form: stages 1 and 2 stage their bulk states from the FP32
-      // copy the update of the stage before wrote
-      const float* Qsf = st >= 1 ? b.Qf[st] : nullptr;
-      float* Qof = st < g.rk - 1 ? b.Qf[st + 1] : nullptr;
+      // FP32-bulk form: every stage stages its bulk states from the FP32 copy
+      // of its state (Q^n rounded at the end of the step before, Q^(s) written
+      // by the update of the stage before) and writes the copy of its output
+      const float* Qsf = b.Qf[st];
+      float* Qof = b.Qf[(st + 1) % g.rk];
       cudaError_t fe = c->ops->flux(g, b, Qs, b.Q[0], Qo, beta, 1.0 - beta, in.bb, Qsf, Qof, s);
       if (fe != cudaSuccess) return fail(c, MSF_ECUDA, std::string("flux launch: ") + cudaGetErrorString(fe));
       if (prof) cudaEventRecord(c->ev[2 * st + 1], s);
@@ -585,6 +588,8 @@ static msf_status enqueue_step(msf_ctx* c, char* tape = nullptr) {
       for (int k = 0; k < g.reinit_iters; k++) launch_reinit(g, b, nb, s);
       launch_bc_phichi(g, b, s);
     }
+    // the band cells' states changed after the last update wrote their FP32 copy
+    c->ops->qf_copy(g, b, 1, nb, s);
   }
   // kernels enqueued above (keep in step with the sequence)
   c->launches = count_launches(c);
@@ -774,6 +779,7 @@ extern "C" msf_status msf_set_levelset(msf_ctx* c, int32_t i, const double* phi,
   cudaMemsetAsync(b.Q[1], 0, sizeof(double) * N * NV * g.ncell, s);
   launch_init_state(g, b, (const double*)dprim, s);
   if (g.fs_mat >= 0) launch_hold_ambient(g, b, b.Q[0], -2, s);
+  c->ops->qf_copy(g, b, 0, 0, s);
   Ctl h{};
   h.t_end = INFINITY;
   CUDA_TRY(c, cudaMemcpyAsync(b.ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
@@ -837,6 +843,7 @@ extern "C" msf_status msf_set_state(msf_ctx* c, int32_t i, const double* Q, cons
   launch_scatter_state(g, in.b, (const double*)dQ, (const double*)dphi, (const int32_t*)dchi, s);
   if ((st = finish_geometry(c, in)) != MSF_OK) return st;
   launch_geometry(g, in.b, in.b.Q[0], nullptr, in.nblk_band, s);
+  c->ops->qf_copy(g, in.b, 0, 0, s);
   // keep the ledger and counters, set t, clear the error
   k_ctl_restart<<<1, 1, 0, s>>>(in.b.ctl, t);
   cudaError_t e = cudaStreamSynchronize(s);
@@ -1090,6 +1097,7 @@ extern "C" msf_status msf_replay_step(msf_ctx* c, const void* tape) {
   if ((st = ensure_adjoint(c)) != MSF_OK) return st;
   enqueue_replay(c, (const char*)tape, false);
   k_replay_end<<<1, 1, 0, c->stream>>>(c->inst[0].b.ctl, (const double*)tape);
+  c->ops->qf_copy(c->inst[0].g, c->inst[0].b, 0, 0, c->stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(c, MSF_ECUDA, std::string("replay launch: ") + cudaGetErrorString(e));
   return read_error(c);
@@ -1105,6 +1113,7 @@ extern "C" msf_status msf_set_conserved(msf_ctx* c, int32_t i, const double* Q, 
   void* dQ = nullptr;
   if ((st = stage_in(c, Q, sizeof(double) * g.n_interior * g.N * g.NV, mem, &dQ)) != MSF_OK) return st;
   launch_adj_io(g, AdjBufs{}, (const double*)dQ, in.b.Q[0], 2, c->stream);
+  c->ops->qf_copy(g, in.b, 0, 0, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   cudaFree(dQ);
   if (e != cudaSuccess) return fail(c, MSF_ECUDA, std::string("set_conserved: ") + cudaGetErrorString(e));
@@ -1187,6 +1196,7 @@ extern "C" msf_status msf_adjoint_step(msf_ctx* c, const void* tape_, const doub
   launch_masks(g, b, s);
   launch_geometry(g, b, b.Q[0], nullptr, nb, s);
   launch_adj_end(b, (const double*)tape, s);
+  c->ops->qf_copy(g, b, 0, 0, s);
   CUDA_TRY(c, cudaMemcpyAsync(c->h_pin, a.deos, sizeof(double) * 2 * MAXM, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(c, cudaMemcpyAsync(c->h_pin + 2 * MAXM, a.dinf, sizeof(double) * 30, cudaMemcpyDeviceToHost, s));
   cudaError_t e = cudaGetLastError();

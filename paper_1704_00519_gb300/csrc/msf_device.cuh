@@ -59,6 +59,7 @@ struct Ctl {
   int nband, nbnd;
   unsigned tile_ctr;  // next flux tile of the running flux-update launch
   unsigned mix_count; // (band cell, material) items of the running mixing pass that mix
+  unsigned geom_count;  // 3D cut items listed by the running geometry pass
   unsigned long long cnt[NCOUNT];
   double ledger[MAXM][5];
 };
@@ -283,23 +284,51 @@ __device__ inline double frac_tet(double a, double b, double c, double d) {
   return num / den;
 }
 
-// The same fractions without divergent branches, for warps whose lanes take
-// different cases: the values are sorted by a network of exact compare and
-// exchange steps (equal values can only be +0 and -0 in another order, which
-// no formula below distinguishes), every case's numerator and denominator is
-// formed with the expressions above, and one division follows the selection,
-// so the results are those of frac_tri and frac_tet bit for bit.
-__device__ __forceinline__ void cx_desc(double& a, double& b) {
-  const double hi = b > a ? b : a, lo = b > a ? a : b;
+// strict sign tests on the bit pattern (integer compares, so that they leave
+// the FP64 pipes free): 0 < x <= +inf, and -inf <= x < 0; a zero of either
+// sign and a NaN fail both
+__device__ __forceinline__ bool pos_bits(double x) {
+  const long long u = __double_as_longlong(x);
+  return u > 0 && u <= 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool neg_bits(double x) {
+  const long long u = __double_as_longlong(x);
+  return u > (long long)0x8000000000000000ULL && u <= (long long)0xfff0000000000000ULL;
+}
+
+// order key of a double: signed integers that compare as the values do (the
+// magnitude bits of a negative value reversed), except that -0 sorts below +0
+__device__ __forceinline__ long long okey(double x) {
+  const long long u = __double_as_longlong(x);
+  return u >= 0 ? u : (u ^ 0x7fffffffffffffffLL);
+}
+
+// The same fractions without divergent branches and without FP64 compares,
+// for warps whose lanes take different cases: the values are sorted by a
+// network of compare and exchange steps on their order keys, the signs are
+// counted with the bit tests, every case's numerator and denominator is
+// formed with the expressions above, and one division follows the selection.
+// For values that are not NaN the results are those of frac_tri and frac_tet
+// bit for bit: equal keys are equal values, and the only equal values that
+// the keys order differently are a +0 and a -0, which no formula
+// distinguishes (they enter only as differences a - 0 and as the one zero of
+// a case with a single zero).
+__device__ __forceinline__ void cx_desc(double& a, long long& ka, double& b, long long& kb) {
+  const bool sw = kb > ka;
+  const double hi = sw ? b : a, lo = sw ? a : b;
+  const long long khi = sw ? kb : ka, klo = sw ? ka : kb;
   a = hi;
   b = lo;
+  ka = khi;
+  kb = klo;
 }
 __device__ __forceinline__ double frac_tri_nb(double a, double b, double c) {
-  cx_desc(a, b);
-  cx_desc(b, c);
-  cx_desc(a, b);
-  const int np = (a > 0.0) + (b > 0.0) + (c > 0.0);
-  const int nn = (a < 0.0) + (b < 0.0) + (c < 0.0);
+  long long ka = okey(a), kb = okey(b), kc = okey(c);
+  cx_desc(a, ka, b, kb);
+  cx_desc(b, kb, c, kc);
+  cx_desc(a, ka, b, kb);
+  const int np = pos_bits(a) + pos_bits(b) + pos_bits(c);
+  const int nn = neg_bits(a) + neg_bits(b) + neg_bits(c);
   const double n1 = a * a, d1 = (a - b) * (a - c);  // np == 1
   const double n2 = c * c, d2 = (a - c) * (b - c);  // np == 2
   const double q = (np == 1 ? n1 : n2) / (np == 1 ? d1 : d2);
@@ -308,13 +337,14 @@ __device__ __forceinline__ double frac_tri_nb(double a, double b, double c) {
   return np == 1 ? q : 1.0 - q;
 }
 __device__ __forceinline__ double frac_tet_nb(double a, double b, double c, double d) {
-  cx_desc(a, b);
-  cx_desc(c, d);
-  cx_desc(a, c);
-  cx_desc(b, d);
-  cx_desc(b, c);
-  const int np = (a > 0.0) + (b > 0.0) + (c > 0.0) + (d > 0.0);
-  const int nn = (a < 0.0) + (b < 0.0) + (c < 0.0) + (d < 0.0);
+  long long ka = okey(a), kb = okey(b), kc = okey(c), kd = okey(d);
+  cx_desc(a, ka, b, kb);
+  cx_desc(c, kc, d, kd);
+  cx_desc(a, ka, c, kc);
+  cx_desc(b, kb, d, kd);
+  cx_desc(b, kb, c, kc);
+  const int np = pos_bits(a) + pos_bits(b) + pos_bits(c) + pos_bits(d);
+  const int nn = neg_bits(a) + neg_bits(b) + neg_bits(c) + neg_bits(d);
   const double n1 = a * a * a, d1 = ((a - b) * (a - c)) * (a - d);  // np == 1
   const double m3 = -d;
   const double n3 = m3 * m3 * m3, d3 = ((a - d) * (b - d)) * (c - d);  // np == 3
@@ -436,6 +466,74 @@ __device__ __forceinline__ void face_geom3(const Grid& g, const double* phi, con
     t[e] = frac_tet_nb(vc, fc, p0, p1);
   }
   ap = ap * 0.25;
+}
+
+// Conversions between binary32 and binary64 on the integer pipes, from the
+// IEEE-754 layouts (sign, biased exponent, fraction); bit for bit the
+// hardware conversions, which run on the FP64 pipes. Values outside the range
+// handled here (subnormals, infinities, NaNs, and for the narrowing the
+// binary32 subnormal and overflow range) take the hardware conversion.
+//
+// float -> double, exact: the exponent is rebiased (127 -> 1023) and the 23
+// fraction bits become the leading 23 of 52.
+__device__ __forceinline__ double f2d_bits(float x) {
+  const unsigned u = __float_as_uint(x), mag = u & 0x7fffffffu;
+  const unsigned e = mag >> 23;
+  if (mag == 0u) return __hiloint2double((int)u, 0);  // +-0
+  if (e == 0u || e == 0xffu) return (double)x;
+  const unsigned hi = (u & 0x80000000u) | ((mag >> 3) + ((1023u - 127u) << 20));
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+// double -> float, rounded to nearest even: the leading 23 of the 52 fraction
+// bits are kept and the 29 dropped bits decide the rounding (a carry out of
+// the fraction raises the exponent; out of the largest binade it gives
+// infinity, as the rounding rule does).
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned mag = hi & 0x7fffffffu, E = mag >> 20;
+  if ((mag | lo) == 0u) return __uint_as_float(hi);  // +-0
+  if (E < 1023u - 126u || E > 1023u + 127u) return (float)x;
+  unsigned r = (hi & 0x80000000u) | ((mag - ((1023u - 127u) << 20)) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu, half = 0x10000000u;
+  r += (rem > half || (rem == half && (r & 1u))) ? 1u : 0u;
+  return __uint_as_float(r);
+}
+// finite (neither infinite nor NaN): the exponent field is not all ones
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (((unsigned)__double2hiint(x) >> 20) & 0x7ffu) != 0x7ffu;
+}
+
+// Uncut cell: the sign that phi^m takes at every simplex vertex of cell c
+// (centre, corners and, in 3D, face centres; the values cell_geom computes,
+// from the same functions): +1 when all are > 0, -1 when all are < 0, 0
+// otherwise. For +1 every segment, triangle and tetrahedron fraction of the
+// cell is exactly 1, for -1 exactly 0, so cell_geom's sums are constants.
+template <int D>
+__device__ __forceinline__ int uncut_sign(const Grid& g, const double* phi, const uint8_t* chi, long long c, int m) {
+  int q[3];
+  coords(g, c, q);
+  const double vc = phi_m(phi, chi, c, m);
+  bool pos = pos_bits(vc), neg = neg_bits(vc);
+  if constexpr (D == 3) {
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+      const double v = facec_val(g, phi, chi, c, f >> 1, f & 1, m);
+      pos = pos && pos_bits(v);
+      neg = neg && neg_bits(v);
+    }
+  }
+  const int nz = D >= 3 ? 2 : 1;
+#pragma unroll
+  for (int a = 0; a < nz; a++)
+#pragma unroll
+    for (int b = 0; b < 2; b++)
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        const double v = vertex_val(g, phi, chi, q[0] + e, q[1] + b, q[2] + a, m);
+        pos = pos && pos_bits(v);
+        neg = neg && neg_bits(v);
+      }
+  return pos ? 1 : (neg ? -1 : 0);
 }
 
 // min / max of phi^m over the simplex vertices of cell c (centre, corners, 3D face centres)

@@ -207,7 +207,16 @@ __device__ __forceinline__ void phase_geom_mat_d(const Grid& g, const Bufs& b, i
         for (int d = 0; d < D; d++) alo[d] = ahi[d] = 1.0;
       }
     } else if ((bits >> m) & 1u) {
-      cell_geom<DD>(g, b.phi, b.chi, c, m, &a, alo, ahi);
+      // an uncut item: every fraction of cell_geom is 1 (all vertex values
+      // > 0) or 0 (all < 0)
+      int un = 0;
+      if constexpr (DD >= 2) un = uncut_sign<DD>(g, b.phi, b.chi, c, m);
+      if (un > 0) {
+        a = 1.0;
+        for (int d = 0; d < D; d++) alo[d] = ahi[d] = 1.0;
+      } else if (un == 0) {
+        cell_geom<DD>(g, b.phi, b.chi, c, m, &a, alo, ahi);
+      }
     }
     b.alpha[midx(g, m, c)] = a;
     for (int d = 0; d < D; d++) {
@@ -216,26 +225,26 @@ __device__ __forceinline__ void phase_geom_mat_d(const Grid& g, const Bufs& b, i
     }
   }
 }
-// 3D: the same per-item results, with the simplex geometry of the items whose
-// 3^d block holds two or more materials (a fifth of the band, each a long FP64
-// chain of 24 tetrahedra) spread over the warp: the lanes holding such items
-// are gathered by a ballot and taken five at a time, six lanes per item (one
-// per face); the owning lane then sums the 24 tetrahedron fractions in
-// cell_geom<3>'s order. first_ and stride_ must be warp-aligned (lane l of a
-// warp starts at a multiple of 32 plus l, stride a multiple of 32).
+// 3D, first pass: per (band cell, material) item the normal, the fractions of
+// the items that need no simplex geometry (a 3^d block of one material, or an
+// uncut item whose vertex values all have one sign: constant fractions, 24
+// unit tetrahedra times 1/24 and faces of four unit triangles times 1/4), and
+// a list of the cut items for k_geom_cut (a tenth of the band or less, each a
+// long FP64 chain of 24 tetrahedra), appended warp by warp; the order of the
+// list does not matter, each item's results depend on the item alone.
+// first_ and stride_ must be warp-aligned (lane l of a warp starts at a
+// multiple of 32 plus l, stride a multiple of 32).
 __device__ __forceinline__ void phase_geom_mat3(const Grid& g, const Bufs& b, int first_, int stride_) {
-  const int nb = b.ctl->nband, N = g.N;
-  const int total = nb * N;
+  const int nb = b.ctl->nband;
+  const int total = nb * g.N;
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
   for (int base = first_ - lane; base < total; base += stride_) {
     const int it = base + lane;
-    int m = 0;
-    long long c = 0;
-    bool heavy = false;
+    bool cut = false;
     if (it < total) {
-      m = it / nb;
-      c = b.band[it - m * nb];
+      const int m = it / nb;
+      const long long c = b.band[it - m * nb];
       int q[3];
       coords(g, c, q);
       const unsigned bits = block_bits(g, b.chi, q);
@@ -244,9 +253,12 @@ __device__ __forceinline__ void phase_geom_mat3(const Grid& g, const Bufs& b, in
         normal_m(g, b.phi, b.chi, c, m, n);
         for (int d = 0; d < 3; d++) b.nrm[((long long)m * 3 + d) * g.ncell + c] = n[d];
       }
-      heavy = popcount8(bits) >= 2 && ((bits >> m) & 1u);
-      if (!heavy) {
-        const double a = (popcount8(bits) < 2 && b.chi[c] == m) ? 1.0 : 0.0;
+      const bool heavy = popcount8(bits) >= 2 && ((bits >> m) & 1u);
+      const int un = heavy ? uncut_sign<3>(g, b.phi, b.chi, c, m) : 0;
+      cut = heavy && un == 0;
+      if (!cut) {
+        const double a = un != 0 ? (un > 0 ? 24.0 * (1.0 / 24.0) : 0.0)
+                                 : ((popcount8(bits) < 2 && b.chi[c] == m) ? 1.0 : 0.0);
         b.alpha[midx(g, m, c)] = a;
         for (int d = 0; d < 3; d++) {
           b.Alo[aidx(g, d, m, c)] = a;
@@ -254,37 +266,54 @@ __device__ __forceinline__ void phase_geom_mat3(const Grid& g, const Bufs& b, in
         }
       }
     }
-    unsigned pend = __ballot_sync(FULL, heavy);
-    while (pend) {
-      // slot s of this round: the s-th pending lane; lanes 30 and 31 idle
-      const int slot = lane / 6, f = lane - 6 * slot;
-      unsigned mm = pend;
-      for (int s2 = 0; s2 < slot; s2++) mm &= mm - 1;
-      const int src = (slot < 5 && mm) ? __ffs(mm) - 1 : -1;
-      const long long ci = __shfl_sync(FULL, c, src < 0 ? 0 : src);
-      const int mi = __shfl_sync(FULL, m, src < 0 ? 0 : src);
-      double ap = 0.0, t[4] = {0.0, 0.0, 0.0, 0.0};
-      if (src >= 0) face_geom3(g, b.phi, b.chi, ci, mi, f, ap, t);
-      const bool mine = (pend >> lane) & 1u;
-      const int my_slot = __popc(pend & ((1u << lane) - 1u));
-      const bool owner = mine && my_slot < 5;
-      const int from = (owner ? my_slot : 0) * 6;
-      double vol = 0.0, apv[6];
+    const unsigned bal = __ballot_sync(FULL, cut);
+    if (bal) {
+      const int leader = __ffs(bal) - 1;
+      int at = 0;
+      if (lane == leader) at = (int)atomicAdd(&b.ctl->geom_count, (unsigned)__popc(bal));
+      at = __shfl_sync(FULL, at, leader);
+      if (cut) b.geomlist[at + __popc(bal & ((1u << lane) - 1u))] = it;
+    }
+  }
+}
+// 3D, second pass: the listed cut items, five per warp round, six lanes per
+// item (one per face, face_geom3); the item's first lane then sums the 24
+// tetrahedron fractions in cell_geom<3>'s order (faces in order, the four
+// tetrahedra of each face in order), so the results are cell_geom<3>'s bits.
+__global__ void k_geom_cut(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+  if (!ctl_active(b)) return;
+  const int total = (int)b.ctl->geom_count, nb = b.ctl->nband;
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  const int slot = lane / 6, f = lane - 6 * slot;  // lanes 30 and 31 idle
+  const unsigned FULL = 0xffffffffu;
+  for (int r0 = 5 * warp; r0 < total; r0 += 5 * nwarps) {
+    const bool has = slot < 5 && r0 + slot < total;
+    int m = 0;
+    long long c = 0;
+    double ap = 0.0, t[4] = {0.0, 0.0, 0.0, 0.0};
+    if (has) {
+      const int it = b.geomlist[r0 + slot];
+      m = it / nb;
+      c = b.band[it - m * nb];
+      face_geom3(g, b.phi, b.chi, c, m, f, ap, t);
+    }
+    const int from = (slot < 5 ? slot : 0) * 6;
+    double vol = 0.0, apv[6];
 #pragma unroll
-      for (int ff = 0; ff < 6; ff++) {
-        apv[ff] = __shfl_sync(FULL, ap, from + ff);
+    for (int ff = 0; ff < 6; ff++) {
+      apv[ff] = __shfl_sync(FULL, ap, from + ff);
 #pragma unroll
-        for (int e = 0; e < 4; e++) vol += __shfl_sync(FULL, t[e], from + ff);
+      for (int e = 0; e < 4; e++) vol += __shfl_sync(FULL, t[e], from + ff);
+    }
+    if (has && f == 0) {
+      b.alpha[midx(g, m, c)] = vol * (1.0 / 24.0);
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        b.Alo[aidx(g, d, m, c)] = apv[2 * d];
+        b.Ahi[aidx(g, d, m, c)] = apv[2 * d + 1];
       }
-      if (owner) {
-        b.alpha[midx(g, m, c)] = vol * (1.0 / 24.0);
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-          b.Alo[aidx(g, d, m, c)] = apv[2 * d];
-          b.Ahi[aidx(g, d, m, c)] = apv[2 * d + 1];
-        }
-      }
-      for (int s2 = 0; s2 < 5 && pend; s2++) pend &= pend - 1;
     }
   }
 }
@@ -1238,7 +1267,7 @@ __device__ inline void flux_face(const Grid& g, const Bufs& b, const T* U, const
   if (exists) {
     const long long cR = cell_at(g, gx, gy, gz), cL = cR - g.st[DIR];
     Af = anyband ? face_aperture(g, b, cL, cR, DIR, m) : 1.0;
-    if (Af > 0.0 && m != g.fs_mat) {
+    if (pos_bits(Af) && m != g.fs_mat) {
       if (anyband) {
         const bool lin = qd - 1 >= g.off[DIR], rin = qd < g.off[DIR] + g.n[DIR];
         if ((lin && !((b.smask[cL] >> m) & 1u)) || (rin && !((b.smask[cR] >> m) & 1u))) err |= ERR_BAND;
@@ -1309,7 +1338,10 @@ __device__ __noinline__ bool stencil_uniform(const T* U, const uint8_t* bad, int
   return same;
 }
 
-// one tile of the flux update (tile index over the (x, y, z) tile grid)
+// a face flux widened to FP64 (exact; integer operations for FP32)
+__device__ __forceinline__ double to_d(float x) { return f2d_bits(x); }
+__device__ __forceinline__ double to_d(double x) { return x; }
+
 // exact error of a float sum: s + x = t + e exactly (Knuth's two-sum; no
 // multiplications, so no FMA contraction applies)
 __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
@@ -1320,6 +1352,7 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
   c += e;
 }
 
+// one tile of the flux update (tile index over the (x, y, z) tile grid)
 template <int D, typename T>
 __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const double* Qs, const double* Qn,
                                           double* Qout, double beta, double omb, const BndBase& bb, int tile,
@@ -1530,11 +1563,11 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
                 two_sum_acc(sh, sc, (float)F[v * S::NF + flo[d]]);
                 two_sum_acc(sh, sc, -(float)F[v * S::NF + fhi[d]]);
               }
-              L = ((double)sh + (double)sc) * g.rh[0];
+              L = (f2d_bits(sh) + f2d_bits(sc)) * g.rh[0];
             } else {
 #pragma unroll
               for (int d = 0; d < D; d++) {
-                const double fl = (double)F[v * S::NF + flo[d]], fh = (double)F[v * S::NF + fhi[d]];
+                const double fl = to_d(F[v * S::NF + flo[d]]), fh = to_d(F[v * S::NF + fhi[d]]);
                 L = L + (A[flo[d]] * fl - A[fhi[d]] * fh) * g.rh[d];
               }
             }
@@ -1551,9 +1584,9 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
           const double qn = Qn[qi];
           qv = beta * qn + omb * (qs + dt * L);
         }
-        if (!isfinite(qv)) err |= ERR_NONFINITE;
+        if (!finite_bits(qv)) err |= ERR_NONFINITE;
         Qout[qi] = qv;
-        if (sizeof(T) == 4 && Qof) Qof[qi] = (float)qv;
+        if (sizeof(T) == 4 && Qof) Qof[qi] = d2f_bits(qv);
       }
     }
     __syncthreads();
@@ -1561,6 +1594,30 @@ __device__ __forceinline__ void flux_tile(const Grid& g, const Bufs& b, const do
   if (err) atomicOr(&s_err, err);
   __syncthreads();
   if (tid == 0 && s_err) atomicOr(&b.ctl->err, s_err);
+}
+
+// FP32 copy Qf[0] of the state Q[0], read by the FP32-bulk flux update of
+// stage 0 for its bulk stencil states (the values it would otherwise convert
+// there). The last flux update of a step writes it for every value it
+// updates; this kernel refreshes the values of the step's band cells (all
+// materials and variables) after the band kernels that follow the update
+// (correction, mixing, scale separation) have changed them, and, with
+// band_only = 0, converts the whole state after a host-side write of Q[0].
+// So Qf[0] equals Q[0] rounded to FP32 at the start of every step.
+__global__ void k_qf_copy(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, int band_only) {
+  if (band_only && !ctl_active(b)) return;
+  const long long per = (long long)g.N * g.NV;
+  const long long nb = band_only ? (long long)b.ctl->nband : 0;
+  const long long total = band_only ? nb * per : g.ncell * per;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long q = i;
+    if (band_only) {
+      const long long mv = i / nb, k = i - mv * nb;
+      q = mv * g.ncell + b.band[k];
+    }
+    b.Qf[0][q] = d2f_bits(b.Q[0][q]);
+  }
 }
 
 // Persistent CTAs (as many as fit on the GPU at once) take tiles from a

@@ -19,9 +19,13 @@ struct Ops {
   void (*dt)(const Grid&, const Bufs&, const double* Qs, cudaStream_t);
   void (*interface)(const Grid&, const Bufs&, const double* Qs, int stage, int nblk, cudaStream_t);
   // Qsf: FP32 copy of Qs for the bulk staging (null: convert Qs); Qof: FP32
-  // copy of Qout to write (null: none); both null in FP64 contexts
+  // copy of Qout to write (null: none); both ignored in FP64 contexts
   cudaError_t (*flux)(const Grid&, const Bufs&, const double* Qs, const double* Qn, double* Qout, double beta,
                       double omb, const BndBase&, const float* Qsf, float* Qof, cudaStream_t);
+  // FP32-bulk form: Q[0] rounded into its FP32 copy Qf[0], for the band
+  // cells of the step (band_only = 1, at the end of a step) or for every cell
+  // (after a host-side write of Q[0]); nothing in FP64 contexts
+  void (*qf_copy)(const Grid&, const Bufs&, int band_only, int nblk, cudaStream_t);
   // n_steps steps of every 1D instance of a batch, one CTA of bs threads per instance
   cudaError_t (*batched)(const BatchEntry* tab, const int* order, int n_inst, int n_steps, int bs, cudaStream_t);
 };

@@ -38,6 +38,7 @@ struct Bufs {
   unsigned* mixin;          // [nbandmax][N] bit (offset code) of every neighbour that mixes into the cell
   double* mixT;             // [nbandmax][N] weight sum of the mixing pairs of the cell
   int* mixlist;             // [nbandmax * N] items (k * N + m) of the running mixing pass that mix
+  int* geomlist;            // [nbandmax * N] 3D cut items (m * nband + k) of the running geometry pass
   uint8_t* mixtouch;        // [nbandmax] 1: a material of band cell k mixes in this pass
   double* phir;             // [nbandmax][N] new local level-set values
   double* bflux;            // [nbnd][N][NV] boundary-face fluxes of the stage
