@@ -325,7 +325,9 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
       const long long nc = g.ncell, N = n_mat, NV = g.NV, nbmax = g.n_interior;
       Bufs& b = in.b;
       for (int k = 0; k < 3; k++) b.Q[k] = (double*)carve(8 * N * NV * nc);
-      for (int k = 0; k < 3; k++) b.Qf[k] = ts == 4 ? (float*)carve(4 * N * NV * nc) : nullptr;
+      // FP32 copies of the stage states (FP32-bulk grid contexts; the
+      // batched kernel stages its states itself)
+      for (int k = 0; k < 3; k++) b.Qf[k] = ts == 4 && !batched ? (float*)carve(4 * N * NV * nc) : nullptr;
       b.phi = (double*)carve(8 * nc);
       b.phin = (double*)carve(8 * nc);
       b.chi = (uint8_t*)carve(nc);
@@ -363,6 +365,7 @@ extern "C" msf_status msf_create(const msf_grid* grids, int32_t n_instances, int
       b.mixT = (double*)carve(8 * nbmax * N);
       b.mixlist = (int*)carve(4 * nbmax * N);
       b.geomlist = (int*)carve(4 * nbmax * N);
+      b.lslist = (int*)carve(4 * nbmax * N);
       b.mixtouch = (uint8_t*)carve(nbmax);
       b.phir = (double*)carve(8 * nbmax * N);
       b.bflux = (double*)carve(8 * std::max<long long>(1, in.nbnd) * N * NV);

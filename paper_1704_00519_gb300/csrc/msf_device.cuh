@@ -60,6 +60,7 @@ struct Ctl {
   unsigned tile_ctr;  // next flux tile of the running flux-update launch
   unsigned mix_count; // (band cell, material) items of the running mixing pass that mix
   unsigned geom_count;  // 3D cut items listed by the running geometry pass
+  unsigned ls_count;    // level-set items listed by the last geometry pass
   unsigned long long cnt[NCOUNT];
   double ledger[MAXM][5];
 };

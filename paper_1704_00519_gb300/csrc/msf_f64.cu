@@ -177,6 +177,7 @@ void launch_masks(const Grid& g, const Bufs& b, cudaStream_t s) {
 }
 void launch_geometry(const Grid& g, const Bufs& b, const double* Qs, const double* mass, int nblk, cudaStream_t s) {
   if (g.D == 3) cudaMemsetAsync(&b.ctl->geom_count, 0, sizeof(unsigned), s);
+  cudaMemsetAsync(&b.ctl->ls_count, 0, sizeof(unsigned), s);
   k_geom_mat<<<nblk, BAND_THREADS, 0, s>>>(g, b);
   if (g.D == 3) k_geom_cut<<<nblk, BAND_THREADS, 0, s>>>(g, b);
   k_geom_cell<<<nblk, BAND_THREADS, 0, s>>>(g, b, Qs, mass);

@@ -330,16 +330,44 @@ __global__ void k_geom_mat(const __grid_constant__ Grid g, const __grid_constant
 // per band cell: flags, partition of each face among the local materials and
 // the conservation correction (Sec. 2.3.1, Eq. vol_corr2).
 // Qs == nullptr and mass == nullptr: raw volume fractions (start-up)
+// With LIST the pass also lists the level-set items (region r, band cell k)
+// of the next level-set stage, one per region present in the cell's 3^d block
+// (k_levelset takes them from the list instead of striding over every pair);
+// first_ and stride_ must then be warp-aligned.
+template <bool LIST>
 __device__ __forceinline__ void phase_geom_cell(const Grid& g, const Bufs& b, const double* Qs, const double* mass, int first_, int stride_) {
     const int nb = b.ctl->nband;
   const int N = g.N, D = g.D;
   unsigned long long nmulti = 0, ncorr = 0;
-  for (int k = first_; k < nb; k += stride_) {
-    const long long c = b.band[k];
-    int q[3];
-    coords(g, c, q);
-    const unsigned bits = block_bits(g, b.chi, q);
-    b.xsS[c] = (uint8_t)bits;
+  const int lane = threadIdx.x & 31;
+  for (int base = first_ - (LIST ? lane : 0); base < nb; base += stride_) {
+    const int k = base + (LIST ? lane : 0);
+    long long c = 0;
+    unsigned bits = 0;
+    int q[3] = {0, 0, 0};
+    if (k < nb) {
+      c = b.band[k];
+      coords(g, c, q);
+      bits = block_bits(g, b.chi, q);
+      b.xsS[c] = (uint8_t)bits;
+    }
+    if (LIST) {
+      const unsigned FULL = 0xffffffffu;
+      const int cnt = popcount8(bits);
+      int incl = cnt;  // inclusive prefix sum of the warp's item counts
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int tot = __shfl_sync(FULL, incl, 31);
+      int at = 0;
+      if (lane == 31 && tot > 0) at = (int)atomicAdd(&b.ctl->ls_count, (unsigned)tot);
+      at = __shfl_sync(FULL, at, 31) + incl - cnt;
+      for (int r = 0; r < N; r++)
+        if ((bits >> r) & 1u) b.lslist[at++] = r * nb + k;
+    }
+    if (k >= nb) continue;
     if (popcount8(bits) < 2) {
       b.gflag[c] = 0;
       continue;
@@ -405,7 +433,7 @@ __device__ __forceinline__ void phase_geom_cell(const Grid& g, const Bufs& b, co
 }
 __global__ void k_geom_cell(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs, const double* mass) {
   if (!ctl_active(b)) return;
-  phase_geom_cell(g, b, Qs, mass, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  phase_geom_cell<true>(g, b, Qs, mass, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // stored unit normal of material m at a band cell (written by k_geom_mat)
@@ -727,20 +755,35 @@ __global__ void k_bc_uhat(const __grid_constant__ Grid g, const __grid_constant_
 template <typename T, int DD>
 __device__ __forceinline__ double dt_items_d(const Grid& g, const Bufs& b, const double* Qs, long long first,
                                            long long stride, unsigned& err) {
-  const int N = g.N, D = DD;
+  const int N = g.N, D = DD, NV = DD + 2;
   double lam = 0.0;
+  // the largest material bound is kept in T: widening to FP64 is exact and
+  // monotone, so the maximum of the widened values is the widened maximum
+  T lamT = T(0);
+  T rhT[3];
+#pragma unroll
+  for (int d = 0; d < D; d++) rhT[d] = (T)g.rh[d];
+  // FP32-bulk form: the bulk states of stage 0 from the FP32 copy of Q^n
+  // (the values interior_uhat<float> converts)
+  const float* Qf = sizeof(T) == 4 ? b.Qf[0] : nullptr;
   for (long long idx = first; idx < g.n_interior; idx += stride) {
     const long long c = interior_cell(g, idx);
     const bool inb = b.bandidx[c] >= 0;
     for (int m = 0; m < N; m++) {
       if ((inb ? !(b.alpha[midx(g, m, c)] > 0.0) : b.chi[c] != m) || m == g.fs_mat) continue;
       T u[5], w[5];
-      interior_uhat<T>(g, b, Qs, c, m, u);
+      if (Qf && !inb) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) u[v] = (T)Qf[qidx(g, m, v, c)];
+      } else {
+        interior_uhat<T>(g, b, Qs, c, m, u);
+      }
       cons_to_prim<T>(g, m, D, u, w);
       const T cs = sound<T>(g, m, w[0], w[D + 1], &err);
       T s = T(0);
-      for (int d = 0; d < D; d++) s += (fabs(w[1 + d]) + cs) * (T)g.rh[d];
-      if ((double)s > lam) lam = (double)s;
+#pragma unroll
+      for (int d = 0; d < D; d++) s += (fabs(w[1 + d]) + cs) * rhT[d];
+      if (s > lamT) lamT = s;
     }
     // a free surface moves at the u* of its wave curve, which the material
     // states do not bound: its cut cells enter the bound with |u*|
@@ -750,7 +793,7 @@ __device__ __forceinline__ double dt_items_d(const Grid& g, const Bufs& b, const
       if (s > lam) lam = s;
     }
   }
-  return lam;
+  return (double)lamT > lam ? (double)lamT : lam;
 }
 template <typename T>
 __device__ __forceinline__ double dt_items(const Grid& g, const Bufs& b, const double* Qs, long long first,
@@ -1682,15 +1725,20 @@ __global__ void k_ledger(const __grid_constant__ Grid g, const __grid_constant__
 // --------------------------------------------- level-set stage (a9) + R
 __device__ inline double phir_stage(const Bufs& b, long long c, int r) { return phi_m(b.phi, b.chi, c, r); }
 
-template <int DD>
+// With LIST the items are the (region, band cell) pairs the geometry pass
+// listed (those whose region is present in the cell's 3^d block), else every
+// pair, skipping the others. The upwind side is a selection of the stencil
+// differences, so lanes with opposite velocity signs share one WENO5 chain.
+template <int DD, bool LIST>
 __device__ __forceinline__ void phase_levelset_d(const Grid& g, const Bufs& b, const double* vel, double beta, double omb, int first_, int stride_) {
     const int nb = b.ctl->nband, N = g.N, D = DD;
   const double dt = b.ctl->dt, eps = g.weno_eps;
-  const int total = nb * N;
+  const int total = LIST ? (int)b.ctl->ls_count : nb * N;
   for (int it = first_; it < total; it += stride_) {
-    const int r = it / nb, k = it - r * nb;
+    const int code = LIST ? b.lslist[it] : it;
+    const int r = code / nb, k = code - r * nb;
     const long long c = b.band[k];
-    if (!((b.xsS[c] >> r) & 1u)) continue;
+    if (!LIST && !((b.xsS[c] >> r) & 1u)) continue;
     // the 7-point line of every axis, loaded up front (one round of latency)
     double pl[3][7], vdir[3];
     for (int d = 0; d < D; d++) {
@@ -1703,36 +1751,30 @@ __device__ __forceinline__ void phase_levelset_d(const Grid& g, const Bufs& b, c
       if (vd == 0.0) continue;
       const double rh = g.rh[d];
       const double* p = pl[d] + 3;  // p[i] = phi^r at c + i e_d
-      double gd;
-      if (vd > 0.0) {
-        double v1 = (p[-2] - p[-3]) * rh;
-        double v2 = (p[-1] - p[-2]) * rh;
-        double v3 = (p[0] - p[-1]) * rh;
-        double v4 = (p[1] - p[0]) * rh;
-        double v5 = (p[2] - p[1]) * rh;
-        gd = weno5<double>(v1, v2, v3, v4, v5, eps);
-      } else {
-        double v1 = (p[3] - p[2]) * rh;
-        double v2 = (p[2] - p[1]) * rh;
-        double v3 = (p[1] - p[0]) * rh;
-        double v4 = (p[0] - p[-1]) * rh;
-        double v5 = (p[-1] - p[-2]) * rh;
-        gd = weno5<double>(v1, v2, v3, v4, v5, eps);
-      }
+      // vd > 0: backward differences from c - 3 e_d; vd < 0: forward
+      // differences from c + 3 e_d, in reverse order
+      const bool up = vd > 0.0;
+      const double v1 = up ? (p[-2] - p[-3]) * rh : (p[3] - p[2]) * rh;
+      const double v2 = up ? (p[-1] - p[-2]) * rh : (p[2] - p[1]) * rh;
+      const double v3 = up ? (p[0] - p[-1]) * rh : (p[1] - p[0]) * rh;
+      const double v4 = up ? (p[1] - p[0]) * rh : (p[0] - p[-1]) * rh;
+      const double v5 = up ? (p[2] - p[1]) * rh : (p[-1] - p[-2]) * rh;
+      const double gd = weno5<double>(v1, v2, v3, v4, v5, eps);
       adv = adv + vd * gd;
     }
     const double phn = b.chin[c] == r ? b.phin[c] : -b.phin[c];
     b.phir[(long long)k * N + r] = beta * phn + omb * (phir_stage(b, c, r) - dt * adv);
   }
 }
+template <bool LIST>
 __device__ __forceinline__ void phase_levelset(const Grid& g, const Bufs& b, const double* vel, double beta, double omb, int first_, int stride_) {
-  if (g.D == 1) phase_levelset_d<1>(g, b, vel, beta, omb, first_, stride_);
-  else if (g.D == 2) phase_levelset_d<2>(g, b, vel, beta, omb, first_, stride_);
-  else phase_levelset_d<3>(g, b, vel, beta, omb, first_, stride_);
+  if (g.D == 1) phase_levelset_d<1, LIST>(g, b, vel, beta, omb, first_, stride_);
+  else if (g.D == 2) phase_levelset_d<2, LIST>(g, b, vel, beta, omb, first_, stride_);
+  else phase_levelset_d<3, LIST>(g, b, vel, beta, omb, first_, stride_);
 }
 __global__ void k_levelset(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* vel, double beta, double omb) {
   if (!ctl_active(b)) return;
-  phase_levelset(g, b, vel, beta, omb, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  phase_levelset<true>(g, b, vel, beta, omb, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 // reconstruction R: |max_r phi^r| and argmax (lowest index on ties), clamped
 __device__ __forceinline__ void phase_levelset_R(const Grid& g, const Bufs& b, int first_, int stride_) {
@@ -2143,14 +2185,26 @@ __device__ __forceinline__ void phase_scale_sep(const Grid& g, const Bufs& b, do
     int q[3];
     coords(g, c, q);
     const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
-    bool near_minus = false;
-    for (int dz = -rz; dz <= rz && !near_minus; dz++)
-      for (int dy = -ry; dy <= ry && !near_minus; dy++)
-        for (int dx = -1; dx <= 1 && !near_minus; dx++) {
-          double mn, mx;
-          vertex_minmax(g, b.phi, b.chi, cell_at(g, q[0] + dx, q[1] + dy, q[2] + dz), chi1, &mn, &mx);
-          if (mn - eps <= 0.0 && mx - eps >= 0.0) near_minus = true;
-        }
+    // any cell of the 3^d block whose simplex values of phi^chi1 reach eps
+    // from both sides; the cell itself (which holds two materials) first,
+    // the answer does not depend on the order
+    double mn0, mx0;
+    vertex_minmax(g, b.phi, b.chi, c, chi1, &mn0, &mx0);
+    bool near_minus = mn0 - eps <= 0.0 && mx0 - eps >= 0.0;
+    // then the neighbours cut by chi1's interface (0 < alpha < 1: their
+    // values have both signs, the likely hits), then the others
+    for (int pass = 0; pass < 2 && !near_minus; pass++)
+      for (int dz = -rz; dz <= rz && !near_minus; dz++)
+        for (int dy = -ry; dy <= ry && !near_minus; dy++)
+          for (int dx = -1; dx <= 1 && !near_minus; dx++) {
+            if (dx == 0 && dy == 0 && dz == 0) continue;
+            const long long nc = cell_at(g, q[0] + dx, q[1] + dy, q[2] + dz);
+            const double an = b.alpha[midx(g, chi1, nc)];
+            if ((an > 0.0 && an < 1.0) != (pass == 0)) continue;
+            double mn, mx;
+            vertex_minmax(g, b.phi, b.chi, nc, chi1, &mn, &mx);
+            if (mn - eps <= 0.0 && mx - eps >= 0.0) near_minus = true;
+          }
     if (near_minus) continue;
     nodd++;
     int chs = -1;
@@ -2469,7 +2523,7 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
     __syncthreads();
     phase_geom_mat_d<1>(g, b, t, nt);
     __syncthreads();
-    phase_geom_cell(g, b, b.Q[0], (const double*)nullptr, t, nt);
+    phase_geom_cell<false>(g, b, b.Q[0], (const double*)nullptr, t, nt);
     __syncthreads();
     if (g.fs_mat >= 0) {
       phase_hold(g, b, b.Q[0], -1, t, nt);
@@ -2535,7 +2589,7 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
         b.ctl->ledger[mv / g.NV][mv % g.NV] += g.rk_lw[s] * b.ctl->dt * sum;
       }
       __syncthreads();
-      phase_levelset_d<1>(g, b, vc ? b.vel1 : b.vel0, beta, 1.0 - beta, t, nt);
+      phase_levelset_d<1, false>(g, b, vc ? b.vel1 : b.vel0, beta, 1.0 - beta, t, nt);
       __syncthreads();
       phase_levelset_R(g, b, t, nt);
       __syncthreads();
@@ -2543,7 +2597,7 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
       __syncthreads();
       phase_geom_mat_d<1>(g, b, t, nt);
       __syncthreads();
-      phase_geom_cell(g, b, (const double*)Qo, (const double*)nullptr, t, nt);
+      phase_geom_cell<false>(g, b, (const double*)Qo, (const double*)nullptr, t, nt);
       __syncthreads();
       if (g.fs_mat >= 0) {
         phase_hold(g, b, Qo, s + 1, t, nt);

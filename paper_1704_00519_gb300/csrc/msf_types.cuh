@@ -39,6 +39,7 @@ struct Bufs {
   double* mixT;             // [nbandmax][N] weight sum of the mixing pairs of the cell
   int* mixlist;             // [nbandmax * N] items (k * N + m) of the running mixing pass that mix
   int* geomlist;            // [nbandmax * N] 3D cut items (m * nband + k) of the running geometry pass
+  int* lslist;              // [nbandmax * N] level-set items (r * nband + k) of the next level-set stage
   uint8_t* mixtouch;        // [nbandmax] 1: a material of band cell k mixes in this pass
   double* phir;             // [nbandmax][N] new local level-set values
   double* bflux;            // [nbnd][N][NV] boundary-face fluxes of the stage
