@@ -574,6 +574,7 @@ def run_gpu(args):
     fma32 = msf.fma_peak(msf.MSF_FP32_BULK, sptr)
     flops64 = npairs64 * 3 * flux_flops_per_pair_stage(case.dim)
     achieved64 = flops64 / flux64_s
+    achieved32_flops = npairs * 3 * flux_flops_per_pair_stage(case.dim) / flux_s
 
     # every output of the FP32-bulk form against the plain FP64 path after the
     # same steps from the same start
@@ -643,6 +644,11 @@ def run_gpu(args):
                           "peak_source": "measured here: msf_fma_peak FP64 (independent FMA chains on every SM)",
                           "flops_per_pair_stage": flux_flops_per_pair_stage(case.dim),
                           "flux_ms_per_step": 1e3 * flux64_s},
+        "roofline_alu_fp32": {"kernel": "k_flux_update<3,float>", "bound": "alu",
+                              "achieved": achieved32_flops / 1e12, "peak": fma32 / 1e12, "unit": "TFLOP/s",
+                              "frac": achieved32_flops / fma32,
+                              "peak_source": "measured here: msf_fma_peak FP32 (independent FMA chains on every SM)",
+                              "flops_per_pair_stage": flux_flops_per_pair_stage(case.dim)},
         "fma_peak_tflops": {"fp64": fma64 / 1e12, "fp32": fma32 / 1e12},
         "fp32_error_vs_fp64": errs,
         "roofline": {"kernel": "k_flux_update<3,float>", "bound": "hbm", "achieved": achieved, "peak": peak,

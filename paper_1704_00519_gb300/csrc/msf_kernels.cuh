@@ -1899,7 +1899,8 @@ __device__ inline bool is_small(const Grid& g, const Bufs& b, const double* Qc, 
       if (Qc[qidx(g, m, v, c)] != 0.0) return true;
   if (as > 0.0) {  // a non-physical state (rho <= 0 or p + pinf <= 0) mixes like a small cell
     double u[5], w[5];
-    for (int v = 0; v < g.NV; v++) u[v] = Qc[qidx(g, m, v, c)] / as;
+    // a division by 1 returns its dividend: a whole cell skips them
+    for (int v = 0; v < g.NV; v++) u[v] = as == 1.0 ? Qc[qidx(g, m, v, c)] : Qc[qidx(g, m, v, c)] / as;
     cons_to_prim<double>(g, m, g.D, u, w);
     if (!(w[0] > 0.0) || !(w[g.NV - 1] + g.pinf[m] > 0.0)) return true;
   }
@@ -1951,20 +1952,15 @@ __global__ void k_mix_mark(const __grid_constant__ Grid g, const __grid_constant
 // cell's with weight beta a_s V_s / (a_s V_s + a_t V_t).
 // T sums a cell's weights: its own pairs in target order, then the pairs of
 // the neighbours that mix into it in (z, y, x) offset order.
-template <int DD, bool LIST>
+template <int DD>
 __device__ __forceinline__ void phase_mix_weights_d(const Grid& g, const Bufs& b, int first_, int stride_) {
-  const int nb = b.ctl->nband, N = g.N, D = DD;
+  const int nb = b.ctl->nband, N = g.N;
   const int total = nb * N;
   for (int it = first_; it < total; it += stride_) {
     const int m = it / nb, k = it - m * nb;
     const long long c = b.band[k];
     const long long r = (long long)k * N + m;
     double T = 0.0;
-    if (LIST && (b.mixn[r] != 0xff || b.mixin[r] != 0u)) {
-      // an item that mixes: small, or a target of a small neighbour
-      b.mixlist[atomicAdd(&b.ctl->mix_count, 1u)] = (int)r;
-      b.mixtouch[k] = 1;
-    }
     if ((b.smask[c] >> m) & 1u) {
       const double ac = b.alpha[midx(g, m, c)], vc = vfac(g, c);
       const int nown = b.mixn[r];
@@ -1973,48 +1969,35 @@ __device__ __forceinline__ void phase_mix_weights_d(const Grid& g, const Bufs& b
         const double at = b.alpha[midx(g, m, tc)], vt = vfac(g, tc);
         T += b.mixbeta[r * MIX_MAXT + t] * (at * vt) / (ac * vc + at * vt);
       }
-      const unsigned inbits = b.mixin[r];
+      // the neighbours that mix into this cell, in (z, y, x) offset order:
+      // the set bits of mixin in increasing offset code
+      unsigned inbits = b.mixin[r];
       if (inbits) {
         int q[3];
         coords(g, c, q);
-        const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
-        for (int dz = -rz; dz <= rz; dz++)
-          for (int dy = -ry; dy <= ry; dy++)
-            for (int dx = -1; dx <= 1; dx++) {
-              if (dx == 0 && dy == 0 && dz == 0) continue;
-              const uint8_t code = off_code(dx, dy, dz);
-              if (!((inbits >> code) & 1u)) continue;
-              const int sx = q[0] - dx, sy = q[1] - dy, sz = q[2] - dz;
-              if (!in_array(g, sx, sy, sz)) continue;
-              const long long s = cell_at(g, sx, sy, sz);
-              const int ks = b.bandidx[s];
-              if (ks < 0) continue;
-              const long long rs = (long long)ks * N + m;
-              const int ns = b.mixn[rs];
-              if (ns == 0xff) continue;
-              for (int t = 0; t < ns; t++) {
-                if (b.mixoff[rs * MIX_MAXT + t] != code) continue;
-                const double as = b.alpha[midx(g, m, s)], vs = vfac(g, s);
-                T += b.mixbeta[rs * MIX_MAXT + t] * (as * vs) / (as * vs + ac * vc);
-              }
-            }
+        while (inbits) {
+          const int code = __ffs(inbits) - 1;
+          inbits &= inbits - 1u;
+          const int dz = code / 9 - 1, dy = (code / 3) % 3 - 1, dx = code % 3 - 1;
+          const int sx = q[0] - dx, sy = q[1] - dy, sz = q[2] - dz;
+          if (!in_array(g, sx, sy, sz)) continue;
+          const long long s = cell_at(g, sx, sy, sz);
+          const int ks = b.bandidx[s];
+          if (ks < 0) continue;
+          const long long rs = (long long)ks * N + m;
+          const int ns = b.mixn[rs];
+          if (ns == 0xff) continue;
+          for (int t = 0; t < ns; t++) {
+            if (b.mixoff[rs * MIX_MAXT + t] != code) continue;
+            const double as = b.alpha[midx(g, m, s)], vs = vfac(g, s);
+            T += b.mixbeta[rs * MIX_MAXT + t] * (as * vs) / (as * vs + ac * vc);
+          }
+        }
       }
     }
     b.mixT[r] = T;
   }
 }
-template <bool LIST>
-__device__ __forceinline__ void phase_mix_weights(const Grid& g, const Bufs& b, int first_, int stride_) {
-  if (g.D == 1) phase_mix_weights_d<1, LIST>(g, b, first_, stride_);
-  else if (g.D == 2) phase_mix_weights_d<2, LIST>(g, b, first_, stride_);
-  else phase_mix_weights_d<3, LIST>(g, b, first_, stride_);
-}
-// grid kernel: also lists the items that mix, for k_mix_compute and k_mix_scatter
-__global__ void k_mix_weights(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
-  if (!ctl_active(b)) return;
-  phase_mix_weights<true>(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-}
-
 // Scale of a pair exchange from the weight sums of its two cells: when a
 // cell's T exceeds one its mixed state would leave the range of the states it
 // mixes with, so the pair is scaled by min(1, 1/T_s, 1/T_t) (both sides by the
@@ -2028,12 +2011,248 @@ __device__ inline double mix_limit(double as, double Ts, double Tt) {
   return f;
 }
 
+// ---- warp-cooperative mixing pairs (grid kernels). The pairs of an item are
+// its own pairs as a small cell (in target order) followed by the pairs of
+// the neighbours that mix into it (in increasing offset code: the (z, y, x)
+// order above). The pairs of a warp's items are numbered consecutively and
+// taken 32 at a time, one per lane, so that their FP64 divisions run on full
+// warps; each item's lane then combines its pairs' values in that order with
+// the operations of the one-lane functions above, so the results are theirs.
+struct MixPair {
+  bool ok;         // the pair exists (the neighbour has a state and targets this cell)
+  bool own;        // the item is the pair's small cell
+  long long p;     // the other cell of the pair
+  long long rp;    // its item (band index * N + material)
+  double beta;     // the pair's mixing weight
+};
+// pair jj of item r (cell c, material m; nown own pairs, inbits incoming bits)
+__device__ __forceinline__ MixPair mix_pair(const Grid& g, const Bufs& b, long long r, long long c, int m, int nown,
+                                            unsigned inbits, int jj) {
+  MixPair P;
+  P.ok = false;
+  P.own = jj < nown;
+  P.p = 0;
+  P.rp = 0;
+  P.beta = 0.0;
+  const int N = g.N;
+  if (P.own) {
+    P.p = off_cell(g, c, b.mixoff[r * MIX_MAXT + jj]);
+    P.rp = (long long)b.bandidx[P.p] * N + m;
+    P.beta = b.mixbeta[r * MIX_MAXT + jj];
+    P.ok = true;
+    return P;
+  }
+  unsigned bits = inbits;  // the (jj - nown)-th set bit, counting from the lowest
+  for (int i = nown; i < jj; i++) bits &= bits - 1u;
+  const int code = __ffs(bits) - 1;
+  const int dz = code / 9 - 1, dy = (code / 3) % 3 - 1, dx = code % 3 - 1;
+  int q[3];
+  coords(g, c, q);
+  const int sx = q[0] - dx, sy = q[1] - dy, sz = q[2] - dz;
+  if (!in_array(g, sx, sy, sz)) return P;
+  const long long sc = cell_at(g, sx, sy, sz);
+  const int ks = b.bandidx[sc];
+  if (ks < 0) return P;
+  const long long rs = (long long)ks * N + m;
+  const int ns = b.mixn[rs];
+  if (ns == 0xff) return P;
+  for (int t = 0; t < ns; t++)  // a small cell's targets have distinct offsets
+    if (b.mixoff[rs * MIX_MAXT + t] == code) {
+      P.beta = b.mixbeta[rs * MIX_MAXT + t];
+      P.ok = true;
+      break;
+    }
+  P.p = sc;
+  P.rp = rs;
+  return P;
+}
+// per-lane table of the warp's items, read by the lanes that evaluate their pairs
+struct MixItemSm {
+  long long r, c;
+  int m, nown, pre;
+  unsigned inbits;
+};
+// exclusive prefix sum of the lanes' pair counts, and the warp's total
+__device__ __forceinline__ int warp_excl_scan(int P, int lane, int& tot) {
+  int incl = P;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  tot = __shfl_sync(0xffffffffu, incl, 31);
+  return incl - P;
+}
+// mark the lanes of round rb whose pairs belong to this lane's item
+__device__ __forceinline__ void mix_owner_map(uint8_t* owner, int pre, int P, int rb, int lane) {
+  const int j0 = pre > rb ? pre : rb, j1 = pre + P < rb + 32 ? pre + P : rb + 32;
+  for (int j = j0; j < j1; j++) owner[j - rb] = (uint8_t)lane;
+}
+
+// weight sums T and the list of the items that mix (grid kernel; first_ and
+// stride_ warp-aligned, blockDim.x == BAND_THREADS)
+__device__ __forceinline__ void mix_weights_coop(const Grid& g, const Bufs& b, int first_, int stride_) {
+  __shared__ MixItemSm s_it[BAND_THREADS];
+  __shared__ uint8_t s_own[BAND_THREADS];
+  __shared__ double s_val[BAND_THREADS];
+  __shared__ uint8_t s_ok[BAND_THREADS];
+  const int nb = b.ctl->nband, N = g.N;
+  const int total = nb * N;
+  const int lane = threadIdx.x & 31, wb = threadIdx.x - lane;
+  for (int base = first_ - lane; base < total; base += stride_) {
+    const int it = base + lane;
+    const bool valid = it < total;
+    int m = 0, nown = 0, P = 0;
+    long long c = 0, r = 0;
+    unsigned inbits = 0;
+    if (valid) {
+      m = it / nb;
+      const int k = it - m * nb;
+      c = b.band[k];
+      r = (long long)k * N + m;
+      const int mn = b.mixn[r];
+      const unsigned mi = b.mixin[r];
+      if (mn != 0xff || mi != 0u) {
+        // an item that mixes: small, or a target of a small neighbour
+        b.mixlist[atomicAdd(&b.ctl->mix_count, 1u)] = (int)r;
+        b.mixtouch[k] = 1;
+      }
+      if ((b.smask[c] >> m) & 1u) {
+        nown = mn == 0xff ? 0 : mn;
+        inbits = mi;
+        P = nown + __popc(mi);
+      }
+    }
+    int tot;
+    const int pre = warp_excl_scan(P, lane, tot);
+    s_it[threadIdx.x] = MixItemSm{r, c, m, nown, pre, inbits};
+    double T = 0.0;
+    for (int rb = 0; rb < tot; rb += 32) {
+      __syncwarp();
+      mix_owner_map(s_own + wb, pre, P, rb, lane);
+      __syncwarp();
+      double val = 0.0;
+      bool ok = false;
+      if (rb + lane < tot) {
+        const MixItemSm o = s_it[wb + s_own[wb + lane]];
+        const MixPair pr = mix_pair(g, b, o.r, o.c, o.m, o.nown, o.inbits, rb + lane - o.pre);
+        if (pr.ok) {
+          ok = true;
+          const double ac = b.alpha[midx(g, o.m, o.c)], vc = vfac(g, o.c);
+          const double ap = b.alpha[midx(g, o.m, pr.p)], vp = vfac(g, pr.p);
+          val = pr.own ? pr.beta * (ap * vp) / (ac * vc + ap * vp) : pr.beta * (ap * vp) / (ap * vp + ac * vc);
+        }
+      }
+      s_val[threadIdx.x] = val;
+      s_ok[threadIdx.x] = ok ? 1 : 0;
+      __syncwarp();
+      const int j0 = pre > rb ? pre : rb, j1 = pre + P < rb + 32 ? pre + P : rb + 32;
+      for (int j = j0; j < j1; j++)
+        if (s_ok[wb + j - rb]) T += s_val[wb + j - rb];
+    }
+    if (valid) b.mixT[r] = T;
+  }
+}
+
+// mixed states of the listed items into mixq (grid kernel; first_ and stride_
+// warp-aligned, blockDim.x == BAND_THREADS)
+template <int DD>
+__device__ __forceinline__ void mix_compute_coop(const Grid& g, const Bufs& b, const double* Qc, int first_,
+                                                 int stride_) {
+  constexpr int NV = DD + 2;
+  __shared__ MixItemSm s_it[BAND_THREADS];
+  __shared__ uint8_t s_own[BAND_THREADS];
+  __shared__ double s_x[NV][BAND_THREADS];
+  __shared__ double s_f[BAND_THREADS], s_mul[BAND_THREADS];
+  __shared__ int8_t s_sg[BAND_THREADS];
+  const int N = g.N, total = (int)b.ctl->mix_count;
+  const int lane = threadIdx.x & 31, wb = threadIdx.x - lane;
+  for (int base = first_ - lane; base < total; base += stride_) {
+    const int it = base + lane;
+    const bool valid = it < total;
+    int m = 0, nown = 0, P = 0;
+    long long c = 0, r = 0;
+    unsigned inbits = 0;
+    bool live = false;
+    if (valid) {
+      r = b.mixlist[it];
+      const int k = (int)(r / N);
+      m = (int)(r - (long long)k * N);
+      c = b.band[k];
+      live = (b.smask[c] >> m) & 1u;
+      if (!live) {
+        for (int v = 0; v < NV; v++) b.mixq[r * NV + v] = Qc[qidx(g, m, v, c)];
+      } else {
+        const int mn = b.mixn[r];
+        if (mn != 0xff) {
+          nown = mn;
+          if (mn == 0 && b.alpha[midx(g, m, c)] == 0.0 && m != b.chi[c]) atomicOr(&b.mixmerge[k], 1u << m);
+        }
+        inbits = b.mixin[r];
+        P = nown + __popc(inbits);
+      }
+    }
+    int tot;
+    const int pre = warp_excl_scan(P, lane, tot);
+    s_it[threadIdx.x] = MixItemSm{r, c, m, nown, pre, inbits};
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) acc[v] = 0.0;
+    for (int rb = 0; rb < tot; rb += 32) {
+      __syncwarp();
+      mix_owner_map(s_own + wb, pre, P, rb, lane);
+      __syncwarp();
+      int8_t sg = 0;
+      if (rb + lane < tot) {
+        const MixItemSm o = s_it[wb + s_own[wb + lane]];
+        const MixPair pr = mix_pair(g, b, o.r, o.c, o.m, o.nown, o.inbits, rb + lane - o.pre);
+        if (pr.ok) {
+          // small cell s and target t of the pair: the item is s (own) or t
+          const long long cs = pr.own ? o.c : pr.p, ct = pr.own ? pr.p : o.c;
+          const double as = b.alpha[midx(g, o.m, cs)], vs = vfac(g, cs);
+          const double at = b.alpha[midx(g, o.m, ct)], vt = vfac(g, ct);
+          const double f = pr.own ? mix_limit(as, b.mixT[o.r], b.mixT[pr.rp]) : mix_limit(as, b.mixT[pr.rp], b.mixT[o.r]);
+#pragma unroll
+          for (int v = 0; v < NV; v++)
+            s_x[v][threadIdx.x] = (pr.beta * (as * Qc[qidx(g, o.m, v, ct)] - at * Qc[qidx(g, o.m, v, cs)])) / (as * vs + at * vt);
+          s_f[threadIdx.x] = f;
+          s_mul[threadIdx.x] = pr.own ? vt : vs;
+          sg = pr.own ? 1 : -1;
+        }
+      }
+      s_sg[threadIdx.x] = sg;
+      __syncwarp();
+      const int j0 = pre > rb ? pre : rb, j1 = pre + P < rb + 32 ? pre + P : rb + 32;
+      for (int j = j0; j < j1; j++) {
+        const int sl = wb + j - rb;
+        const int8_t sj = s_sg[sl];
+        if (sj == 0) continue;
+        const double f = s_f[sl], mul = s_mul[sl];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          const double x = f * (s_x[v][sl] * mul);
+          acc[v] = sj > 0 ? acc[v] + x : acc[v] - x;
+        }
+      }
+    }
+    if (valid && live)
+      for (int v = 0; v < NV; v++) b.mixq[r * NV + v] = Qc[qidx(g, m, v, c)] + acc[v];
+  }
+}
+
+// grid kernel: also lists the items that mix, for k_mix_compute and k_mix_scatter
+__global__ void k_mix_weights(const __grid_constant__ Grid g, const __grid_constant__ Bufs b) {
+  if (!ctl_active(b)) return;
+  mix_weights_coop(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+
 // new state of material m of every band cell: own exchanges minus the
 // exchanges its small neighbours send to it (lexicographic neighbour order),
 // each scaled by mix_limit
 template <int DD>
 __device__ __forceinline__ void mix_compute_item(const Grid& g, const Bufs& b, const double* Qc, int k, int m) {
-    const int N = g.N, NV = DD + 2, D = DD;
+    const int N = g.N, NV = DD + 2;
   {
     const long long c = b.band[k];
     const long long r = (long long)k * N + m;
@@ -2059,33 +2278,32 @@ __device__ __forceinline__ void mix_compute_item(const Grid& g, const Bufs& b, c
           acc[v] += f * ((beta * (as * Qc[qidx(g, m, v, tc)] - at * Qc[qidx(g, m, v, c)]) / (as * vs + at * vt)) * vt);
       }
     }
-    // neighbours that mix into this cell (bits set by the marking pass)
-    const unsigned inbits = b.mixin[r];
-    const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
-    for (int dz = -rz; dz <= rz && inbits; dz++)
-      for (int dy = -ry; dy <= ry; dy++)
-        for (int dx = -1; dx <= 1; dx++) {
-          if (dx == 0 && dy == 0 && dz == 0) continue;
-          const uint8_t code = off_code(dx, dy, dz);
-          if (!((inbits >> code) & 1u)) continue;
-          const int sx = q[0] - dx, sy = q[1] - dy, sz = q[2] - dz;
-          if (!in_array(g, sx, sy, sz)) continue;
-          const long long s = cell_at(g, sx, sy, sz);
-          const int ks = b.bandidx[s];
-          if (ks < 0) continue;
-          const long long rs = (long long)ks * N + m;
-          const int ns = b.mixn[rs];
-          if (ns == 0xff) continue;
-          for (int t = 0; t < ns; t++) {
-            if (b.mixoff[rs * MIX_MAXT + t] != code) continue;
-            const double beta = b.mixbeta[rs * MIX_MAXT + t];
-            const double as = b.alpha[midx(g, m, s)], vs = vfac(g, s);
-            const double at = b.alpha[midx(g, m, c)], vt = vfac(g, c);
-            const double f = mix_limit(as, b.mixT[rs], b.mixT[r]);
-            for (int v = 0; v < NV; v++)
-              acc[v] -= f * ((beta * (as * Qc[qidx(g, m, v, c)] - at * Qc[qidx(g, m, v, s)]) / (as * vs + at * vt)) * vs);
-          }
-        }
+    // neighbours that mix into this cell (bits set by the marking pass), in
+    // (z, y, x) offset order: the set bits in increasing offset code, so that
+    // the lanes of a warp take their k-th neighbour together
+    unsigned inbits = b.mixin[r];
+    while (inbits) {
+      const int code = __ffs(inbits) - 1;
+      inbits &= inbits - 1u;
+      const int dz = code / 9 - 1, dy = (code / 3) % 3 - 1, dx = code % 3 - 1;
+      const int sx = q[0] - dx, sy = q[1] - dy, sz = q[2] - dz;
+      if (!in_array(g, sx, sy, sz)) continue;
+      const long long s = cell_at(g, sx, sy, sz);
+      const int ks = b.bandidx[s];
+      if (ks < 0) continue;
+      const long long rs = (long long)ks * N + m;
+      const int ns = b.mixn[rs];
+      if (ns == 0xff) continue;
+      for (int t = 0; t < ns; t++) {
+        if (b.mixoff[rs * MIX_MAXT + t] != code) continue;
+        const double beta = b.mixbeta[rs * MIX_MAXT + t];
+        const double as = b.alpha[midx(g, m, s)], vs = vfac(g, s);
+        const double at = b.alpha[midx(g, m, c)], vt = vfac(g, c);
+        const double f = mix_limit(as, b.mixT[rs], b.mixT[r]);
+        for (int v = 0; v < NV; v++)
+          acc[v] -= f * ((beta * (as * Qc[qidx(g, m, v, c)] - at * Qc[qidx(g, m, v, s)]) / (as * vs + at * vt)) * vs);
+      }
+    }
     for (int v = 0; v < NV; v++) out[v] = Qc[qidx(g, m, v, c)] + acc[v];
   }
 }
@@ -2099,28 +2317,14 @@ __device__ __forceinline__ void phase_mix_compute_d(const Grid& g, const Bufs& b
     mix_compute_item<DD>(g, b, Qc, k, m);
   }
 }
-__device__ __forceinline__ void phase_mix_compute(const Grid& g, const Bufs& b, const double* Qc, int first_, int stride_) {
-  if (g.D == 1) phase_mix_compute_d<1>(g, b, Qc, first_, stride_);
-  else if (g.D == 2) phase_mix_compute_d<2>(g, b, Qc, first_, stride_);
-  else phase_mix_compute_d<3>(g, b, Qc, first_, stride_);
-}
 // grid kernel: only the listed items (a fifth of the band or less; the others
-// keep their state), so that the FP64 work of the exchanges runs on full
-// warps instead of the few lanes of a warp that hold a small cell
-template <int DD>
-__device__ __forceinline__ void mix_compute_listed(const Grid& g, const Bufs& b, const double* Qc, int first_, int stride_) {
-  const int N = g.N, total = (int)b.ctl->mix_count;
-  for (int it = first_; it < total; it += stride_) {
-    const int r = b.mixlist[it];
-    mix_compute_item<DD>(g, b, Qc, r / N, r - (r / N) * N);
-  }
-}
+// keep their state), their pairs spread over the lanes of each warp
 __global__ void k_mix_compute(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qc) {
   if (!ctl_active(b)) return;
   const int first = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  if (g.D == 1) mix_compute_listed<1>(g, b, Qc, first, stride);
-  else if (g.D == 2) mix_compute_listed<2>(g, b, Qc, first, stride);
-  else mix_compute_listed<3>(g, b, Qc, first, stride);
+  if (g.D == 1) mix_compute_coop<1>(g, b, Qc, first, stride);
+  else if (g.D == 2) mix_compute_coop<2>(g, b, Qc, first, stride);
+  else mix_compute_coop<3>(g, b, Qc, first, stride);
 }
 // write the mixed states back; a material that lost all volume and has no
 // same-material neighbour is merged into the cell's primary material
@@ -2168,43 +2372,57 @@ __global__ void k_mix_scatter(const __grid_constant__ Grid g, const __grid_const
 }
 
 // ------------------------------------------------- scale separation (a12)
+// first_ and stride_ must be warp-aligned (lane l of a warp starts at a
+// multiple of 32 plus l, stride a multiple of 32): the test of a candidate's
+// 3^d block runs on the lanes of its warp, one block cell per lane.
 __device__ __forceinline__ void phase_scale_sep(const Grid& g, const Bufs& b, double* Q, int first_, int stride_) {
     const int nb = b.ctl->nband, N = g.N, D = g.D;
   const double eps = g.eps_ss;
   unsigned long long nodd = 0, nmove = 0;
-  for (int k = first_; k < nb; k += stride_) {
-    const long long c = b.band[k];
-    b.phit[k] = b.phi[c];
-    b.chit[k] = b.chi[c];
-    if (!(b.gflag[c] & GF_MIXED)) continue;
-    int np = 0;
-    for (int m = 0; m < N; m++)
-      if (present(g, b, c, m)) np++;
-    if (np < 2) continue;
-    const int chi1 = b.chi[c];
+  const int lane = threadIdx.x & 31;
+  const unsigned FULL = 0xffffffffu;
+  const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
+  const int nblock = (2 * rz + 1) * (2 * ry + 1) * 3;  // cells of the 3^d block
+  for (int base = first_ - lane; base < nb; base += stride_) {
+    const int k = base + lane;
+    long long c = 0;
+    int chi1 = 0;
+    bool cand = false;
+    if (k < nb) {
+      c = b.band[k];
+      b.phit[k] = b.phi[c];
+      b.chit[k] = b.chi[c];
+      if (b.gflag[c] & GF_MIXED) {
+        int np = 0;
+        for (int m = 0; m < N; m++)
+          if (present(g, b, c, m)) np++;
+        cand = np >= 2;
+        chi1 = b.chi[c];
+      }
+    }
+    // near_minus: some cell of the candidate's 3^d block whose simplex values
+    // of phi^chi1 reach eps from both sides (an OR over the block, taken by
+    // the warp's lanes together for each candidate in turn)
+    bool near_minus = false;
+    unsigned pend = __ballot_sync(FULL, cand);
+    while (pend) {
+      const int src = __ffs(pend) - 1;
+      pend &= pend - 1u;
+      const long long cs = __shfl_sync(FULL, c, src);
+      const int ch = __shfl_sync(FULL, chi1, src);
+      bool hit = false;
+      if (lane < nblock) {
+        const int dx = lane % 3 - 1, dy = (lane / 3) % (2 * ry + 1) - ry, dz = lane / (3 * (2 * ry + 1)) - rz;
+        double mn, mx;
+        vertex_minmax(g, b.phi, b.chi, cs + dx + g.st[1] * dy + g.st[2] * dz, ch, &mn, &mx);
+        hit = mn - eps <= 0.0 && mx - eps >= 0.0;
+      }
+      const bool any = __ballot_sync(FULL, hit) != 0u;
+      if (lane == src) near_minus = any;
+    }
+    if (!cand) continue;
     int q[3];
     coords(g, c, q);
-    const int rz = D >= 3 ? 1 : 0, ry = D >= 2 ? 1 : 0;
-    // any cell of the 3^d block whose simplex values of phi^chi1 reach eps
-    // from both sides; the cell itself (which holds two materials) first,
-    // the answer does not depend on the order
-    double mn0, mx0;
-    vertex_minmax(g, b.phi, b.chi, c, chi1, &mn0, &mx0);
-    bool near_minus = mn0 - eps <= 0.0 && mx0 - eps >= 0.0;
-    // then the neighbours cut by chi1's interface (0 < alpha < 1: their
-    // values have both signs, the likely hits), then the others
-    for (int pass = 0; pass < 2 && !near_minus; pass++)
-      for (int dz = -rz; dz <= rz && !near_minus; dz++)
-        for (int dy = -ry; dy <= ry && !near_minus; dy++)
-          for (int dx = -1; dx <= 1 && !near_minus; dx++) {
-            if (dx == 0 && dy == 0 && dz == 0) continue;
-            const long long nc = cell_at(g, q[0] + dx, q[1] + dy, q[2] + dz);
-            const double an = b.alpha[midx(g, chi1, nc)];
-            if ((an > 0.0 && an < 1.0) != (pass == 0)) continue;
-            double mn, mx;
-            vertex_minmax(g, b.phi, b.chi, nc, chi1, &mn, &mx);
-            if (mn - eps <= 0.0 && mx - eps >= 0.0) near_minus = true;
-          }
     if (near_minus) continue;
     nodd++;
     int chs = -1;
@@ -2605,7 +2823,7 @@ __global__ void __launch_bounds__(BS) k_batched(const BatchEntry* tab, const int
       }
       phase_mix_mark(g, b, (const double*)Qo, t, nt);
       __syncthreads();
-      phase_mix_weights_d<1, false>(g, b, t, nt);
+      phase_mix_weights_d<1>(g, b, t, nt);
       __syncthreads();
       phase_mix_compute_d<1>(g, b, (const double*)Qo, t, nt);
       __syncthreads();
