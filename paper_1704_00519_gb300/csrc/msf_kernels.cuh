@@ -2401,10 +2401,17 @@ __device__ __forceinline__ void phase_scale_sep(const Grid& g, const Bufs& b, do
       }
     }
     // near_minus: some cell of the candidate's 3^d block whose simplex values
-    // of phi^chi1 reach eps from both sides (an OR over the block, taken by
-    // the warp's lanes together for each candidate in turn)
+    // of phi^chi1 reach eps from both sides (an OR over the block): the cell
+    // itself first, on its own lane (it holds two materials: usually a hit),
+    // then the whole block of the remaining candidates, taken by the warp's
+    // lanes together for each candidate in turn
     bool near_minus = false;
-    unsigned pend = __ballot_sync(FULL, cand);
+    if (cand) {
+      double mn, mx;
+      vertex_minmax(g, b.phi, b.chi, c, chi1, &mn, &mx);
+      near_minus = mn - eps <= 0.0 && mx - eps >= 0.0;
+    }
+    unsigned pend = __ballot_sync(FULL, cand && !near_minus);
     while (pend) {
       const int src = __ffs(pend) - 1;
       pend &= pend - 1u;
