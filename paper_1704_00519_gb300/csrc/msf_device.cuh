@@ -304,6 +304,15 @@ __device__ __forceinline__ long long okey(double x) {
   return u >= 0 ? u : (u ^ 0x7fffffffffffffffLL);
 }
 
+// a < b on the bit patterns (integer compares): the order keys, with a +0 and
+// a -0 equal and a NaN unordered, as the IEEE comparison has them
+__device__ __forceinline__ bool lt_bits(double a, double b) {
+  const long long ma = __double_as_longlong(a) & 0x7fffffffffffffffLL;
+  const long long mb = __double_as_longlong(b) & 0x7fffffffffffffffLL;
+  const bool nan = ma > 0x7ff0000000000000LL || mb > 0x7ff0000000000000LL;
+  return !nan && (ma | mb) != 0 && okey(a) < okey(b);
+}
+
 // The same fractions without divergent branches and without FP64 compares,
 // for warps whose lanes take different cases: the values are sorted by a
 // network of compare and exchange steps on their order keys, the signs are

@@ -537,13 +537,21 @@ __device__ __forceinline__ void extend_items_d(const Grid& g, const Bufs& b, con
         for (int v = 0; v < NV; v++) x[i][v] = Wi[qidx(g, m, v, j)];
       }
     T acc[5] = {T(0), T(0), T(0), T(0), T(0)}, acc2[5] = {T(0), T(0), T(0), T(0), T(0)};
+    // the normal in T once per item (FP32: on the integer pipes, the same bits
+    // as the hardware conversion; the rounding is symmetric, so -(T)x = (T)(-x))
+    T nt[3];
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+      if constexpr (sizeof(T) == 4) nt[d] = d2f_bits(n[d]);
+      else nt[d] = (T)n[d];
+    }
     T sw = T(0);
     int cnt = 0;
     for (int d = 0; d < D; d++)
       for (int s = 0; s < 2; s++) {
         const int i = 2 * d + s;
         if (!use[i]) continue;
-        T w = (T)(s ? n[d] : -n[d]);
+        T w = s ? nt[d] : -nt[d];
         w = w > T(0) ? w : T(0);
         for (int v = 0; v < NV; v++) {
           acc[v] += w * x[i][v];
@@ -963,6 +971,17 @@ __global__ void k_interface(const __grid_constant__ Grid g, const __grid_constan
   phase_interface<T>(g, b, Qs, stage, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
+// x / n for a neighbour count n (1 to 6): a division by 1, 2 or 4 is the exact
+// scaling x, x / 2, x / 4, which a multiplication by 1/2 or 1/4 gives with the
+// same rounding; the count as a double without a conversion instruction
+__device__ __forceinline__ double div_count(double x, int n) {
+  if (n == 1) return x;
+  if (n == 2) return x * 0.5;
+  if (n == 4) return x * 0.25;
+  const double dn = n == 3 ? 3.0 : (n == 5 ? 5.0 : (n == 6 ? 6.0 : (double)n));
+  return x / dn;
+}
+
 // one sweep of the interface-velocity extension into the band
 template <int DD>
 __device__ __forceinline__ void extend_vel_items_d(const Grid& g, const Bufs& b, const double* vin, double* vout,
@@ -994,15 +1013,17 @@ __device__ __forceinline__ void extend_vel_items_d(const Grid& g, const Bufs& b,
         phj[i] = b.phi[j];
         for (int e = 0; e < D; e++) vj[i][e] = vin[e * g.ncell + j];
       }
-    double acc[3] = {0, 0, 0}, acc2[3] = {0, 0, 0};
+    // upwind neighbours (phi_j < phi_c, compared on the bit patterns), and the
+    // count of all filled ones; their plain mean is formed only when no
+    // neighbour is upwind (the same sums in the same order)
+    double acc[3] = {0, 0, 0};
     int cnt = 0, cnt2 = 0;
     for (int d = 0; d < D; d++)
       for (int s = 0; s < 2; s++) {
         const int i = 2 * d + s;
         if (!use[i]) continue;
-        for (int e = 0; e < D; e++) acc2[e] += vj[i][e];
         cnt2++;
-        if (phj[i] < phc) {
+        if (lt_bits(phj[i], phc)) {
           for (int e = 0; e < D; e++) acc[e] += vj[i][e];
           cnt++;
         }
@@ -1010,10 +1031,15 @@ __device__ __forceinline__ void extend_vel_items_d(const Grid& g, const Bufs& b,
     uint8_t filled = 0;
     for (int e = 0; e < 3; e++) vout[e * g.ncell + c] = vc[e];
     if (cnt > 0) {
-      for (int e = 0; e < D; e++) vout[e * g.ncell + c] = acc[e] / (double)cnt;
+      for (int e = 0; e < D; e++) vout[e * g.ncell + c] = div_count(acc[e], cnt);
       filled = 1;
     } else if (cnt2 > 0) {
-      for (int e = 0; e < D; e++) vout[e * g.ncell + c] = acc2[e] / (double)cnt2;
+      double acc2[3] = {0, 0, 0};
+      for (int d = 0; d < D; d++)
+        for (int s = 0; s < 2; s++)
+          if (use[2 * d + s])
+            for (int e = 0; e < D; e++) acc2[e] += vj[2 * d + s][e];
+      for (int e = 0; e < D; e++) vout[e * g.ncell + c] = div_count(acc2[e], cnt2);
       filled = 1;
     } else if (finc) {
       filled = 1;

@@ -59,8 +59,8 @@ __device__ unsigned long long pattern64(unsigned long long k) {
   return splitmix64(k * 0x632be59bd9b4e019ull);
 }
 
-// d2f_bits against the hardware narrowing; finite_bits, pos_bits and
-// neg_bits against isfinite, x > 0 and x < 0
+// d2f_bits against the hardware narrowing; finite_bits, pos_bits, neg_bits
+// and lt_bits against isfinite, x > 0, x < 0 and x < y
 __global__ void k_d2f(Result* r, unsigned long long count) {
   unsigned long long n = 0;
   for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < count;
@@ -72,6 +72,9 @@ __global__ void k_d2f(Result* r, unsigned long long count) {
     ok = ok && msf::finite_bits(x) == (bool)isfinite(x);
     ok = ok && msf::pos_bits(x) == (x > 0.0);
     ok = ok && msf::neg_bits(x) == (x < 0.0);
+    const double y = __longlong_as_double((long long)pattern64(k + 1));  // a neighbouring pattern
+    ok = ok && msf::lt_bits(x, y) == (x < y) && msf::lt_bits(y, x) == (y < x) && !msf::lt_bits(x, x);
+    ok = ok && msf::lt_bits(x, -x) == (x < -x) && msf::lt_bits(-x, x) == (-x < x);  // +0 against -0 too
     if (!ok) record(r, p);
     n++;
   }

@@ -108,7 +108,7 @@ def test_float_to_double_every_pattern(conv_libs, unit):
 
 
 @pytest.mark.parametrize("unit", ["f32", "f64"])
-def test_double_to_float_and_sign_tests(conv_libs, unit):
+def test_double_to_float_sign_and_order_tests(conv_libs, unit):
     count = 1 << 28
     out = (C.c_ulonglong * 3)()
     assert conv_libs[unit].conv_check(1, count, out) == 0
