@@ -119,9 +119,10 @@ __device__ inline double tait_pressure(const Grid& g, int m, double rho) {
   const double B = g.tait_B[m];
   return B * pow(rho / g.tait_rho0[m], g.gamma[m]) - B + g.tait_p0[m];
 }
-// conservative (rho, rho u, rho E) -> primitive (rho, u, p), in T
+// conservative (rho, rho u, rho E) -> primitive (rho, u, p), in T, with the
+// material's gamma - 1 and gamma pinf given in T
 template <typename T>
-__device__ inline void cons_to_prim(const Grid& g, int m, int D, const T* u, T* w) {
+__device__ inline void cons_to_prim_k(const Grid& g, int m, int D, const T* u, T* w, T gm1, T gpi) {
   T rho = u[0];
   T vel[3] = {T(0), T(0), T(0)};
   T q = T(0);
@@ -130,7 +131,11 @@ __device__ inline void cons_to_prim(const Grid& g, int m, int D, const T* u, T* 
   T ke = T(0.5) * rho * q;
   w[0] = rho;
   for (int d = 0; d < D; d++) w[1 + d] = vel[d];
-  w[D + 1] = g.eos_kind[m] == 1 ? (T)tait_pressure(g, m, (double)rho) : T(g.gm1[m]) * (u[D + 1] - ke) - T(g.gpi[m]);
+  w[D + 1] = g.eos_kind[m] == 1 ? (T)tait_pressure(g, m, (double)rho) : gm1 * (u[D + 1] - ke) - gpi;
+}
+template <typename T>
+__device__ inline void cons_to_prim(const Grid& g, int m, int D, const T* u, T* w) {
+  cons_to_prim_k<T>(g, m, D, u, w, T(g.gm1[m]), T(g.gpi[m]));
 }
 template <typename T>
 __device__ inline void prim_to_cons(const Grid& g, int m, int D, const T* w, T* u) {
@@ -141,15 +146,20 @@ __device__ inline void prim_to_cons(const Grid& g, int m, int D, const T* w, T* 
   for (int d = 0; d < D; d++) u[1 + d] = rho * w[1 + d];
   u[D + 1] = (w[D + 1] + T(g.gpi[m])) / T(g.gm1[m]) + T(0.5) * rho * q;
 }
-// c = sqrt(gamma (p + pinf) / rho); flags a non-physical state
+// c = sqrt(gamma (p + pinf) / rho); flags a non-physical state; gamma and
+// pinf given in T
 template <typename T>
-__device__ inline T sound(const Grid& g, int m, T rho, T p, unsigned* err) {
-  T c2 = (T(g.gamma[m]) * (p + T(g.pinf[m]))) / rho;
+__device__ inline T sound_k(T gam, T pinf, T rho, T p, unsigned* err) {
+  T c2 = (gam * (p + pinf)) / rho;
   if (!(rho > T(0)) || !(c2 > T(0))) {
     *err |= ERR_NEGATIVE;
     c2 = c2 > T(0) ? c2 : T(0);
   }
   return sqrt(c2);
+}
+template <typename T>
+__device__ inline T sound(const Grid& g, int m, T rho, T p, unsigned* err) {
+  return sound_k<T>(T(g.gamma[m]), T(g.pinf[m]), rho, p, err);
 }
 
 // -------------------------- axisymmetric grid and free surface (Sec. 3, Case II)

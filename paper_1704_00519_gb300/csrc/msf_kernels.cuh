@@ -382,7 +382,10 @@ __device__ __forceinline__ void phase_geom_cell(const Grid& g, const Bufs& b, co
         double s = 0.0;
         for (int m = 0; m < N; m++)
           if ((bits >> m) & 1u) s += A[aidx(g, d, m, c)];
-        if (s > 0.0) {
+        if (s == 1.0) {
+          // a division by 1 returns its dividend: nothing to scale (the faces
+          // of uncut cells, apertures 1 and 0)
+        } else if (s > 0.0) {
           for (int m = 0; m < N; m++)
             if ((bits >> m) & 1u) A[aidx(g, d, m, c)] = A[aidx(g, d, m, c)] / s;
         } else {
@@ -762,7 +765,7 @@ __global__ void k_bc_uhat(const __grid_constant__ Grid g, const __grid_constant_
 // largest sum_d (|u_d| + c) / h_d over the items [first, n_interior) with stride
 template <typename T, int DD>
 __device__ __forceinline__ double dt_items_d(const Grid& g, const Bufs& b, const double* Qs, long long first,
-                                           long long stride, unsigned& err) {
+                                           long long stride, unsigned& err, const T* tab = nullptr) {
   const int N = g.N, D = DD, NV = DD + 2;
   double lam = 0.0;
   // the largest material bound is kept in T: widening to FP64 is exact and
@@ -786,8 +789,16 @@ __device__ __forceinline__ double dt_items_d(const Grid& g, const Bufs& b, const
       } else {
         interior_uhat<T>(g, b, Qs, c, m, u);
       }
-      cons_to_prim<T>(g, m, D, u, w);
-      const T cs = sound<T>(g, m, w[0], w[D + 1], &err);
+      // material constants in T from the table when given (the values the
+      // conversions below produce)
+      T cs;
+      if (tab) {
+        cons_to_prim_k<T>(g, m, D, u, w, tab[m], tab[MAXM + m]);
+        cs = sound_k<T>(tab[2 * MAXM + m], tab[3 * MAXM + m], w[0], w[D + 1], &err);
+      } else {
+        cons_to_prim<T>(g, m, D, u, w);
+        cs = sound<T>(g, m, w[0], w[D + 1], &err);
+      }
       T s = T(0);
 #pragma unroll
       for (int d = 0; d < D; d++) s += (fabs(w[1 + d]) + cs) * rhT[d];
@@ -805,10 +816,10 @@ __device__ __forceinline__ double dt_items_d(const Grid& g, const Bufs& b, const
 }
 template <typename T>
 __device__ __forceinline__ double dt_items(const Grid& g, const Bufs& b, const double* Qs, long long first,
-                                           long long stride, unsigned& err) {
-  if (g.D == 1) return dt_items_d<T, 1>(g, b, Qs, first, stride, err);
-  if (g.D == 2) return dt_items_d<T, 2>(g, b, Qs, first, stride, err);
-  return dt_items_d<T, 3>(g, b, Qs, first, stride, err);
+                                           long long stride, unsigned& err, const T* tab) {
+  if (g.D == 1) return dt_items_d<T, 1>(g, b, Qs, first, stride, err, tab);
+  if (g.D == 2) return dt_items_d<T, 2>(g, b, Qs, first, stride, err, tab);
+  return dt_items_d<T, 3>(g, b, Qs, first, stride, err, tab);
 }
 // block maximum of per-thread values (blockDim.x a power of two <= 1024)
 __device__ __forceinline__ double block_max(double v) {
@@ -826,9 +837,19 @@ __device__ __forceinline__ double block_max(double v) {
 template <typename T>
 __global__ void k_dt(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, const double* Qs) {
   if (!ctl_active(b)) return;
+  // per-material constants in T: gamma - 1, gamma pinf, gamma, pinf
+  __shared__ T s_tab[4 * MAXM];
+  if (threadIdx.x < (unsigned)g.N) {
+    const int m = threadIdx.x;
+    s_tab[m] = T(g.gm1[m]);
+    s_tab[MAXM + m] = T(g.gpi[m]);
+    s_tab[2 * MAXM + m] = T(g.gamma[m]);
+    s_tab[3 * MAXM + m] = T(g.pinf[m]);
+  }
+  __syncthreads();
   unsigned err = 0;
   const double lam = dt_items<T>(g, b, Qs, blockIdx.x * (long long)blockDim.x + threadIdx.x,
-                                 (long long)gridDim.x * blockDim.x, err);
+                                 (long long)gridDim.x * blockDim.x, err, s_tab);
   const double bm = block_max(lam);
   if (threadIdx.x == 0) atomic_max_pos_double(&b.ctl->lam_bits, bm);
   if (err) atomicOr(&b.ctl->err, err);
@@ -1711,40 +1732,50 @@ __global__ void __launch_bounds__(Tile<D>::X* Tile<D>::Y* Tile<D>::Z, sizeof(T) 
   }
 }
 
+// sum of a value over the lanes of a warp, by a butterfly of exchanges in a
+// fixed order (every lane gets the same bits, on every run)
+__device__ __forceinline__ double warp_sum_fixed(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 // sum the boundary-face fluxes of the stage into the ledger, in two fixed-order
-// passes: each block adds NTHREADS faces for every (material, variable) by a
-// tree in shared memory, then one block adds the partial sums of all blocks
+// passes: each block adds NTHREADS faces for every (material, variable), warp
+// by warp and then over its warps in order, and one block adds the partial
+// sums of all blocks the same way
 __global__ void k_ledger_partial(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, int nbnd) {
   if (!ctl_active(b)) return;
   const int NMV = g.N * g.NV;
   const int f = blockIdx.x * NTHREADS + threadIdx.x;
-  __shared__ double red[NTHREADS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ double red[NTHREADS / 32][MAXM * 5];
   for (int mv = 0; mv < NMV; mv++) {
-    red[threadIdx.x] = f < nbnd ? b.bflux[(long long)f * NMV + mv] : 0.0;
-    __syncthreads();
-    for (int k = NTHREADS / 2; k > 0; k >>= 1) {
-      if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) b.lpart[(long long)blockIdx.x * NMV + mv] = red[0];
-    __syncthreads();
+    const double v = warp_sum_fixed(f < nbnd ? b.bflux[(long long)f * NMV + mv] : 0.0);
+    if (lane == 0) red[warp][mv] = v;
+  }
+  __syncthreads();
+  for (int mv = threadIdx.x; mv < NMV; mv += NTHREADS) {
+    double s = 0.0;
+    for (int w = 0; w < NTHREADS / 32; w++) s += red[w][mv];
+    b.lpart[(long long)blockIdx.x * NMV + mv] = s;
   }
 }
 __global__ void k_ledger(const __grid_constant__ Grid g, const __grid_constant__ Bufs b, int nparts, double w) {
   if (!ctl_active(b)) return;
   const int NMV = g.N * g.NV;
-  __shared__ double red[NTHREADS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ double red[NTHREADS / 32][MAXM * 5];
   for (int mv = 0; mv < NMV; mv++) {
     double s = 0.0;
     for (int k = threadIdx.x; k < nparts; k += NTHREADS) s += b.lpart[(long long)k * NMV + mv];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int k = NTHREADS / 2; k > 0; k >>= 1) {
-      if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) b.ctl->ledger[mv / g.NV][mv % g.NV] += w * b.ctl->dt * red[0];
-    __syncthreads();
+    s = warp_sum_fixed(s);
+    if (lane == 0) red[warp][mv] = s;
+  }
+  __syncthreads();
+  for (int mv = threadIdx.x; mv < NMV; mv += NTHREADS) {
+    double s = 0.0;
+    for (int k = 0; k < NTHREADS / 32; k++) s += red[k][mv];
+    b.ctl->ledger[mv / g.NV][mv % g.NV] += w * b.ctl->dt * s;
   }
 }
 
