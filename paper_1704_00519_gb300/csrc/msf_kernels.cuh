@@ -821,17 +821,18 @@ __device__ __forceinline__ double dt_items(const Grid& g, const Bufs& b, const d
   if (g.D == 2) return dt_items_d<T, 2>(g, b, Qs, first, stride, err, tab);
   return dt_items_d<T, 3>(g, b, Qs, first, stride, err, tab);
 }
-// block maximum of per-thread values (blockDim.x a power of two <= 1024)
+// block maximum of per-thread values (blockDim.x a multiple of 32, at most
+// 1024): a butterfly of exchanges in each warp, then the warps' maxima (a
+// maximum does not depend on the order)
 __device__ __forceinline__ double block_max(double v) {
-  __shared__ double red[1024];
-  red[threadIdx.x] = v;
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();  // the previous call's readers are done with red
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-    __syncthreads();
-  }
-  const double r = red[0];
-  __syncthreads();
+  double r = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); w++) r = fmax(r, red[w]);
   return r;
 }
 template <typename T>
@@ -2610,7 +2611,8 @@ __global__ void k_reinit(const __grid_constant__ Grid g, const __grid_constant__
   reinit_items(g, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 // ------------------------------------------------------- totals and init
-// one block per (m, v): fixed-order block reduction over interior cells
+// one block per (m, v): fixed-order reduction over interior cells (strided
+// per-thread sums, a butterfly in each warp, then the warps in order)
 __global__ void k_totals(const __grid_constant__ Grid g, const double* Q, double* out) {
   const int mv = blockIdx.x;
   const int m = mv / g.NV, v = mv % g.NV;
@@ -2619,14 +2621,15 @@ __global__ void k_totals(const __grid_constant__ Grid g, const double* Q, double
     const long long c = interior_cell(g, idx);
     s += g.geom == 1 ? Q[qidx(g, m, v, c)] * vfac(g, c) : Q[qidx(g, m, v, c)];
   }
-  __shared__ double red[NTHREADS];
-  red[threadIdx.x] = s;
+  s = warp_sum_fixed(s);
+  __shared__ double red[NTHREADS / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
-  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+    out[mv] = t * g.V;
   }
-  if (threadIdx.x == 0) out[mv] = red[0] * g.V;
 }
 
 // The free-surface ambient is not solved: its conserved state is
